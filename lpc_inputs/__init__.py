@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs for the lattice-propagation workloads.
+
+This module only prepares inputs: solid masks, site free energies F (in kT),
+chemical shifts and the angular frequencies derived from them, initial
+populations, and the request stream of the serving workload.  It holds none of
+the method's arithmetic (no hop weights, no stencil, no reductions), so both
+the FP64 oracle and the CUDA path can consume the same arrays.
+
+Conventions
+-----------
+* Arrays are C-order ``[z][y][x]`` (x contiguous), shape ``(nz, ny, nx)``.
+* Random draws use ``numpy.random.Generator(PCG64(seed))``.  Full arrays are
+  drawn in a fixed order (mask, then F, then shift) before any masking, so the
+  draws never depend on the mask.
+* Correlated noise: N(0, 1) white noise, a periodic Gaussian filter of width
+  sigma (in sites) applied through the FFT, rescaled to unit standard
+  deviation, then mapped through the normal CDF to u in (0, 1).  A log-normal
+  pore size exp(s*g) is monotone in g, so mapping u onto a range is the
+  "log-normal pore-size field -> range" map of the workloads.
+* Shifts are given in ppm and converted to angular frequency with the 19F
+  Larmor frequency of a 300 MHz spectrometer (282 MHz, Sec. 4):
+  omega = 2*pi*nu0*delta_ppm*1e-6 rad/s.
+* Time step 5 us and residence time 1 ms (Sec. 4), so alpha = dt/tau = 0.005.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+DT = 5.0e-6            # s, Sec. 4
+NU0 = 282.0e6          # Hz, 19F at 300 MHz, Sec. 4
+TAU = 1.0e-3           # s, residence time, Sec. 4
+ALPHA = DT / TAU       # jump probability factor, Eq. 7 (alpha = dt / tau)
+KT = 1.0
+
+
+def ppm_to_omega(delta_ppm):
+    """Chemical shift (ppm) -> angular frequency (rad/s) at nu0 = 282 MHz."""
+    return 2.0 * math.pi * NU0 * np.asarray(delta_ppm, dtype=np.float64) * 1e-6
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def correlated_uniform(shape, sigma, rng):
+    """Periodic Gaussian-filtered white noise mapped to u in (0, 1).
+
+    Returns (u, g): g is the filtered field at unit standard deviation and
+    u = Phi(g) with Phi the standard normal CDF.
+    """
+    import scipy.fft
+    import scipy.special
+
+    white = rng.standard_normal(shape)
+    spec = scipy.fft.rfftn(white, workers=-1)
+    kf = [np.fft.fftfreq(n) for n in shape[:-1]] + [np.fft.rfftfreq(shape[-1])]
+    grids = np.meshgrid(*kf, indexing="ij", sparse=True)
+    k2 = sum((2.0 * math.pi * g) ** 2 for g in grids)
+    spec *= np.exp(-0.5 * sigma * sigma * k2)
+    g = scipy.fft.irfftn(spec, s=shape, workers=-1)
+    del spec
+    g -= g.mean()
+    sd = g.std()
+    if sd > 0:
+        g /= sd
+    u = scipy.special.ndtr(g)
+    return u, g
+
+
+@dataclasses.dataclass
+class LatticeInput:
+    """One lattice problem: geometry, fields and run length."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    periodic: tuple            # (px, py, pz), 1 = periodic, 0 = wall
+    alpha: float
+    dt: float
+    kT: float
+    F: np.ndarray              # float64 (nz, ny, nx), kT units
+    omega: np.ndarray          # float64 (nz, ny, nx), rad/s
+    solid: np.ndarray          # uint8 (nz, ny, nx), 1 = solid
+    rho0: np.ndarray | None    # float64 (nz, ny, nx) or None -> 1 on pore sites
+    steps: int
+    weight_dtype: int = 0      # 0 = FP32 weights, 1 = BF16 weights
+    msd_axes: int = 0          # bitmask x=1, y=2, z=4
+    regions: dict | None = None
+
+    @property
+    def n_sites(self):
+        return self.nx * self.ny * self.nz
+
+    def uniform_rho0(self):
+        """rho0 = 1 on pore sites, 0 on solid sites."""
+        return (self.solid == 0).astype(np.float64)
+
+
+def particle(edge=32, seed=1, steps=2000, solid_frac=0.30, F_mean=-2.0, F_sd=1.0,
+             shift_mean=-6.0, shift_sd=2.0, weight_dtype=0, msd_axes=7, alpha=ALPHA,
+             shape=None, periodic=(1, 1, 1)):
+    """Single carbon particle: Bernoulli solid mask, Gaussian F and shift.
+
+    Default is the 32^3 particle: 30 % solid, F ~ N(-2, 1) kT and
+    shift ~ N(-6, 2) ppm on pore sites, 0 on solid, rho0 = 1, 2000 steps.
+    ``shape`` = (nz, ny, nx) overrides the cubic edge.
+    """
+    rng = _rng(seed)
+    shp = tuple(shape) if shape is not None else (edge, edge, edge)
+    solid = (rng.random(shp) < solid_frac).astype(np.uint8)
+    F = rng.normal(F_mean, F_sd, shp)
+    delta = rng.normal(shift_mean, shift_sd, shp)
+    pore = solid == 0
+    F = np.where(pore, F, 0.0)
+    delta = np.where(pore, delta, 0.0)
+    nz, ny, nx = shp
+    return LatticeInput("particle", nx, ny, nz, tuple(periodic), alpha, DT, KT, F,
+                        ppm_to_omega(delta), solid, None, steps, weight_dtype, msd_axes)
+
+
+def particle_in_bath(edge=256, radius=80.0, seed=2, steps=10000, sigma=4.0,
+                     weight_dtype=0, msd_axes=0, alpha=ALPHA):
+    """Porous sphere of radius 80 in a 256^3 electrolyte bath, no solid sites.
+
+    Inside: F = -4 (1 - u) kT, shift = -10 (1 - u) ppm with u from correlated
+    noise (sigma 4 sites).  Outside (bulk): F = shift = 0.
+    """
+    rng = _rng(seed)
+    shp = (edge, edge, edge)
+    u, _ = correlated_uniform(shp, sigma, rng)
+    c = (edge - 1) / 2.0
+    i = np.arange(edge, dtype=np.float64) - c
+    r2 = i[:, None, None] ** 2 + i[None, :, None] ** 2 + i[None, None, :] ** 2
+    inside = r2 < radius * radius
+    F = np.where(inside, -4.0 * (1.0 - u), 0.0)
+    delta = np.where(inside, -10.0 * (1.0 - u), 0.0)
+    solid = np.zeros(shp, np.uint8)
+    return LatticeInput("particle_in_bath", edge, edge, edge, (1, 1, 1), alpha, DT, KT, F,
+                        ppm_to_omega(delta), solid, None, steps, weight_dtype, msd_axes,
+                        regions={"inside": inside})
+
+
+def supercapacitor(nx=2048, ny=256, nz=256, electrode=896, bulk=256, seeds=(31, 32),
+                   sigma=4.0, steps=5000, weight_dtype=1, msd_axes=1, alpha=ALPHA):
+    """Electrode / bulk / electrode slab along x, walls at x = 0 and x = nx - 1.
+
+    Each electrode has its own correlated field (its own seed) on its own
+    sub-box; F = -4 (1 - u) kT and shift = -10 (1 - u) ppm there; the bulk
+    separator has F = shift = 0.  No solid sites.  BF16 weights, MSD along x.
+    """
+    assert 2 * electrode + bulk == nx
+    F = np.zeros((nz, ny, nx))
+    delta = np.zeros((nz, ny, nx))
+    x_lo = (0, electrode + bulk)
+    for seed, x0 in zip(seeds, x_lo):
+        u, _ = correlated_uniform((nz, ny, electrode), sigma, _rng(seed))
+        F[:, :, x0:x0 + electrode] = -4.0 * (1.0 - u)
+        delta[:, :, x0:x0 + electrode] = -10.0 * (1.0 - u)
+        del u
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    regions = {"electrode_minus": (0, electrode), "bulk": (electrode, electrode + bulk),
+               "electrode_plus": (electrode + bulk, nx)}
+    return LatticeInput("supercapacitor", nx, ny, nz, (0, 1, 1), alpha, DT, KT, F,
+                        ppm_to_omega(delta), solid, None, steps, weight_dtype, msd_axes,
+                        regions=regions)
+
+
+def monolith(edge=512, seed=5, steps=20000, sigma=4.0, solid_quantile=0.40,
+             weight_dtype=0, msd_axes=0, alpha=ALPHA, sub=None):
+    """Porous monolith: solid where a correlated field is below its 40 % quantile.
+
+    A second correlated field u (drawn after the mask field) sets
+    F = -5 (1 - u) kT and shift = -12 (1 - u) ppm on pore sites.
+    ``sub`` = e (int) returns the periodic [0, e)^3 corner of the same fields.
+    """
+    rng = _rng(seed)
+    shp = (edge, edge, edge)
+    _, gm = correlated_uniform(shp, sigma, rng)
+    thr = np.quantile(gm, solid_quantile) if edge <= 256 else _quantile_sample(gm, solid_quantile)
+    solid = (gm < thr).astype(np.uint8)
+    del gm
+    u, _ = correlated_uniform(shp, sigma, rng)
+    pore = solid == 0
+    F = np.where(pore, -5.0 * (1.0 - u), 0.0)
+    delta = np.where(pore, -12.0 * (1.0 - u), 0.0)
+    del u
+    name = "monolith"
+    if sub is not None:
+        F = np.ascontiguousarray(F[:sub, :sub, :sub])
+        delta = np.ascontiguousarray(delta[:sub, :sub, :sub])
+        solid = np.ascontiguousarray(solid[:sub, :sub, :sub])
+        shp = (sub, sub, sub)
+        name = "monolith_sub"
+    nz, ny, nx = shp
+    return LatticeInput(name, nx, ny, nz, (1, 1, 1), alpha, DT, KT, F, ppm_to_omega(delta),
+                        solid, None, steps, weight_dtype, msd_axes)
+
+
+def _quantile_sample(a, q):
+    """Exact quantile by partition (avoids the full sort of a huge array)."""
+    flat = a.reshape(-1)
+    k = int(q * (flat.size - 1))
+    return float(np.partition(flat, k)[k])
+
+
+def random_case(shape, seed, periodic=(1, 1, 1), solid_frac=0.2, F_sd=1.0, shift_sd=5.0,
+                alpha=0.5, steps=50, weight_dtype=0, msd_axes=7, dt=DT):
+    """Small random lattice for tests: Bernoulli solid, Gaussian F and shift."""
+    rng = _rng(seed)
+    shp = tuple(shape)
+    solid = (rng.random(shp) < solid_frac).astype(np.uint8)
+    F = rng.normal(0.0, F_sd, shp)
+    delta = rng.normal(0.0, shift_sd, shp)
+    pore = solid == 0
+    F = np.where(pore, F, 0.0)
+    delta = np.where(pore, delta, 0.0)
+    nz, ny, nx = shp
+    return LatticeInput("random", nx, ny, nz, tuple(periodic), alpha, dt, KT, F,
+                        ppm_to_omega(delta), solid, None, steps, weight_dtype, msd_axes)
+
+
+@dataclasses.dataclass
+class Request:
+    """One lattice solve of the serving stream."""
+    rid: int
+    arrival_s: float
+    edge: int
+    steps: int
+    seed: int
+
+    def lattice(self, steps=None):
+        return particle(edge=self.edge, seed=self.seed,
+                        steps=self.steps if steps is None else steps, msd_axes=0)
+
+
+def request_stream(n=1000, seed=4, edge_lo=24, edge_hi=192, steps_lo=1000, steps_hi=20000,
+                   rate_per_s=50.0):
+    """Serving stream: log-uniform cubic edges, uniform step counts, Poisson arrivals.
+
+    Request i uses the particle fields of seed 1000 + i.
+    """
+    rng = _rng(seed)
+    edges = np.rint(np.exp(rng.uniform(math.log(edge_lo), math.log(edge_hi), n))).astype(int)
+    steps = rng.integers(steps_lo, steps_hi + 1, n)
+    gaps = rng.exponential(1.0 / rate_per_s, n)
+    t = np.cumsum(gaps) - gaps[0]
+    return [Request(i, float(t[i]), int(edges[i]), int(steps[i]), 1000 + i) for i in range(n)]
+
+
+CONFIGS = {
+    "particle_32": lambda: particle(),
+    "particle_in_bath_256": lambda: particle_in_bath(),
+    "supercapacitor_2048x256x256": lambda: supercapacitor(),
+    "monolith_512": lambda: monolith(),
+    "monolith_512_sub64": lambda: monolith(sub=64),
+}

@@ -1,0 +1,215 @@
+"""FP64 CPU oracle of the LPC3D lattice step (arXiv 2603.22553).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library ``paper_2603_22553_b300``; both consume the seeded
+inputs of ``lpc_inputs``.
+
+The arithmetic lives in ``lpc_oracle.c`` (plain triple loops, FP64); this
+module marshals numpy arrays into it and adds the plain downstream formulas:
+
+* ``pack``: hop weights w_k (Eq. 1, Sec. 2.1, alpha of Eq. 7), stay weights
+  s = 1 - sum_k w_k, rotation factors R = exp(i omega dt).
+* ``run``: the step recursion (Eq. 13 in 3D with the stay term) for the
+  population, the complex magnetisation and the first displacement moments,
+  with the per-step sums M(n) (Eq. 12), P(n) and the MSD increments (Eq. 5).
+* ``msd``: MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0); ``diffusion``: D = MSD/(2 n dt)
+  per axis (Eq. 6-7).
+* ``spectrum``: the plain DFT of M (Eq. 9), numpy's e^{-2 pi i k n / N}.
+* ``boltzmann``: the equilibrium densities of Eq. 2 over pore sites.
+
+Parity pins are in ``tests/test_oracle_pins.py``.  The physics outputs of the
+paper's Sec. 4 (D/D_bulk in Table 1, spectral peaks of Fig. 9) need the
+missing MD/DFT parametrisation: parity unpinned for those (out of scope).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lpc_oracle.c")
+_SO = os.path.join(_HERE, "liblpc_oracle.so")
+_lib = None
+
+MODE_EXACT, MODE_F32, MODE_BF16 = 0, 1, 2
+
+
+def build(force=False):
+    """Compile the oracle with gcc (-O2 -fopenmp), in place."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.or_pack.argtypes = [ctypes.c_int] * 3 + [ip, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, ctypes.c_int, dp, dp, u8p,
+                                                     dp, dp, dp]
+        lib.or_pack.restype = ctypes.c_int
+        lib.or_run.argtypes = [ctypes.c_int] * 3 + [ip, dp, dp, dp, ctypes.c_int, ctypes.c_int64,
+                                                    ctypes.c_int, dp, dp, dp, dp, dp, dp]
+        lib.or_run.restype = ctypes.c_int
+        lib.or_boltzmann.argtypes = [ctypes.c_int64, dp, u8p, ctypes.c_double, ctypes.c_double, dp]
+        lib.or_boltzmann.restype = ctypes.c_int
+        lib.or_round_f32.argtypes = [ctypes.c_double]
+        lib.or_round_f32.restype = ctypes.c_double
+        lib.or_round_bf16.argtypes = [ctypes.c_double]
+        lib.or_round_bf16.restype = ctypes.c_double
+        lib.or_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Packed:
+    """Weights w[N, 6] (k = +x, -x, +y, -y, +z, -z), stay s[N], rotation R[N] (complex)."""
+
+    def __init__(self, shape, periodic, w, s, R):
+        self.shape = shape
+        self.periodic = periodic
+        self.w = w
+        self.s = s
+        self.R = R
+
+
+def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT):
+    lib = _load()
+    N = nx * ny * nz
+    F = _c64(F, (N,))
+    omega = _c64(omega, (N,))
+    solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+    w = np.empty((N, 6))
+    s = np.empty(N)
+    R = np.empty((N, 2))
+    per = (ctypes.c_int * 3)(*[int(p) for p in periodic])
+    rc = lib.or_pack(nx, ny, nz, per, float(alpha), float(dt), float(kT), int(mode), _dp(F),
+                     _dp(omega), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                     _dp(w), _dp(s), _dp(R))
+    if rc != 0:
+        raise ValueError("oracle pack rejected its inputs")
+    return Packed((nz, ny, nx), tuple(int(p) for p in periodic), w, s, R[:, 0] + 1j * R[:, 1])
+
+
+def pack_input(inp, mode=MODE_EXACT):
+    """``pack`` on an ``lpc_inputs.LatticeInput``."""
+    return pack(inp.nx, inp.ny, inp.nz, inp.periodic, inp.alpha, inp.dt, inp.kT, inp.F,
+                inp.omega, inp.solid, mode)
+
+
+class Result:
+    """Final state and per-step histories of an oracle run."""
+
+    def __init__(self, rho, m, mu, M, P, dmsd, msd_axes):
+        self.rho = rho          # (nz, ny, nx) float64
+        self.m = m              # (nz, ny, nx) complex128
+        self.mu = mu            # (3, nz, ny, nx) float64
+        self.M = M              # (steps+1,) complex128
+        self.P = P              # (steps+1,) float64
+        self.dmsd = dmsd        # (3, steps) float64
+        self.msd_axes = msd_axes
+
+    def msd(self, axis):
+        """MSD_a(n), n = 0..steps."""
+        return msd(self.dmsd[axis], self.P[0])
+
+
+def run(packed, rho0, steps, m0=None, mu0=None, msd_axes=7, nthreads=0):
+    """Run ``steps`` steps from rho0 (m0 = rho0 and mu0 = 0 unless given)."""
+    lib = _load()
+    nz, ny, nx = packed.shape
+    N = nx * ny * nz
+    rho = _c64(rho0, (N,)).copy()
+    if m0 is None:
+        m = np.zeros((N, 2))
+        m[:, 0] = rho
+    else:
+        m0 = np.asarray(m0, dtype=np.complex128).reshape(N)
+        m = np.ascontiguousarray(np.stack([m0.real, m0.imag], axis=1))
+    mu = np.zeros((3, N)) if mu0 is None else _c64(mu0, (3, N)).copy()
+    w = np.ascontiguousarray(packed.w, dtype=np.float64)
+    s = np.ascontiguousarray(packed.s, dtype=np.float64)
+    R = np.ascontiguousarray(np.stack([packed.R.real, packed.R.imag], axis=1))
+    M = np.zeros((steps + 1, 2))
+    P = np.zeros(steps + 1)
+    dmsd = np.zeros((3, max(steps, 1)))
+    per = (ctypes.c_int * 3)(*packed.periodic)
+    rc = lib.or_run(nx, ny, nz, per, _dp(w), _dp(s), _dp(R), int(msd_axes), int(steps),
+                    int(nthreads), _dp(rho), _dp(m), _dp(mu), _dp(M), _dp(P), _dp(dmsd))
+    if rc != 0:
+        raise ValueError("oracle run rejected its inputs")
+    return Result(rho.reshape(nz, ny, nx), (m[:, 0] + 1j * m[:, 1]).reshape(nz, ny, nx),
+                  mu.reshape(3, nz, ny, nx), M[:, 0] + 1j * M[:, 1], P, dmsd[:, :steps],
+                  msd_axes)
+
+
+def boltzmann(F, solid, kT=1.0, mean_rho=1.0):
+    """Eq. 2 over pore sites: rho_i = <rho> n_pore e^{-F_i/kT} / sum_j e^{-F_j/kT}."""
+    lib = _load()
+    shape = np.shape(F)
+    F = _c64(F).reshape(-1)
+    solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+    rho = np.empty_like(F)
+    rc = lib.or_boltzmann(F.size, _dp(F), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                          float(kT), float(mean_rho), _dp(rho))
+    if rc != 0:
+        raise ValueError("no pore site")
+    return rho.reshape(shape)
+
+
+def msd(dmsd_axis, P0):
+    """MSD(n) = sum_{j<n} dMSD(j) / P(0) for n = 0..len(dmsd)."""
+    out = np.zeros(len(dmsd_axis) + 1)
+    np.cumsum(dmsd_axis, out=out[1:])
+    return out / P0
+
+
+def diffusion(msd_n, dt):
+    """D(n) = MSD(n) / (2 n dt) per axis (Eq. 6-7 with d = 1 per axis), n >= 1."""
+    n = np.arange(len(msd_n), dtype=np.float64)
+    D = np.full(len(msd_n), np.nan)
+    D[1:] = msd_n[1:] / (2.0 * n[1:] * dt)
+    return D
+
+
+def spectrum(M, dt):
+    """Plain DFT of the FID (Eq. 9), fftshifted; returns (freq_hz, S)."""
+    S = np.fft.fftshift(np.fft.fft(np.asarray(M, dtype=np.complex128)))
+    f = np.fft.fftshift(np.fft.fftfreq(len(M), d=dt))
+    return f, S
+
+
+def round_f32(v):
+    return _load().or_round_f32(float(v))
+
+
+def round_bf16(v):
+    return _load().or_round_bf16(float(v))
+
+
+def max_threads():
+    return _load().or_max_threads()

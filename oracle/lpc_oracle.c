@@ -1,0 +1,250 @@
+/*
+ * FP64 CPU oracle for the lattice-gas / moment-propagation step of LPC3D
+ * (arXiv 2603.22553).  TEST INFRASTRUCTURE ONLY: used by the tests, the smoke
+ * check and the CPU baseline of the benchmark.  It shares no code, header or
+ * constant with the CUDA library; the two meet only through seeded inputs.
+ *
+ * What it computes (plain definitions, no blocking or fusion):
+ *
+ *  Hop weights (Sec. 2.1, Fig. 1, Eq. 1; Eq. 7 for alpha):
+ *    each of the z = 6 neighbours is attempted with probability 1/6; a move
+ *    is accepted with the Metropolis probability of Eq. 1 (1 when the target
+ *    free energy is not higher, exp(-dF/kT) otherwise) and scaled by the jump
+ *    factor alpha of Eq. 7.  A move towards a solid site, or out of the
+ *    domain across a non-periodic face, is rejected (weight 0); the particle
+ *    stays.  w_k(x) = (alpha/6) * P(x -> x+e_k) and the stay weight is
+ *    s(x) = 1 - sum_k w_k(x).
+ *
+ *  One step (master equation of the average densities, Sec. 2.1 / Eq. 2, and
+ *  the moment-propagation recursion of Sec. 2.2-2.3, Eq. 13 in 3D with the
+ *  stay term and the 1/z attempt factor):
+ *    rho'(y) = s(y) rho(y) + sum_k w_k(y-e_k) rho(y-e_k)
+ *    m'(y)   = R(y) [ s(y) m(y) + sum_k w_k(y-e_k) m(y-e_k) ],
+ *              R(y) = exp(i omega(y) dt)   (Eq. 8, 11, 13: the phase of the
+ *              destination site, applied after the hop)
+ *    mu_a'(y) = s(y) mu_a(y) + sum_k w_k(y-e_k) [mu_a(y-e_k) + d_ka rho(y-e_k)]
+ *              (first moment of the displacement along axis a, d_ka = +1 / -1
+ *              when e_k points along +a / -a, else 0: Sec. 2.2)
+ *
+ *  Per-step sums (Eq. 12, Eq. 5):
+ *    M(n) = sum_x m(x, n), P(n) = sum_x rho(x, n),
+ *    dMSD_a(n) = sum_x [2 (w_+a - w_-a)(x) mu_a(x, n) + (w_+a + w_-a)(x) rho(x, n)]
+ *    so that MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0).
+ *
+ * Readings of the paper taken here: Eq. 13 as printed has no stay term and no
+ * 1/z factor; the full master-equation form above conserves population as the
+ * text requires.  omega is an angular frequency (rad/s); R = exp(+i omega dt).
+ * Ties in Eq. 1 (E_j = E_i) accept.
+ *
+ * Layout: C order [z][y][x], x fastest; weights w[site*6 + k] with
+ * k = 0:+x 1:-x 2:+y 3:-y 4:+z 5:-z.  Sums are taken per z-plane in a fixed
+ * order and then over planes in z order, so results do not depend on the
+ * thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <fenv.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_INVALID 1
+
+/* Round a double to the nearest value with `bits` significand bits
+ * (ties to even): bits = 24 is IEEE binary32, bits = 8 is bfloat16.  Only used
+ * for finite values inside the normal range of the target format. */
+static double round_sig(double v, int bits)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    double f = frexp(v, &e);              /* v = f * 2^e, 0.5 <= |f| < 1 */
+    double scaled = ldexp(f, bits);       /* |scaled| in [2^(bits-1), 2^bits) */
+    double r = nearbyint(scaled);         /* default mode: nearest, ties even */
+    return ldexp(r, e - bits);
+}
+
+double or_round_f32(double v) { return round_sig(v, 24); }
+double or_round_bf16(double v) { return round_sig(v, 8); }
+
+static int64_t site(int x, int y, int z, int nx, int ny) { return ((int64_t)z * ny + y) * nx + x; }
+
+/* Neighbour of (x, y, z) along direction k, or -1 when it lies outside a
+ * non-periodic face. */
+static int64_t neighbour(int x, int y, int z, int k, int nx, int ny, int nz, const int* periodic)
+{
+    static const int off[6][3] = {{1,0,0},{-1,0,0},{0,1,0},{0,-1,0},{0,0,1},{0,0,-1}};
+    int c[3] = {x + off[k][0], y + off[k][1], z + off[k][2]};
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] < 0 || c[a] >= n[a]) {
+            if (!periodic[a]) return -1;
+            c[a] = (c[a] % n[a] + n[a]) % n[a];
+        }
+    }
+    return site(c[0], c[1], c[2], nx, ny);
+}
+
+/*
+ * Hop weights, stay weights and rotation factors.
+ * mode 0: exact FP64.  mode 1: weights and R rounded to binary32.
+ * mode 2: weights rounded to bfloat16, R rounded to binary32.
+ * In the rounded modes s = 1 - sum of the rounded weights (in FP64).
+ */
+int or_pack(int nx, int ny, int nz, const int* periodic, double alpha, double dt, double kT,
+            int mode, const double* F, const double* omega, const uint8_t* solid,
+            double* w, double* s, double* R)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !(alpha > 0.0 && alpha <= 1.0) || !(kT > 0.0)) return OR_INVALID;
+    const int64_t N = (int64_t)nx * ny * nz;
+    const double attempt = alpha / 6.0;
+    #pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t i = site(x, y, z, nx, ny);
+                double out = 0.0;
+                for (int k = 0; k < 6; ++k) {
+                    int64_t j = neighbour(x, y, z, k, nx, ny, nz, periodic);
+                    double wk = 0.0;
+                    if (j >= 0 && !solid[i] && !solid[j]) {
+                        double dE = (F[j] - F[i]) / kT;
+                        double p = (dE > 0.0) ? exp(-dE) : 1.0;   /* Eq. 1 */
+                        wk = attempt * p;
+                    }
+                    if (mode == 1) wk = or_round_f32(wk);
+                    else if (mode == 2) wk = or_round_bf16(wk);
+                    w[i * 6 + k] = wk;
+                    out += wk;
+                }
+                s[i] = 1.0 - out;
+                double th = omega[i] * dt;
+                double c = cos(th), sn = sin(th);
+                if (mode != 0) { c = or_round_f32(c); sn = or_round_f32(sn); }
+                R[2 * i] = c;
+                R[2 * i + 1] = sn;
+            }
+    (void)N;
+    return OR_OK;
+}
+
+/* Boltzmann densities of Eq. 2 over pore sites:
+ * rho_i = mean_rho * n_pore * exp(-F_i/kT) / sum_j exp(-F_j/kT), 0 on solid. */
+int or_boltzmann(int64_t N, const double* F, const uint8_t* solid, double kT, double mean_rho, double* rho)
+{
+    double z = 0.0;
+    int64_t npore = 0;
+    for (int64_t i = 0; i < N; ++i)
+        if (!solid[i]) { z += exp(-F[i] / kT); ++npore; }
+    if (npore == 0 || !(z > 0.0)) return OR_INVALID;
+    for (int64_t i = 0; i < N; ++i)
+        rho[i] = solid[i] ? 0.0 : mean_rho * (double)npore * exp(-F[i] / kT) / z;
+    return OR_OK;
+}
+
+/*
+ * nsteps steps from the state (rho, m, mu); the state arrays are updated in
+ * place.  M has 2*(nsteps+1) entries (re, im), P has nsteps+1 entries,
+ * dmsd has 3*nsteps entries laid out [axis][n] (only the axes in msd_axes,
+ * bit 0 = x, 1 = y, 2 = z, are written).  mu is [3][N].
+ */
+int or_run(int nx, int ny, int nz, const int* periodic, const double* w, const double* s,
+           const double* R, int msd_axes, int64_t nsteps, int nthreads,
+           double* rho, double* m, double* mu, double* M, double* P, double* dmsd)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0) return OR_INVALID;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int64_t N = (int64_t)nx * ny * nz;
+    double* rho2 = (double*)malloc(sizeof(double) * N);
+    double* m2 = (double*)malloc(sizeof(double) * 2 * N);
+    double* mu2 = (double*)malloc(sizeof(double) * 3 * N);
+    double* plane = (double*)malloc(sizeof(double) * 6 * nz);
+    if (!rho2 || !m2 || !mu2 || !plane) { free(rho2); free(m2); free(mu2); free(plane); return OR_INVALID; }
+
+    for (int64_t n = 0; n <= nsteps; ++n) {
+        /* sums of the current state n, and the MSD increment of step n -> n+1 */
+        #pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z) {
+            double sr = 0.0, si = 0.0, sp = 0.0, sa[3] = {0.0, 0.0, 0.0};
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    int64_t i = site(x, y, z, nx, ny);
+                    sr += m[2 * i];
+                    si += m[2 * i + 1];
+                    sp += rho[i];
+                    for (int a = 0; a < 3; ++a) {
+                        if (!(msd_axes >> a & 1)) continue;
+                        double wp = w[i * 6 + 2 * a], wm = w[i * 6 + 2 * a + 1];
+                        sa[a] += 2.0 * (wp - wm) * mu[a * N + i] + (wp + wm) * rho[i];
+                    }
+                }
+            plane[6 * z + 0] = sr; plane[6 * z + 1] = si; plane[6 * z + 2] = sp;
+            plane[6 * z + 3] = sa[0]; plane[6 * z + 4] = sa[1]; plane[6 * z + 5] = sa[2];
+        }
+        double tot[6] = {0, 0, 0, 0, 0, 0};
+        for (int z = 0; z < nz; ++z)
+            for (int q = 0; q < 6; ++q) tot[q] += plane[6 * z + q];
+        M[2 * n] = tot[0];
+        M[2 * n + 1] = tot[1];
+        P[n] = tot[2];
+        if (n == nsteps) break;
+        for (int a = 0; a < 3; ++a)
+            if (msd_axes >> a & 1) dmsd[a * nsteps + n] = tot[3 + a];
+
+        /* the step n -> n+1 (gather form) */
+        #pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    int64_t i = site(x, y, z, nx, ny);
+                    double r = s[i] * rho[i];
+                    double mr = s[i] * m[2 * i], mi = s[i] * m[2 * i + 1];
+                    double ua[3];
+                    for (int a = 0; a < 3; ++a) ua[a] = (msd_axes >> a & 1) ? s[i] * mu[a * N + i] : 0.0;
+                    for (int k = 0; k < 6; ++k) {
+                        /* the source of a hop along e_k into i sits at i - e_k,
+                         * i.e. the neighbour of i in the opposite direction k^1 */
+                        int64_t j = neighbour(x, y, z, k ^ 1, nx, ny, nz, periodic);
+                        if (j < 0) continue;
+                        double wk = w[j * 6 + k];
+                        r += wk * rho[j];
+                        mr += wk * m[2 * j];
+                        mi += wk * m[2 * j + 1];
+                        int axis = k >> 1;
+                        double d = (k & 1) ? -1.0 : 1.0;
+                        for (int a = 0; a < 3; ++a) {
+                            if (!(msd_axes >> a & 1)) continue;
+                            ua[a] += wk * (mu[a * N + j] + (a == axis ? d * rho[j] : 0.0));
+                        }
+                    }
+                    rho2[i] = r;
+                    double c = R[2 * i], sn = R[2 * i + 1];
+                    m2[2 * i] = c * mr - sn * mi;
+                    m2[2 * i + 1] = c * mi + sn * mr;
+                    for (int a = 0; a < 3; ++a)
+                        if (msd_axes >> a & 1) mu2[a * N + i] = ua[a];
+                }
+        memcpy(rho, rho2, sizeof(double) * N);
+        memcpy(m, m2, sizeof(double) * 2 * N);
+        for (int a = 0; a < 3; ++a)
+            if (msd_axes >> a & 1) memcpy(mu + a * N, mu2 + a * N, sizeof(double) * N);
+    }
+    free(rho2); free(m2); free(mu2); free(plane);
+    return OR_OK;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
