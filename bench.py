@@ -1,0 +1,385 @@
+"""Throughput of the lattice-propagation step on B300.
+
+One bench step = one call of ``lattice_step_n(h, block)`` (``block`` lattice
+time steps, each a full pass of the hot path: population hop, magnetisation
+hop and rotation, FID / population sums) over the workload's lattice.  The
+default workload is the 512^3 porous monolith (40 % solid, FP32 state and
+FP32 hop weights); its state and weights (7.8 GB) are far larger than L2, so
+no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the workload on its own GPU (no data-path collective); ``value``
+is the site updates of all ranks divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle instead (the only other place
+this script runs it), on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lpc_inputs  # noqa: E402
+
+WORKLOADS = {
+    "monolith_512": dict(make=lambda: lpc_inputs.monolith(edge=512, msd_axes=0),
+                         desc="512^3 porous monolith, 40% solid (correlated noise sigma 4), "
+                              "F in [-5,0] kT, shift in [-12,0] ppm, periodic, FP32 state, "
+                              "FP32 hop weights", sub=64),
+    "monolith_512_bf16": dict(make=lambda: lpc_inputs.monolith(edge=512, msd_axes=0, weight_dtype=1),
+                              desc="512^3 porous monolith, FP32 state, BF16 hop weights", sub=64),
+    "particle_in_bath_256": dict(make=lambda: lpc_inputs.particle_in_bath(),
+                                 desc="256^3 bath with a porous sphere of radius 80, FP32", sub=64),
+    "supercapacitor_2048x256x256": dict(make=lambda: lpc_inputs.supercapacitor(),
+                                        desc="2048x256x256 electrode/bulk/electrode slab, x walls, "
+                                             "BF16 weights, MSD along x", sub=64),
+    "particle_32": dict(make=lambda: lpc_inputs.particle(msd_axes=0), desc="32^3 particle, FP32",
+                        sub=32),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--block", type=int, default=64, help="lattice steps per bench step")
+    ap.add_argument("--schedule", default="auto", help="auto | step1 | tb:K")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels_step.cu", "kernels_tb.cu", "lpc_internal.cuh"):
+        p = os.path.join(ROOT, "paper_2603_22553_b300", "csrc", name)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload, sites):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+    except Exception:
+        return None
+    if e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"]) * sites / float(e["sites"])
+
+
+def oracle_sample(inp_sub, seconds, nthreads=0):
+    """Time the FP64 oracle on a sub-lattice for about ``seconds``."""
+    import oracle
+    pk = oracle.pack_input(inp_sub, oracle.MODE_EXACT)
+    rho0 = inp_sub.uniform_rho0()
+    t0 = time.perf_counter()
+    oracle.run(pk, rho0, 10, msd_axes=inp_sub.msd_axes, nthreads=nthreads)
+    t_probe = time.perf_counter() - t0
+    steps = max(10, int(10 * seconds / max(t_probe, 1e-3)))
+    t0 = time.perf_counter()
+    res = oracle.run(pk, rho0, steps, msd_axes=inp_sub.msd_axes, nthreads=nthreads)
+    t = time.perf_counter() - t0
+    return inp_sub.n_sites * steps / t, steps, t, res
+
+
+def sub_lattice(inp, e):
+    """The periodic [0, e)^3 corner of a workload's fields (same seeds)."""
+    sub = lpc_inputs.LatticeInput(inp.name + "_sub", e, e, e, (1, 1, 1), inp.alpha, inp.dt, inp.kT,
+                                  np.ascontiguousarray(inp.F[:e, :e, :e]),
+                                  np.ascontiguousarray(inp.omega[:e, :e, :e]),
+                                  np.ascontiguousarray(inp.solid[:e, :e, :e]), None, inp.steps,
+                                  inp.weight_dtype, inp.msd_axes)
+    return sub
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = WORKLOADS[args.workload]
+    inp = wl["make"]()
+    sub = sub_lattice(inp, wl["sub"])
+    del inp
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(sub, per_step / 4)
+    rates = []
+    t_all = 0.0
+    steps_all = 0
+    for _ in range(args.steps):
+        r, s, t, _ = oracle_sample(sub, per_step)
+        rates.append(r)
+        t_all += t
+        steps_all += s
+    value = sub.n_sites * steps_all / t_all
+    sample = "%d^3 periodic corner of the %s fields, FP64, %d lattice steps over %d bench steps" % (
+        wl["sub"], args.workload, steps_all, args.steps)
+    line = {"impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def parse_schedule(s):
+    from paper_2603_22553_b300 import binding as B
+    if s == "auto":
+        return None
+    if s == "step1":
+        return (B.LPC_KERNEL_STEP1, 1)
+    if s.startswith("tb:"):
+        return (B.LPC_KERNEL_TB, int(s[3:]))
+    raise SystemExit("bad --schedule " + s)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.load()
+
+    wl = WORKLOADS[args.workload]
+    inp = wl["make"]()
+    N = inp.n_sites
+    sched = parse_schedule(args.schedule)
+
+    lat = Lattice.from_input(inp)
+    if sched:
+        lat.set_schedule(*sched)
+    info = lat.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        lat.step(args.block)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(dev)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lat.step(args.block)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    lattice_steps = args.steps * args.block
+    value = ws * N * lattice_steps / (ms / 1e3)
+    kernel_name = "step_tb" if info["kernel"] == B.LPC_KERNEL_TB else "step1"
+    launches = args.steps * (args.block // max(1, info["block_steps"]))
+    bpu = info["bytes_per_site_update"]
+    per_launch_ms = ms / launches
+    achieved = bpu * N * info["block_steps"] / (per_launch_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic(kernel_name, args.workload, N)
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    cpu = None
+    parity = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        sub = sub_lattice(inp, wl["sub"])
+        r, s, t, res = oracle_sample(sub, args.cpu_seconds)
+        cpu = {"value": r, "unit": "site-updates/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": "%d^3 periodic corner of the workload fields, %d steps, FP64 (%.1f s)" % (
+                   wl["sub"], s, t)}
+        # parity of the same sample on the GPU (FID relative L2 vs the exact oracle)
+        g = Lattice.from_input(sub)
+        if sched:
+            g.set_schedule(*sched)
+        g.step(s)
+        M = g.fid()
+        rho = g.density().astype(np.float64)
+        g.close()
+        parity = {"fid_rel_l2": float(np.linalg.norm(M - res.M) / np.linalg.norm(res.M)),
+                  "density_rel_l2": float(np.linalg.norm(rho - res.rho) / np.linalg.norm(res.rho)),
+                  "sample": "%d^3 corner, %d steps, GPU (as benched) vs FP64 oracle" % (wl["sub"], s)}
+
+    e2e = None
+    if not args.no_e2e:
+        # the whole job through the public API from pinned host buffers:
+        # create (H2D of F, omega, mask + pack), K bench steps, FID + density read-back
+        Fp = torch.from_numpy(np.ascontiguousarray(inp.F)).pin_memory()
+        Op = torch.from_numpy(np.ascontiguousarray(inp.omega)).pin_memory()
+        Sp = torch.from_numpy(np.ascontiguousarray(inp.solid)).pin_memory()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lat = Lattice(inp.nx, inp.ny, inp.nz, Fp.numpy(), Op.numpy(), Sp.numpy(),
+                      periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
+                      weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes)
+        if sched:
+            lat.set_schedule(*sched)
+        for _ in range(args.steps):
+            lat.step(args.block)
+        M = lat.fid()
+        rho = lat.density()
+        t1 = time.perf_counter()
+        lat.close()
+        te = t1 - t0
+        if ws > 1:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = Fp.numel() * 8 + Op.numel() * 8 + Sp.numel()
+        d2h = M.size * 16 + rho.size * 4
+        e2e = {"value": ws * N * lattice_steps / te, "unit": "site-updates/s",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "seconds": te}
+
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if inp.weight_dtype == 0 else "f32/bf16-weights", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"],
+                       "sites": N, "lattice_steps_per_step": args.block, "kernel": kernel_name,
+                       "block_steps": info["block_steps"], "ghost": info["ghost"],
+                       "l2": "inputs larger than L2 (%.1f GB on device)" % (info["device_bytes"] / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "bytes_per_site_update": bpu},
+            "cpu_baseline": cpu,
+            "parity": parity,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * lpc3d.h -- C ABI of the B300 (sm_103a) lattice-propagation library.
+ *
+ * The library advances the lattice-gas / moment-propagation model of LPC3D
+ * (arXiv 2603.22553) on one GPU.  Per time step, for every site y of an
+ * nx x ny x nz simple cubic lattice (Sec. 2.1, Fig. 1):
+ *
+ *   rho'(y) = s(y) rho(y) + sum_k w_k(y - e_k) rho(y - e_k)
+ *   m'(y)   = R(y) [ s(y) m(y) + sum_k w_k(y - e_k) m(y - e_k) ]
+ *   mu_a'(y)= s(y) mu_a(y) + sum_k w_k(y - e_k) [ mu_a(y - e_k) + d_ka rho(y - e_k) ]
+ *
+ * with the six neighbour offsets e_k (k = +x, -x, +y, -y, +z, -z), the hop
+ * weight w_k(x) = (alpha/6) * P(x -> x + e_k) from the Metropolis rule of
+ * Eq. 1 (zero towards a solid site or across a wall), the stay weight
+ * s(x) = 1 - sum_k w_k(x) (Sec. 2.1: a rejected move leaves the particle in
+ * place; alpha is the jump factor of Eq. 7), the rotation R(y) =
+ * exp(i omega(y) dt) of the destination site (Eq. 8, 11, 13), and the first
+ * displacement moment mu_a used for the mean-square displacement (moment
+ * propagation, Sec. 2.2; d_ka = +1 / -1 for a hop along +a / -a).
+ *
+ * Every step also reduces, in FP64 from FP32 partials,
+ *   M(n) = sum_x m(x, n)                      (the FID, Eq. 12)
+ *   P(n) = sum_x rho(x, n)                    (population)
+ *   dMSD_a(n) = sum_x [2 (w_+a - w_-a) mu_a + (w_+a + w_-a) rho](x, n)
+ * and MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0) (Eq. 5 summed over steps).
+ *
+ * Conventions
+ *  - Host arrays are C order [z][y][x] with x fastest (N = nx*ny*nz values).
+ *  - Input arrays are copied during lattice_create; the caller keeps them.
+ *  - Output buffers belong to the caller.  Query calls synchronise the
+ *    lattice's stream before returning.
+ *  - Every call returns an lpc_status and never aborts the process; on
+ *    failure lpc_last_error() gives a message (thread-local).
+ *  - lattice_step_n and lattice_step_many are asynchronous on the lattice's
+ *    stream.
+ */
+#ifndef LPC3D_H
+#define LPC3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lpc_lattice lpc_lattice;   /* opaque; created and destroyed by the caller */
+
+typedef enum {
+    LPC_OK = 0,
+    LPC_ERR_INVALID = 1,   /* bad argument or misuse; nothing was changed */
+    LPC_ERR_OOM = 2,       /* the allocator returned NULL */
+    LPC_ERR_CUDA = 3,      /* a CUDA call failed; the message names it */
+    LPC_ERR_TIMEOUT = 4,   /* a bounded device wait ran out */
+    LPC_ERR_STATE = 5      /* the handle is in a state that forbids the call */
+} lpc_status;
+
+enum { LPC_WEIGHTS_F32 = 0, LPC_WEIGHTS_BF16 = 1 };
+enum { LPC_INIT_UNIFORM = 0, LPC_INIT_BOLTZMANN = 1 };
+enum { LPC_KERNEL_AUTO = 0, LPC_KERNEL_STEP1 = 1, LPC_KERNEL_TB = 2 };
+
+/*
+ * Device memory hooks.  alloc returns device memory of at least `bytes`
+ * bytes, aligned to 256 bytes, usable on `stream` (a cudaStream_t), or NULL.
+ * free releases it.  With a NULL lpc_allocator the library uses
+ * cudaMallocAsync / cudaFreeAsync on the lattice's stream.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* p, void* stream, void* ctx);
+    void* ctx;
+} lpc_allocator;
+
+/*
+ * Lattice parameters (Sec. 3.2 item 1: dimensions, time step, boundary
+ * conditions).
+ *   nx, ny, nz    lattice edge lengths, each >= 1; nx*ny*nz <= 2^31 - 1.
+ *   periodic[a]   1 = periodic along axis a (ghost-layer semantics),
+ *                 0 = wall: a move out of the domain is rejected.
+ *   alpha         jump probability factor of Eq. 7, 0 < alpha <= 1.
+ *   dt            time step in seconds; R = exp(i omega dt).
+ *   kT            thermal energy in the units of F (> 0).
+ *   weight_dtype  LPC_WEIGHTS_F32 or LPC_WEIGHTS_BF16 storage of w_k.
+ *   msd_axes      bit mask of the axes whose first moment is propagated
+ *                 (x = 1, y = 2, z = 4); 0 = none.
+ *   init          initial population when rho0 is NULL: LPC_INIT_UNIFORM
+ *                 (1 on pore sites) or LPC_INIT_BOLTZMANN (Eq. 2 with
+ *                 mean 1 over pore sites).
+ *   ghost         ghost-layer width in x and y (1..8), 0 = automatic; the
+ *                 temporally blocked kernel needs ghost >= its block depth.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t periodic[3];
+    double alpha;
+    double dt;
+    double kT;
+    int32_t weight_dtype;
+    int32_t msd_axes;
+    int32_t init;
+    int32_t ghost;
+} lpc_params;
+
+/* Static facts about a lattice (for sizing, admission and reporting). */
+typedef struct {
+    int64_t n_sites;          /* nx*ny*nz */
+    int64_t n_padded;         /* sites of the ghost-padded device arrays */
+    int32_t ghost;            /* ghost width in x and y */
+    int32_t pitch_x;          /* padded x extent (elements) */
+    int32_t pitch_y;          /* padded y extent */
+    int32_t kernel;           /* LPC_KERNEL_* chosen for lattice_step_n */
+    int32_t block_steps;      /* time steps per launch of that kernel */
+    int32_t reserved;
+    int64_t device_bytes;     /* device memory held by the lattice */
+    int64_t bytes_per_site_update; /* algorithmic HBM bytes of one site update */
+} lpc_info;
+
+/*
+ * Create a lattice (Sec. 3.2 items 1-2: fields are created from the site
+ * free energies F, frequencies omega and the solid mask; hop weights are
+ * packed once from Eq. 1 and Eq. 7, rotation factors R are computed in
+ * FP64 and rounded to FP32).
+ *   F       [N] double, free energy of every site (kT units when kT = 1);
+ *           must be finite on pore sites, ignored on solid sites.
+ *   omega   [N] double, angular frequency in rad/s (finite).
+ *   solid   [N] uint8, nonzero = solid (inaccessible) site.
+ *   rho0    [N] double initial population or NULL (see params.init); solid
+ *           sites are forced to 0.  m(x, 0) = rho(x, 0), mu(x, 0) = 0.
+ *   a       allocator or NULL.   stream: cudaStream_t or NULL (default).
+ *   out     receives the handle (NULL on failure).
+ * Records M(0) and P(0).  Errors: LPC_ERR_INVALID (bad shape, alpha outside
+ * (0, 1], non-finite inputs on pore sites, NULL arrays), LPC_ERR_OOM,
+ * LPC_ERR_CUDA.
+ */
+lpc_status lattice_create(const lpc_params* p, const double* F, const double* omega,
+                          const uint8_t* solid, const double* rho0, const lpc_allocator* a,
+                          void* stream, lpc_lattice** out);
+
+/* Release every device buffer of the lattice.  NULL-safe. */
+lpc_status lattice_destroy(lpc_lattice* h);
+
+/*
+ * Advance n >= 0 time steps (Sec. 3.2 item 4, the propagation phase),
+ * recording M, P and dMSD for every step.  Asynchronous on the lattice's
+ * stream; may grow the device history buffers (via the allocator) before
+ * launching.  Errors: LPC_ERR_INVALID (NULL handle, n < 0), LPC_ERR_OOM,
+ * LPC_ERR_CUDA.
+ */
+lpc_status lattice_step_n(lpc_lattice* h, int64_t n);
+
+/*
+ * Advance several lattices; lattice i by n[i] steps.  Lattices that share a
+ * stream are advanced together in batched launches (one launch covers the
+ * tiles of every lattice in the group), so many small lattices fill the
+ * GPU.  Each lattice's results are identical to lattice_step_n on it alone.
+ */
+lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count);
+
+/* Choose the step kernel: LPC_KERNEL_AUTO / STEP1 / TB, with TB block
+ * depth k (1..ghost).  LPC_ERR_INVALID if the combination is impossible. */
+lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps);
+
+/* Wait for all queued work of the lattice. */
+lpc_status lattice_sync(lpc_lattice* h);
+
+/* Number of time steps completed (queued steps count once queued). */
+lpc_status lattice_steps_done(lpc_lattice* h, int64_t* n);
+
+/* Static facts about the lattice. */
+lpc_status lattice_info(lpc_lattice* h, lpc_info* out);
+
+/*
+ * FID samples M(n) for n = first .. first+count-1 (Eq. 12; G(n) = M(n)/P(0)
+ * is the normalised FID of Eq. 8 / Eq. 11).  out: 2*count doubles,
+ * (re, im) pairs, host memory.  LPC_ERR_INVALID if the range exceeds the
+ * steps done (0 .. steps_done inclusive).
+ */
+lpc_status lattice_fid(lpc_lattice* h, int64_t first, int64_t count, double* out);
+
+/* Population P(n) = sum_x rho(x, n), same range rules as lattice_fid. */
+lpc_status lattice_population(lpc_lattice* h, int64_t first, int64_t count, double* out);
+
+/*
+ * Mean-square displacement along `axis` (0 = x, 1 = y, 2 = z):
+ * MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0) for n = first .. first+count-1,
+ * from moment propagation (Sec. 2.2, Eq. 5); D = MSD / (2 n dt) per axis.
+ * LPC_ERR_INVALID if the axis is not in msd_axes or the range is invalid.
+ */
+lpc_status lattice_msd(lpc_lattice* h, int32_t axis, int64_t first, int64_t count, double* out);
+
+/*
+ * Current site populations rho(x, n) (the densities of Sec. 3.2 item 5),
+ * N floats, C order.  out_is_device = 1: `out` is device memory (copied on
+ * the lattice's stream), 0: host memory.
+ */
+lpc_status lattice_density(lpc_lattice* h, float* out, int32_t out_is_device);
+
+/* Current magnetisation m(x, n): N (re, im) float pairs. */
+lpc_status lattice_magnetization(lpc_lattice* h, float* out, int32_t out_is_device);
+
+/* Current first moment mu_axis(x, n): N floats; the axis must be enabled. */
+lpc_status lattice_moment(lpc_lattice* h, int32_t axis, float* out, int32_t out_is_device);
+
+/*
+ * Packed hop weights as stored, widened to float: out[k*N + i] = w_k(site i)
+ * for k = +x, -x, +y, -y, +z, -z (6*N floats, host).  Solid sites and moves
+ * into solids or across walls are exactly 0 (the geometry of Fig. 1).
+ */
+lpc_status lattice_weights(lpc_lattice* h, float* out);
+
+/* Rotation factors R(x) = exp(i omega dt) as stored: N (re, im) float pairs. */
+lpc_status lattice_rotation(lpc_lattice* h, float* out);
+
+/* Solid mask as stored on the device: N bytes (0 pore, 1 solid). */
+lpc_status lattice_solid(lpc_lattice* h, uint8_t* out);
+
+/*
+ * Checkpoint / resume.  The state blob holds rho, m, mu (FP32, interior
+ * sites), the step counter and the FP64 history; lattice_state_size gives
+ * its size.  lattice_set_state requires a lattice created with the same
+ * parameters.  Resuming and running m more steps gives the same results,
+ * bit for bit, as running them without the checkpoint.
+ */
+lpc_status lattice_state_size(lpc_lattice* h, size_t* bytes);
+lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes);
+lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes);
+
+/*
+ * Equilibration phase (Sec. 3.2 item 3): advance the population only
+ * (m and mu are reset to m = rho, mu = 0 afterwards and the history is
+ * restarted at n = 0) until max_x |rho(x, t+1) - rho(x, t)| < threshold,
+ * checked every check_every steps, or until max_iter steps.  iters and
+ * max_diff (nullable) receive the steps taken and the last difference.
+ */
+lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_iter,
+                               int32_t check_every, int64_t* iters, double* max_diff);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lpc_last_error(void);
+
+/* Library version string. */
+const char* lpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPC3D_H */

@@ -1,0 +1,309 @@
+// Once-per-lattice kernels: hop-weight packing, state initialisation, the
+// initial sums, and the layout conversions used by the query calls.
+#include "lpc_internal.cuh"
+
+namespace lpc {
+
+namespace {
+
+// Interior coordinate of a padded position along one axis, or -1 when the
+// position lies outside a wall (or in the pitch padding).
+__device__ __forceinline__ int unpad_coord(int p, int G, int n, int per) {
+    int c = p - G;
+    if (c >= 0 && c < n) return c;
+    if (!per || p >= n + 2 * G) return -1;
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+__device__ __forceinline__ long long nb_site(int x, int y, int z, int k, int nx, int ny, int nz,
+                                             int px, int py, int pz) {
+    int c[3] = {x, y, z};
+    const int n[3] = {nx, ny, nz};
+    const int per[3] = {px, py, pz};
+    const int a = k >> 1;
+    c[a] += (k & 1) ? -1 : 1;
+    if (c[a] < 0 || c[a] >= n[a]) {
+        if (!per[a]) return -1;
+        c[a] = c[a] < 0 ? n[a] - 1 : 0;
+    }
+    return ((long long)c[2] * ny + c[1]) * nx + c[0];
+}
+
+template <typename WT> __device__ __forceinline__ WT round_weight(double w);
+template <> __device__ __forceinline__ float round_weight<float>(double w) { return __double2float_rn(w); }
+template <> __device__ __forceinline__ __nv_bfloat16 round_weight<__nv_bfloat16>(double w) {
+    return __double2bfloat16(w);
+}
+
+// Hop weights of Eq. 1 (Metropolis) times alpha/6 (six equally likely
+// attempts, jump factor of Eq. 7); zero towards solids and across walls.
+// Rotation R = exp(i omega dt) in FP64, rounded to FP32.
+template <typename WT>
+__global__ void k_pack(LatticeView v, const double* __restrict__ F, const double* __restrict__ omega,
+                       const uint8_t* __restrict__ solid, double alpha, double dt, double kT) {
+    const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pidx >= v.Np) return;
+    WT* W = static_cast<WT*>(const_cast<void*>(v.w));
+    float2* R = const_cast<float2*>(v.R);
+    const int px = (int)(pidx % v.Xp);
+    const long long t = pidx / v.Xp;
+    const int py = (int)(t % v.Yp);
+    const int z = (int)(t / v.Yp);
+    const int x = unpad_coord(px, v.G, v.nx, v.per_x);
+    const int y = unpad_coord(py, v.G, v.ny, v.per_y);
+    double w[6] = {0, 0, 0, 0, 0, 0};
+    float2 rot = make_float2(1.0f, 0.0f);
+    if (x >= 0 && y >= 0) {
+        const long long i = ((long long)z * v.ny + y) * v.nx + x;
+        if (!solid[i]) {
+            const double attempt = alpha / 6.0;
+            for (int k = 0; k < 6; ++k) {
+                const long long j = nb_site(x, y, z, k, v.nx, v.ny, v.nz, v.per_x, v.per_y, v.per_z);
+                if (j < 0 || solid[j]) continue;
+                const double dE = (F[j] - F[i]) / kT;
+                w[k] = attempt * (dE > 0.0 ? exp(-dE) : 1.0);
+            }
+        }
+        double s, c;
+        sincos(omega[i] * dt, &s, &c);
+        rot = make_float2(__double2float_rn(c), __double2float_rn(s));
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) W[k * v.Np + pidx] = round_weight<WT>(w[k]);
+    R[pidx] = rot;
+}
+
+// Deterministic FP64 sums for the Boltzmann normalisation: per-block fixed
+// order, then one block over the partials.
+__global__ void k_boltz_partial(const double* __restrict__ F, const uint8_t* __restrict__ solid,
+                                long long N, double kT, double* part) {
+    __shared__ double sz[256];
+    __shared__ double sn[256];
+    double z = 0.0, n = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        if (!solid[i]) { z += exp(-F[i] / kT); n += 1.0; }
+    sz[threadIdx.x] = z;
+    sn[threadIdx.x] = n;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { sz[threadIdx.x] += sz[threadIdx.x + o]; sn[threadIdx.x] += sn[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = sz[0]; part[2 * blockIdx.x + 1] = sn[0]; }
+}
+
+__global__ void k_boltz_final(double* part, int nblk) {
+    if (threadIdx.x != 0) return;
+    double z = 0.0, n = 0.0;
+    for (int b = 0; b < nblk; ++b) { z += part[2 * b]; n += part[2 * b + 1]; }
+    part[2 * nblk] = z;
+    part[2 * nblk + 1] = n;
+}
+
+// rho(x, 0) from rho0 (FP64, interior order), 1 on pore sites, or Eq. 2.
+// m = rho, mu = 0.  Every padded position gets the value of its interior
+// preimage (0 outside walls and in the pitch padding).
+__global__ void k_init(LatticeView v, const double* __restrict__ rho0, int mode,
+                       const double* __restrict__ F, const uint8_t* __restrict__ solid, double kT,
+                       const double* __restrict__ zsum /* [Z, npore] or null */) {
+    const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pidx >= v.Np) return;
+    const int px = (int)(pidx % v.Xp);
+    const long long t = pidx / v.Xp;
+    const int py = (int)(t % v.Yp);
+    const int z = (int)(t / v.Yp);
+    const int x = unpad_coord(px, v.G, v.nx, v.per_x);
+    const int y = unpad_coord(py, v.G, v.ny, v.per_y);
+    float r = 0.0f;
+    if (x >= 0 && y >= 0) {
+        const long long i = ((long long)z * v.ny + y) * v.nx + x;
+        if (!solid[i]) {
+            if (rho0) r = __double2float_rn(rho0[i]);
+            else if (mode == LPC_INIT_BOLTZMANN) r = __double2float_rn(zsum[1] * exp(-F[i] / kT) / zsum[0]);
+            else r = 1.0f;
+        }
+    }
+    v.rho_out[pidx] = r;
+    v.m_out[pidx] = make_float2(r, 0.0f);
+    for (int a = 0; a < 3; ++a)
+        if (v.msd_axes >> a & 1) v.mu_out[a][pidx] = 0.0f;
+}
+
+// Sums of the current state (M, P) into history entry *step + 1, using the
+// same row-butterfly structure as the step kernels.
+__global__ void __launch_bounds__(256) k_sum_state(LatticeView v) {
+    __shared__ double smem[8 * kNumSums];
+    double acc[1][kNumSums] = {{0, 0, 0, 0, 0, 0}};
+    const int lane = threadIdx.x;
+    const int rows = v.ny * v.nz;
+    const int segs = (v.nx + 31) / 32;
+    const long long plane = (long long)v.Xp * v.Yp;
+    for (long long r = (long long)blockIdx.x * 8 + threadIdx.y; r < (long long)rows * segs;
+         r += (long long)gridDim.x * 8) {
+        const int seg = (int)(r % segs);
+        const int row = (int)(r / segs);
+        const int y = row % v.ny, z = row / v.ny;
+        const int x = seg * 32 + lane;
+        float vr = 0.f, vi = 0.f, vp = 0.f;
+        if (x < v.nx) {
+            const long long i = z * plane + (long long)(y + v.G) * v.Xp + x + v.G;
+            const float2 m = v.m_in[i];
+            vr = m.x; vi = m.y; vp = v.rho_in[i];
+        }
+        vr = warp_sum_f32(vr); vi = warp_sum_f32(vi); vp = warp_sum_f32(vp);
+        if (lane == 0) { acc[0][0] += vr; acc[0][1] += vi; acc[0][2] += vp; }
+    }
+    block_finish<8>(v, acc, 1, smem);
+}
+
+// Interior extraction: dst[i] = src[padded(i)] for elements of 4 or 8 bytes.
+template <typename T>
+__global__ void k_unpad(const T* __restrict__ src, LatticeView v, T* __restrict__ dst) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % v.nx);
+        const long long t = i / v.nx;
+        const int y = (int)(t % v.ny);
+        const int z = (int)(t / v.ny);
+        dst[i] = src[((long long)z * v.Yp + y + v.G) * v.Xp + x + v.G];
+    }
+}
+
+// Interior scatter with ghost images (inverse of k_unpad).
+template <typename T>
+__global__ void k_pad(const T* __restrict__ src, LatticeView v, T* __restrict__ dst) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    const long long plane = (long long)v.Xp * v.Yp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % v.nx);
+        const long long t = i / v.nx;
+        const int y = (int)(t % v.ny);
+        const int z = (int)(t / v.ny);
+        store_images(dst, v, x, y, z * plane, src[i]);
+    }
+}
+
+template <typename WT>
+__global__ void k_weights_f32(LatticeView v, float* __restrict__ dst) {
+    const WT* W = static_cast<const WT*>(v.w);
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % v.nx);
+        const long long t = i / v.nx;
+        const int y = (int)(t % v.ny);
+        const int z = (int)(t / v.ny);
+        const long long p = ((long long)z * v.Yp + y + v.G) * v.Xp + x + v.G;
+        for (int k = 0; k < 6; ++k) dst[k * N + i] = ldw<WT>(W + k * v.Np + p);
+    }
+}
+
+// max_x |a - b| over interior sites (non-negative floats order like their bits).
+__global__ void k_maxdiff(const float* __restrict__ a, const float* __restrict__ b, LatticeView v,
+                          unsigned int* out) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    float m = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % v.nx);
+        const long long t = i / v.nx;
+        const int y = (int)(t % v.ny);
+        const int z = (int)(t / v.ny);
+        const long long p = ((long long)z * v.Yp + y + v.G) * v.Xp + x + v.G;
+        m = fmaxf(m, fabsf(a[p] - b[p]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    const long long cap = (long long)device_props().sm_count * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
+                        const uint8_t* solid, double alpha, double dt, double kT, cudaStream_t st) {
+    const int B = 256;
+    const long long g = (v.Np + B - 1) / B;
+    if (wdtype == LPC_WEIGHTS_BF16)
+        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, dt, kT);
+    else
+        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, dt, kT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
+                              const double* F, const uint8_t* solid, double kT, double* scratch,
+                              cudaStream_t st) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    const double* zsum = nullptr;
+    if (!rho0_dev && init_mode == LPC_INIT_BOLTZMANN) {
+        const int nb = 256;
+        k_boltz_partial<<<nb, 256, 0, st>>>(F, solid, N, kT, scratch);
+        k_boltz_final<<<1, 32, 0, st>>>(scratch, nb);
+        zsum = scratch + 2 * nb;
+    }
+    const int B = 256;
+    const long long g = (v.Np + B - 1) / B;
+    k_init<<<(unsigned)g, B, 0, st>>>(v, rho0_dev, init_mode, F, solid, kT, zsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_state(const LatticeView& v, cudaStream_t st) {
+    const long long rows = (long long)v.ny * v.nz * ((v.nx + 31) / 32);
+    long long g = (rows + 7) / 8;
+    const long long cap = (long long)device_props().sm_count * 8;
+    if (g > cap) g = cap;
+    k_sum_state<<<(unsigned)g, dim3(32, 8), 0, st>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpad(const void* src, int elem_bytes, const LatticeView& v, void* dst_dev,
+                         cudaStream_t st) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    const int g = grid_for(N, 256);
+    if (elem_bytes == 8)
+        k_unpad<float2><<<g, 256, 0, st>>>(static_cast<const float2*>(src), v, static_cast<float2*>(dst_dev));
+    else
+        k_unpad<float><<<g, 256, 0, st>>>(static_cast<const float*>(src), v, static_cast<float*>(dst_dev));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad(const void* src_dev, int elem_bytes, const LatticeView& v, void* dst,
+                       cudaStream_t st) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    const int g = grid_for(N, 256);
+    if (elem_bytes == 8)
+        k_pad<float2><<<g, 256, 0, st>>>(static_cast<const float2*>(src_dev), v, static_cast<float2*>(dst));
+    else
+        k_pad<float><<<g, 256, 0, st>>>(static_cast<const float*>(src_dev), v, static_cast<float*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_f32(const LatticeView& v, int wdtype, float* dst_dev, cudaStream_t st) {
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    const int g = grid_for(N, 256);
+    if (wdtype == LPC_WEIGHTS_BF16) k_weights_f32<__nv_bfloat16><<<g, 256, 0, st>>>(v, dst_dev);
+    else k_weights_f32<float><<<g, 256, 0, st>>>(v, dst_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxdiff(const float* a, const float* b, const LatticeView& v, double* out2,
+                           cudaStream_t st) {
+    unsigned int* u = reinterpret_cast<unsigned int*>(out2);
+    cudaError_t e = cudaMemsetAsync(u, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const long long N = (long long)v.nx * v.ny * v.nz;
+    k_maxdiff<<<grid_for(N, 256), 256, 0, st>>>(a, b, v, u);
+    return cudaGetLastError();
+}
+
+}  // namespace lpc

@@ -1,0 +1,234 @@
+// Internal declarations of the lattice-propagation library (not part of the ABI).
+//
+// Device layout (all per-site arrays share it):
+//   ghost-padded planes of pitch_x * pitch_y sites, nz planes, C order
+//   [z][py][px] with px = x + G, py = y + G for interior (x, y).  The G-wide
+//   ghost bands in x and y hold copies of the periodic images (or zeros
+//   across a wall); kernels keep them current by writing every updated site
+//   to all of its images.  z has no ghosts: kernels wrap plane indices.
+//   pitch_x is a multiple of 8 so every row starts on a 16-byte boundary for
+//   FP32 / FP32x2 / BF16 arrays (required by TMA tensor maps).
+//   Hop weights are 6 planes [k][site] (k = +x, -x, +y, -y, +z, -z), FP32 or
+//   BF16; rotation factors are float2; the state is rho (float), m (float2)
+//   and mu_a (float, per enabled axis), each double-buffered.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lpc3d.h"
+
+namespace lpc {
+
+constexpr int kMaxGhost = 8;
+constexpr int kNumSums = 6;          // Mre, Mim, P, dMSD_x, dMSD_y, dMSD_z
+constexpr int kMaxTB = 8;            // deepest temporal block
+
+// Everything a step kernel needs about one lattice, passed by value.
+struct LatticeView {
+    int nx, ny, nz;
+    int G, Xp, Yp;
+    int per_x, per_y, per_z;
+    int msd_axes;
+    long long Np;                    // padded sites
+    const float* rho_in;
+    const float2* m_in;
+    const float* mu_in[3];
+    float* rho_out;
+    float2* m_out;
+    float* mu_out[3];
+    const void* w;                   // [6][Np] float or bf16
+    const float2* R;                 // [Np]
+    // reductions: per-block partials, completion counter, history
+    double* partials;                // [levels][grid][kNumSums]
+    unsigned int* counter;
+    long long* step;                 // device step counter (index of the input state)
+    double2* histM;                  // [cap]
+    double* histP;                   // [cap]
+    double* histD;                   // [3][cap]
+    long long cap;
+};
+
+// Deterministic sum helpers --------------------------------------------------
+
+// FP32 butterfly over the 32 lanes; every lane ends with the same value.
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Load a weight (FP32 or BF16 plane) widened to float.
+template <typename WT> __device__ __forceinline__ float ldw(const WT* p);
+template <> __device__ __forceinline__ float ldw<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldw<__nv_bfloat16>(const __nv_bfloat16* p) {
+    unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(static_cast<unsigned int>(u) << 16);
+}
+
+// The per-site update (shared by every kernel so that all schedules give
+// bit-identical states).  win[k] is the weight of the hop along e_k into the
+// site from its source y - e_k, nb*[k] the state at that source; wout the
+// site's own out-weights.  Explicit _rn intrinsics forbid FMA contraction
+// differences between kernels.
+struct SiteIn {
+    float wout[6];
+    float win[6];
+    float r[6];
+    float2 m[6];
+    float rc;
+    float2 mc;
+    float2 R;
+};
+
+__device__ __forceinline__ float stay_weight(const float* wout) {
+    float t = __fadd_rn(wout[0], wout[1]);
+    t = __fadd_rn(t, wout[2]);
+    t = __fadd_rn(t, wout[3]);
+    t = __fadd_rn(t, wout[4]);
+    t = __fadd_rn(t, wout[5]);
+    return __fsub_rn(1.0f, t);
+}
+
+__device__ __forceinline__ void site_rho_m(const SiteIn& q, float s, float& r_out, float2& m_out) {
+    float r = __fmul_rn(s, q.rc);
+    float ar = __fmul_rn(s, q.mc.x);
+    float ai = __fmul_rn(s, q.mc.y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        r = __fmaf_rn(q.win[k], q.r[k], r);
+        ar = __fmaf_rn(q.win[k], q.m[k].x, ar);
+        ai = __fmaf_rn(q.win[k], q.m[k].y, ai);
+    }
+    r_out = r;
+    // rotation by the destination's phase: (R.x + i R.y)(ar + i ai)
+    m_out.x = __fmaf_rn(q.R.x, ar, __fmul_rn(-q.R.y, ai));
+    m_out.y = __fmaf_rn(q.R.x, ai, __fmul_rn(q.R.y, ar));
+}
+
+// First moment along axis a: mu'(y) = s mu(y) + sum_k win_k [mu_k + d_ka r_k].
+__device__ __forceinline__ float site_mu(const float* win, const float* r, const float* mu_nb,
+                                         float s, float mu_c, int a) {
+    float u = __fmul_rn(s, mu_c);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u = __fmaf_rn(win[k], mu_nb[k], u);
+    u = __fmaf_rn(win[2 * a], r[2 * a], u);             // hop along +a: displacement +1
+    u = __fmaf_rn(-win[2 * a + 1], r[2 * a + 1], u);    // hop along -a: displacement -1
+    return u;
+}
+
+// dMSD contribution of a site: 2 (w+a - w-a) mu + (w+a + w-a) rho.
+__device__ __forceinline__ float site_dmsd(const float* wout, float mu_c, float rc, int a) {
+    float u = __fsub_rn(wout[2 * a], wout[2 * a + 1]);
+    float q = __fadd_rn(wout[2 * a], wout[2 * a + 1]);
+    return __fmaf_rn(__fmul_rn(2.0f, u), mu_c, __fmul_rn(q, rc));
+}
+
+// Write a site value to its interior position and every ghost image.
+template <typename T>
+__device__ __forceinline__ void store_images(T* base, const LatticeView& v, int x, int y,
+                                             long long zoff, T val) {
+    const int G = v.G;
+    if (x >= G && x < v.nx - G && y >= G && y < v.ny - G) {
+        base[zoff + (long long)(y + G) * v.Xp + (x + G)] = val;
+        return;
+    }
+    const int px0 = v.per_x ? (x + G) % v.nx : x + G;
+    const int pxe = v.per_x ? v.nx + 2 * G : x + G + 1;
+    const int py0 = v.per_y ? (y + G) % v.ny : y + G;
+    const int pye = v.per_y ? v.ny + 2 * G : y + G + 1;
+    for (int py = py0; py < pye; py += v.ny)
+        for (int px = px0; px < pxe; px += v.nx)
+            base[zoff + (long long)py * v.Xp + px] = val;
+}
+
+// Block reduction of per-warp FP64 accumulators, partial store and the
+// final fixed-order reduction by the last block to finish.  `acc` holds the
+// warp's sums in lane 0.  Writes the history entry for `levels` consecutive
+// steps starting at *v.step.
+template <int NW>
+__device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int levels,
+                             double* smem /* NW*kNumSums*levels */) {
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (lane == 0)
+        for (int l = 0; l < levels; ++l)
+            for (int q = 0; q < kNumSums; ++q) smem[(l * NW + warp) * kNumSums + q] = acc[l][q];
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < levels * kNumSums) {
+        const int l = tid / kNumSums, q = tid % kNumSums;
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += smem[(l * NW + w) * kNumSums + q];
+        v.partials[((long long)l * nblk + bid) * kNumSums + q] = s;
+    }
+    __threadfence();
+    __shared__ unsigned int is_last;
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(v.counter, 1u) == (unsigned)nblk - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // one warp per (level, quantity): lanes stride over blocks, then butterfly
+    const long long n0 = *v.step;
+    for (int job = warp; job < levels * kNumSums; job += NW) {
+        const int l = job / kNumSums, q = job % kNumSums;
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += __ldcg(&v.partials[((long long)l * nblk + b) * kNumSums + q]);
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            const long long n = n0 + l;            // input state index of this level
+            if (q == 0) v.histM[n + 1].x = s;
+            else if (q == 1) v.histM[n + 1].y = s;
+            else if (q == 2) v.histP[n + 1] = s;
+            else if (n >= 0 && (v.msd_axes >> (q - 3) & 1)) v.histD[(long long)(q - 3) * v.cap + n] = s;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *v.step = n0 + levels;
+        *v.counter = 0u;
+    }
+}
+
+// Host side --------------------------------------------------------------------
+
+void set_error(const std::string& msg);
+lpc_status cuda_fail(cudaError_t e, const char* what);
+
+struct DeviceProps {
+    int sm_count;
+    int max_smem_optin;
+};
+const DeviceProps& device_props();
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
+                        const uint8_t* solid, double alpha, double dt, double kT, cudaStream_t st);
+cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
+                              const double* F, const uint8_t* solid, double kT, double* scratch,
+                              cudaStream_t st);
+cudaError_t launch_sum_state(const LatticeView& v, cudaStream_t st);
+cudaError_t launch_step1(const LatticeView& v, int wdtype, cudaStream_t st);
+int step1_grid(const LatticeView& v, int wdtype);
+cudaError_t launch_unpad(const void* src, int elem_bytes, const LatticeView& v, void* dst_dev,
+                         cudaStream_t st);
+cudaError_t launch_pad(const void* src_dev, int elem_bytes, const LatticeView& v, void* dst,
+                       cudaStream_t st);
+cudaError_t launch_weights_f32(const LatticeView& v, int wdtype, float* dst_dev, cudaStream_t st);
+cudaError_t launch_maxdiff(const float* a, const float* b, const LatticeView& v, double* out2,
+                           cudaStream_t st);
+
+}  // namespace lpc

@@ -1,0 +1,709 @@
+// C ABI of the lattice-propagation library: handle lifetime, validation,
+// device memory through the caller's allocator, the step schedule (direct
+// launches or replay of captured CUDA graphs), history buffers and queries.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "lpc_internal.cuh"
+
+#define LPC_VERSION "lpc3d-b300 0.1 (sm_103a)"
+
+namespace lpc {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+lpc_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return LPC_ERR_CUDA;
+}
+
+const DeviceProps& device_props() {
+    static DeviceProps props[64];
+    static bool init[64] = {false};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!init[dev]) {
+        cudaDeviceGetAttribute(&props[dev].sm_count, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&props[dev].max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (props[dev].sm_count < 1) props[dev].sm_count = 1;
+        init[dev] = true;
+    }
+    return props[dev];
+}
+
+}  // namespace lpc
+
+using namespace lpc;
+
+struct lpc_lattice {
+    lpc_params p;
+    int G = 1, Xp = 0, Yp = 0;
+    long long N = 0, Np = 0;
+    int device = 0;
+    cudaStream_t ustream = nullptr;     // the caller's stream
+    cudaStream_t wstream = nullptr;     // private stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    lpc_allocator alloc{};
+    bool user_alloc = false;
+    long long device_bytes = 0;
+
+    float* rho[2] = {nullptr, nullptr};
+    float2* m[2] = {nullptr, nullptr};
+    float* mu[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    void* w = nullptr;
+    float2* R = nullptr;
+    uint8_t* solid = nullptr;
+    double2* histM = nullptr;
+    double* histP = nullptr;
+    double* histD = nullptr;
+    long long cap = 0;
+    double* partials = nullptr;
+    size_t partials_doubles = 0;
+    unsigned int* counter = nullptr;    // [0] completion counter, [2..3] step counter (int64)
+    long long* dstep = nullptr;
+    double* scratch = nullptr;          // small device scratch (Boltzmann sums, maxdiff)
+
+    int cur = 0;
+    long long steps = 0;
+    int kernel = LPC_KERNEL_STEP1;
+    int kdepth = 1;
+
+    // captured step sequences: [parity] -> graph of graph_len steps
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_len = 0;
+};
+
+namespace {
+
+struct Entry {
+    // Orders the private stream after the caller's stream on entry and the
+    // caller's stream after the private stream on exit.
+    lpc_lattice* h;
+    explicit Entry(lpc_lattice* hh) : h(hh) {
+        cudaSetDevice(h->device);
+        cudaEventRecord(h->ev_in, h->ustream);
+        cudaStreamWaitEvent(h->wstream, h->ev_in, 0);
+    }
+    ~Entry() {
+        cudaEventRecord(h->ev_out, h->wstream);
+        cudaStreamWaitEvent(h->ustream, h->ev_out, 0);
+    }
+};
+
+void* dalloc(lpc_lattice* h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (h->user_alloc) {
+        p = h->alloc.alloc(bytes, (void*)h->ustream, h->alloc.ctx);
+    } else {
+        if (cudaMallocAsync(&p, bytes, h->wstream) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (p) h->device_bytes += (long long)bytes;
+    return p;
+}
+
+void dfree(lpc_lattice* h, void* p, size_t bytes) {
+    if (!p) return;
+    if (h->user_alloc) h->alloc.free(p, (void*)h->ustream, h->alloc.ctx);
+    else cudaFreeAsync(p, h->wstream);
+    h->device_bytes -= (long long)bytes;
+}
+
+size_t wbytes(const lpc_lattice* h) { return h->p.weight_dtype == LPC_WEIGHTS_BF16 ? 2 : 4; }
+
+size_t history_bytes(long long cap) { return (size_t)cap * (sizeof(double2) + sizeof(double) * 4); }
+
+LatticeView make_view(lpc_lattice* h, int in) {
+    LatticeView v;
+    v.nx = h->p.nx; v.ny = h->p.ny; v.nz = h->p.nz;
+    v.G = h->G; v.Xp = h->Xp; v.Yp = h->Yp;
+    v.per_x = h->p.periodic[0]; v.per_y = h->p.periodic[1]; v.per_z = h->p.periodic[2];
+    v.msd_axes = h->p.msd_axes;
+    v.Np = h->Np;
+    v.rho_in = h->rho[in]; v.m_in = h->m[in];
+    v.rho_out = h->rho[in ^ 1]; v.m_out = h->m[in ^ 1];
+    for (int a = 0; a < 3; ++a) { v.mu_in[a] = h->mu[in][a]; v.mu_out[a] = h->mu[in ^ 1][a]; }
+    v.w = h->w; v.R = h->R;
+    v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
+    v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
+    return v;
+}
+
+void drop_graphs(lpc_lattice* h) {
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) { cudaGraphExecDestroy(h->graph[i]); h->graph[i] = nullptr; }
+    h->graph_len = 0;
+}
+
+lpc_status ensure_history(lpc_lattice* h, long long needed) {
+    if (needed <= h->cap) return LPC_OK;
+    long long ncap = h->cap * 2;
+    if (ncap < needed) ncap = needed;
+    if (ncap < 1024) ncap = 1024;
+    char* blk = (char*)dalloc(h, history_bytes(ncap));
+    if (!blk) { set_error("history allocation failed"); return LPC_ERR_OOM; }
+    double2* nM = (double2*)blk;
+    double* nP = (double*)(blk + sizeof(double2) * ncap);
+    double* nD = nP + ncap;
+    cudaError_t e = cudaMemsetAsync(blk, 0, history_bytes(ncap), h->wstream);
+    if (e == cudaSuccess && h->cap > 0) {
+        e = cudaMemcpyAsync(nM, h->histM, sizeof(double2) * h->cap, cudaMemcpyDeviceToDevice, h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(nP, h->histP, sizeof(double) * h->cap, cudaMemcpyDeviceToDevice, h->wstream);
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(nD + a * ncap, h->histD + a * h->cap, sizeof(double) * h->cap,
+                                cudaMemcpyDeviceToDevice, h->wstream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "history copy");
+    if (h->histM) {
+        // the old block must not be reused before the copies above finish
+        cudaStreamSynchronize(h->wstream);
+        dfree(h, h->histM, history_bytes(h->cap));
+    }
+    h->histM = nM; h->histP = nP; h->histD = nD; h->cap = ncap;
+    drop_graphs(h);
+    return LPC_OK;
+}
+
+lpc_status launch_one(lpc_lattice* h, cudaStream_t st) {
+    LatticeView v = make_view(h, h->cur);
+    cudaError_t e = launch_step1(v, h->p.weight_dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    h->cur ^= 1;
+    return LPC_OK;
+}
+
+constexpr int kGraphLen = 32;   // steps per captured graph (even: keeps buffer parity)
+
+lpc_status build_graph(lpc_lattice* h, int parity) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->wstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+    const int save = h->cur;
+    h->cur = parity;
+    lpc_status st = LPC_OK;
+    for (int i = 0; i < kGraphLen && st == LPC_OK; ++i) st = launch_one(h, h->wstream);
+    h->cur = save;
+    e = cudaStreamEndCapture(h->wstream, &g);
+    if (st != LPC_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+    e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    h->graph_len = kGraphLen;
+    return LPC_OK;
+}
+
+bool finite_all(const double* a, const uint8_t* solid, long long n, bool pore_only) {
+    for (long long i = 0; i < n; ++i)
+        if ((!pore_only || !solid[i]) && !std::isfinite(a[i])) return false;
+    return true;
+}
+
+void release_all(lpc_lattice* h) {
+    if (h->wstream) cudaStreamSynchronize(h->wstream);
+    drop_graphs(h);
+    const size_t Np = (size_t)h->Np;
+    for (int b = 0; b < 2; ++b) {
+        dfree(h, h->rho[b], Np * 4);
+        dfree(h, h->m[b], Np * 8);
+        for (int a = 0; a < 3; ++a) dfree(h, h->mu[b][a], Np * 4);
+    }
+    dfree(h, h->w, Np * 6 * wbytes(h));
+    dfree(h, h->R, Np * 8);
+    dfree(h, h->solid, (size_t)h->N);
+    if (h->histM) dfree(h, h->histM, history_bytes(h->cap));
+    dfree(h, h->partials, h->partials_doubles * 8);
+    dfree(h, h->counter, 256);
+    dfree(h, h->scratch, 8 * 1024);
+    if (h->ustream) cudaStreamSynchronize(h->ustream);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->wstream) cudaStreamDestroy(h->wstream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lpc_last_error(void) { return g_err.c_str(); }
+
+const char* lpc_version(void) { return LPC_VERSION; }
+
+lpc_status lattice_create(const lpc_params* p, const double* F, const double* omega,
+                          const uint8_t* solid, const double* rho0, const lpc_allocator* a,
+                          void* stream, lpc_lattice** out) {
+    if (out) *out = nullptr;
+    if (!p || !F || !omega || !solid || !out) { set_error("lattice_create: NULL argument"); return LPC_ERR_INVALID; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { set_error("lattice_create: edges must be >= 1"); return LPC_ERR_INVALID; }
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (N > 2147483647LL) { set_error("lattice_create: more than 2^31-1 sites"); return LPC_ERR_INVALID; }
+    if (!(p->alpha > 0.0 && p->alpha <= 1.0)) { set_error("lattice_create: alpha must be in (0, 1]"); return LPC_ERR_INVALID; }
+    if (!(p->kT > 0.0) || !std::isfinite(p->kT) || !std::isfinite(p->dt)) { set_error("lattice_create: kT must be > 0 and dt finite"); return LPC_ERR_INVALID; }
+    if (p->weight_dtype != LPC_WEIGHTS_F32 && p->weight_dtype != LPC_WEIGHTS_BF16) { set_error("lattice_create: weight_dtype must be 0 (FP32) or 1 (BF16)"); return LPC_ERR_INVALID; }
+    if (p->msd_axes < 0 || p->msd_axes > 7) { set_error("lattice_create: msd_axes must be a mask of 1, 2, 4"); return LPC_ERR_INVALID; }
+    if (p->init != LPC_INIT_UNIFORM && p->init != LPC_INIT_BOLTZMANN) { set_error("lattice_create: init must be 0 or 1"); return LPC_ERR_INVALID; }
+    if (p->ghost < 0 || p->ghost > kMaxGhost) { set_error("lattice_create: ghost must be in 0..8"); return LPC_ERR_INVALID; }
+    for (int i = 0; i < 3; ++i)
+        if (p->periodic[i] != 0 && p->periodic[i] != 1) { set_error("lattice_create: periodic flags must be 0 or 1"); return LPC_ERR_INVALID; }
+    if (a && (!a->alloc || !a->free)) { set_error("lattice_create: allocator needs alloc and free"); return LPC_ERR_INVALID; }
+    if (!finite_all(F, solid, N, true)) { set_error("lattice_create: non-finite F on a pore site"); return LPC_ERR_INVALID; }
+    if (!finite_all(omega, solid, N, false)) { set_error("lattice_create: non-finite omega"); return LPC_ERR_INVALID; }
+    if (rho0 && !finite_all(rho0, solid, N, true)) { set_error("lattice_create: non-finite rho0 on a pore site"); return LPC_ERR_INVALID; }
+
+    lpc_lattice* h = new (std::nothrow) lpc_lattice();
+    if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
+    h->p = *p;
+    h->N = N;
+    cudaGetDevice(&h->device);
+    int G = p->ghost;
+    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 1;
+    h->G = G;
+    h->Xp = ((p->nx + 2 * G) + 7) / 8 * 8;
+    h->Yp = p->ny + 2 * G;
+    h->Np = (long long)h->Xp * h->Yp * p->nz;
+    h->ustream = (cudaStream_t)stream;
+    if (a) { h->alloc = *a; h->user_alloc = true; }
+
+    cudaError_t e = cudaStreamCreateWithFlags(&h->wstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) { lpc_status s = cuda_fail(e, "lattice_create: stream setup"); release_all(h); delete h; return s; }
+
+    const size_t Np = (size_t)h->Np;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && (h->rho[b] = (float*)dalloc(h, Np * 4));
+        ok = ok && (h->m[b] = (float2*)dalloc(h, Np * 8));
+        for (int ax = 0; ax < 3 && ok; ++ax)
+            if (p->msd_axes >> ax & 1) ok = ok && (h->mu[b][ax] = (float*)dalloc(h, Np * 4));
+    }
+    ok = ok && (h->w = dalloc(h, Np * 6 * wbytes(h)));
+    ok = ok && (h->R = (float2*)dalloc(h, Np * 8));
+    ok = ok && (h->solid = (uint8_t*)dalloc(h, (size_t)N));
+    h->partials_doubles = (size_t)device_props().sm_count * 32 * kMaxTB * kNumSums;
+    ok = ok && (h->partials = (double*)dalloc(h, h->partials_doubles * 8));
+    ok = ok && (h->counter = (unsigned int*)dalloc(h, 256));
+    ok = ok && (h->scratch = (double*)dalloc(h, 8 * 1024));
+    // temporaries for the inputs
+    double* dF = nullptr; double* dO = nullptr; double* dR0 = nullptr;
+    ok = ok && (dF = (double*)dalloc(h, (size_t)N * 8));
+    ok = ok && (dO = (double*)dalloc(h, (size_t)N * 8));
+    if (ok && rho0) ok = (dR0 = (double*)dalloc(h, (size_t)N * 8)) != nullptr;
+    if (!ok) {
+        set_error("lattice_create: device allocation failed");
+        dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
+        release_all(h); delete h;
+        return LPC_ERR_OOM;
+    }
+    h->dstep = reinterpret_cast<long long*>(h->counter + 2);
+    lpc_status st = LPC_OK;
+    {
+        Entry en(h);
+        const long long minus_one = -1;
+        e = cudaMemsetAsync(h->counter, 0, 256, h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dO, omega, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid, solid, (size_t)N, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess && rho0) e = cudaMemcpyAsync(dR0, rho0, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+        // the byte mask is stored as given; solid means nonzero
+        if (e == cudaSuccess) st = ensure_history(h, 1024);
+        if (e == cudaSuccess && st == LPC_OK) {
+            LatticeView v = make_view(h, 1);   // writes go to buffer 0
+            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, p->dt, p->kT, h->wstream);
+            if (e == cudaSuccess)
+                e = launch_init_state(v, dR0, p->init, dF, h->solid, p->kT, h->scratch, h->wstream);
+            h->cur = 0;
+            if (e == cudaSuccess) e = launch_sum_state(make_view(h, 0), h->wstream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    }
+    dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
+    if (e != cudaSuccess || st != LPC_OK) {
+        if (st == LPC_OK) st = cuda_fail(e, "lattice_create");
+        release_all(h); delete h;
+        return st;
+    }
+    h->steps = 0;
+    *out = h;
+    return LPC_OK;
+}
+
+lpc_status lattice_destroy(lpc_lattice* h) {
+    if (!h) return LPC_OK;
+    cudaSetDevice(h->device);
+    release_all(h);
+    delete h;
+    return LPC_OK;
+}
+
+lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps) {
+    if (!h) { set_error("lattice_set_schedule: NULL handle"); return LPC_ERR_INVALID; }
+    if (kernel == LPC_KERNEL_AUTO || kernel == LPC_KERNEL_STEP1) {
+        h->kernel = LPC_KERNEL_STEP1; h->kdepth = 1;
+        drop_graphs(h);
+        return LPC_OK;
+    }
+    set_error("lattice_set_schedule: kernel not available in this build");
+    (void)block_steps;
+    return LPC_ERR_INVALID;
+}
+
+lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
+    if (!h) { set_error("lattice_step_n: NULL handle"); return LPC_ERR_INVALID; }
+    if (n < 0) { set_error("lattice_step_n: n must be >= 0"); return LPC_ERR_INVALID; }
+    if (n == 0) return LPC_OK;
+    Entry en(h);
+    lpc_status st = ensure_history(h, h->steps + n + 1);
+    if (st != LPC_OK) return st;
+    long long left = n;
+    while (left >= kGraphLen) {
+        if (!h->graph[h->cur]) {
+            st = build_graph(h, h->cur);
+            if (st != LPC_OK) return st;
+        }
+        cudaError_t e = cudaGraphLaunch(h->graph[h->cur], h->wstream);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        left -= kGraphLen;     // kGraphLen is even: parity unchanged
+    }
+    while (left > 0) {
+        st = launch_one(h, h->wstream);
+        if (st != LPC_OK) return st;
+        --left;
+    }
+    h->steps += n;
+    return LPC_OK;
+}
+
+lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count) {
+    if (count < 0 || (count > 0 && (!hs || !n))) { set_error("lattice_step_many: bad arguments"); return LPC_ERR_INVALID; }
+    for (int i = 0; i < count; ++i) {
+        lpc_status s = lattice_step_n(hs[i], n[i]);
+        if (s != LPC_OK) return s;
+    }
+    return LPC_OK;
+}
+
+lpc_status lattice_sync(lpc_lattice* h) {
+    if (!h) { set_error("lattice_sync: NULL handle"); return LPC_ERR_INVALID; }
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->ustream);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_sync");
+}
+
+lpc_status lattice_steps_done(lpc_lattice* h, int64_t* n) {
+    if (!h || !n) { set_error("lattice_steps_done: NULL argument"); return LPC_ERR_INVALID; }
+    *n = h->steps;
+    return LPC_OK;
+}
+
+lpc_status lattice_info(lpc_lattice* h, lpc_info* out) {
+    if (!h || !out) { set_error("lattice_info: NULL argument"); return LPC_ERR_INVALID; }
+    out->n_sites = h->N;
+    out->n_padded = h->Np;
+    out->ghost = h->G;
+    out->pitch_x = h->Xp;
+    out->pitch_y = h->Yp;
+    out->kernel = h->kernel;
+    out->block_steps = h->kdepth;
+    out->reserved = 0;
+    out->device_bytes = h->device_bytes;
+    long long b = 24 + 6 * (long long)wbytes(h) + 8;
+    for (int a = 0; a < 3; ++a) if (h->p.msd_axes >> a & 1) b += 8;
+    out->bytes_per_site_update = b;
+    return LPC_OK;
+}
+
+static lpc_status range_check(lpc_lattice* h, int64_t first, int64_t count, const void* out, const char* who) {
+    if (!h || (!out && count > 0)) { set_error(std::string(who) + ": NULL argument"); return LPC_ERR_INVALID; }
+    if (first < 0 || count < 0 || first + count > h->steps + 1) {
+        set_error(std::string(who) + ": range outside 0..steps_done");
+        return LPC_ERR_INVALID;
+    }
+    return LPC_OK;
+}
+
+lpc_status lattice_fid(lpc_lattice* h, int64_t first, int64_t count, double* out) {
+    lpc_status s = range_check(h, first, count, out, "lattice_fid");
+    if (s != LPC_OK || count == 0) return s;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, h->histM + first, sizeof(double2) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_fid");
+}
+
+lpc_status lattice_population(lpc_lattice* h, int64_t first, int64_t count, double* out) {
+    lpc_status s = range_check(h, first, count, out, "lattice_population");
+    if (s != LPC_OK || count == 0) return s;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, h->histP + first, sizeof(double) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_population");
+}
+
+lpc_status lattice_msd(lpc_lattice* h, int32_t axis, int64_t first, int64_t count, double* out) {
+    lpc_status s = range_check(h, first, count, out, "lattice_msd");
+    if (s != LPC_OK) return s;
+    if (axis < 0 || axis > 2 || !(h->p.msd_axes >> axis & 1)) { set_error("lattice_msd: axis not enabled"); return LPC_ERR_INVALID; }
+    if (count == 0) return LPC_OK;
+    cudaSetDevice(h->device);
+    const long long upto = first + count - 1;   // need dMSD[0 .. upto-1]
+    std::vector<double> d((size_t)(upto > 0 ? upto : 1));
+    double P0 = 0.0;
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess && upto > 0) e = cudaMemcpy(d.data(), h->histD + axis * h->cap, sizeof(double) * upto, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&P0, h->histP, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_msd");
+    double acc = 0.0;
+    for (long long n = 0; n <= upto; ++n) {
+        if (n >= first) out[n - first] = acc / P0;
+        if (n < upto) acc += d[(size_t)n];
+    }
+    return LPC_OK;
+}
+
+static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* out, int32_t out_is_device, const char* who) {
+    if (!h || !out) { set_error(std::string(who) + ": NULL argument"); return LPC_ERR_INVALID; }
+    Entry en(h);
+    LatticeView v = make_view(h, h->cur);
+    void* dst = out;
+    void* tmp = nullptr;
+    if (!out_is_device) {
+        tmp = dalloc(h, (size_t)h->N * elem);
+        if (!tmp) { set_error(std::string(who) + ": temporary allocation failed"); return LPC_ERR_OOM; }
+        dst = tmp;
+    }
+    cudaError_t e = launch_unpad(src, elem, v, dst, h->wstream);
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, (size_t)h->N * elem, cudaMemcpyDeviceToHost, h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    if (tmp) dfree(h, tmp, (size_t)h->N * elem);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, who);
+}
+
+lpc_status lattice_density(lpc_lattice* h, float* out, int32_t out_is_device) {
+    if (!h) { set_error("lattice_density: NULL handle"); return LPC_ERR_INVALID; }
+    return read_field(h, h->rho[h->cur], 4, out, out_is_device, "lattice_density");
+}
+
+lpc_status lattice_magnetization(lpc_lattice* h, float* out, int32_t out_is_device) {
+    if (!h) { set_error("lattice_magnetization: NULL handle"); return LPC_ERR_INVALID; }
+    return read_field(h, h->m[h->cur], 8, out, out_is_device, "lattice_magnetization");
+}
+
+lpc_status lattice_moment(lpc_lattice* h, int32_t axis, float* out, int32_t out_is_device) {
+    if (!h) { set_error("lattice_moment: NULL handle"); return LPC_ERR_INVALID; }
+    if (axis < 0 || axis > 2 || !(h->p.msd_axes >> axis & 1)) { set_error("lattice_moment: axis not enabled"); return LPC_ERR_INVALID; }
+    return read_field(h, h->mu[h->cur][axis], 4, out, out_is_device, "lattice_moment");
+}
+
+lpc_status lattice_weights(lpc_lattice* h, float* out) {
+    if (!h || !out) { set_error("lattice_weights: NULL argument"); return LPC_ERR_INVALID; }
+    Entry en(h);
+    float* tmp = (float*)dalloc(h, (size_t)h->N * 6 * 4);
+    if (!tmp) { set_error("lattice_weights: temporary allocation failed"); return LPC_ERR_OOM; }
+    cudaError_t e = launch_weights_f32(make_view(h, h->cur), h->p.weight_dtype, tmp, h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)h->N * 24, cudaMemcpyDeviceToHost, h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    dfree(h, tmp, (size_t)h->N * 24);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_weights");
+}
+
+lpc_status lattice_rotation(lpc_lattice* h, float* out) {
+    if (!h) { set_error("lattice_rotation: NULL handle"); return LPC_ERR_INVALID; }
+    return read_field(h, h->R, 8, out, 0, "lattice_rotation");
+}
+
+lpc_status lattice_solid(lpc_lattice* h, uint8_t* out) {
+    if (!h || !out) { set_error("lattice_solid: NULL argument"); return LPC_ERR_INVALID; }
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, h->solid, (size_t)h->N, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_solid");
+}
+
+// State blob: header, rho [N] f32, m [N] f32x2, mu [axes][N] f32, M [steps+1]
+// f64x2, P [steps+1] f64, dMSD [axes][steps] f64.
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, nz, msd_axes;
+    int64_t steps;
+};
+
+static size_t state_bytes(const lpc_lattice* h) {
+    int na = 0;
+    for (int a = 0; a < 3; ++a) na += h->p.msd_axes >> a & 1;
+    const size_t N = (size_t)h->N;
+    const size_t S = (size_t)h->steps;
+    return sizeof(StateHeader) + N * (12 + 4 * na) + (S + 1) * 24 + S * 8 * na;
+}
+
+lpc_status lattice_state_size(lpc_lattice* h, size_t* bytes) {
+    if (!h || !bytes) { set_error("lattice_state_size: NULL argument"); return LPC_ERR_INVALID; }
+    *bytes = state_bytes(h);
+    return LPC_OK;
+}
+
+lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
+    if (!h || !buf) { set_error("lattice_get_state: NULL argument"); return LPC_ERR_INVALID; }
+    if (bytes < state_bytes(h)) { set_error("lattice_get_state: buffer too small"); return LPC_ERR_INVALID; }
+    char* p = (char*)buf;
+    StateHeader hd;
+    memcpy(hd.magic, "LPC3DST1", 8);
+    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.nz = h->p.nz; hd.msd_axes = h->p.msd_axes; hd.steps = h->steps;
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    const size_t N = (size_t)h->N;
+    lpc_status s = read_field(h, h->rho[h->cur], 4, p, 0, "lattice_get_state");
+    if (s != LPC_OK) return s;
+    p += N * 4;
+    s = read_field(h, h->m[h->cur], 8, p, 0, "lattice_get_state");
+    if (s != LPC_OK) return s;
+    p += N * 8;
+    for (int a = 0; a < 3; ++a) {
+        if (!(h->p.msd_axes >> a & 1)) continue;
+        s = read_field(h, h->mu[h->cur][a], 4, p, 0, "lattice_get_state");
+        if (s != LPC_OK) return s;
+        p += N * 4;
+    }
+    const size_t S = (size_t)h->steps;
+    cudaError_t e = cudaMemcpy(p, h->histM, (S + 1) * 16, cudaMemcpyDeviceToHost);
+    p += (S + 1) * 16;
+    if (e == cudaSuccess) e = cudaMemcpy(p, h->histP, (S + 1) * 8, cudaMemcpyDeviceToHost);
+    p += (S + 1) * 8;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        if (!(h->p.msd_axes >> a & 1)) continue;
+        if (S > 0) e = cudaMemcpy(p, h->histD + a * h->cap, S * 8, cudaMemcpyDeviceToHost);
+        p += S * 8;
+    }
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_get_state");
+}
+
+lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
+    if (!h || !buf) { set_error("lattice_set_state: NULL argument"); return LPC_ERR_INVALID; }
+    if (bytes < sizeof(StateHeader)) { set_error("lattice_set_state: buffer too small"); return LPC_ERR_INVALID; }
+    StateHeader hd;
+    memcpy(&hd, buf, sizeof hd);
+    if (memcmp(hd.magic, "LPC3DST1", 8) != 0 || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz ||
+        hd.msd_axes != h->p.msd_axes || hd.steps < 0) {
+        set_error("lattice_set_state: blob does not match this lattice");
+        return LPC_ERR_INVALID;
+    }
+    const long long old_steps = h->steps;
+    h->steps = hd.steps;
+    const size_t need = state_bytes(h);
+    h->steps = old_steps;
+    if (bytes < need) { set_error("lattice_set_state: truncated blob"); return LPC_ERR_INVALID; }
+    Entry en(h);
+    lpc_status st = ensure_history(h, hd.steps + 1);
+    if (st != LPC_OK) return st;
+    const char* p = (const char*)buf + sizeof hd;
+    const size_t N = (size_t)h->N;
+    void* tmp = dalloc(h, N * 8);
+    if (!tmp) { set_error("lattice_set_state: temporary allocation failed"); return LPC_ERR_OOM; }
+    LatticeView v = make_view(h, h->cur);
+    cudaError_t e = cudaMemcpyAsync(tmp, p, N * 4, cudaMemcpyHostToDevice, h->wstream);
+    if (e == cudaSuccess) e = launch_pad(tmp, 4, v, h->rho[h->cur], h->wstream);
+    p += N * 4;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, p, N * 8, cudaMemcpyHostToDevice, h->wstream);
+    if (e == cudaSuccess) e = launch_pad(tmp, 8, v, h->m[h->cur], h->wstream);
+    p += N * 8;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        if (!(h->p.msd_axes >> a & 1)) continue;
+        e = cudaStreamSynchronize(h->wstream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, p, N * 4, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess) e = launch_pad(tmp, 4, v, h->mu[h->cur][a], h->wstream);
+        p += N * 4;
+    }
+    const size_t S = (size_t)hd.steps;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->histM, p, (S + 1) * 16, cudaMemcpyHostToDevice, h->wstream);
+    p += (S + 1) * 16;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->histP, p, (S + 1) * 8, cudaMemcpyHostToDevice, h->wstream);
+    p += (S + 1) * 8;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        if (!(h->p.msd_axes >> a & 1)) continue;
+        if (S > 0) e = cudaMemcpyAsync(h->histD + a * h->cap, p, S * 8, cudaMemcpyHostToDevice, h->wstream);
+        p += S * 8;
+    }
+    const long long dstep = hd.steps;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &dstep, 8, cudaMemcpyHostToDevice, h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    dfree(h, tmp, N * 8);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_set_state");
+    h->steps = hd.steps;
+    return LPC_OK;
+}
+
+lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_iter, int32_t check_every,
+                               int64_t* iters, double* max_diff) {
+    if (!h) { set_error("lattice_equilibrate: NULL handle"); return LPC_ERR_INVALID; }
+    if (!(threshold >= 0.0) || max_iter < 0 || check_every < 1) { set_error("lattice_equilibrate: bad arguments"); return LPC_ERR_INVALID; }
+    if (h->steps != 0) { set_error("lattice_equilibrate: only before the propagation phase (steps_done must be 0)"); return LPC_ERR_STATE; }
+    Entry en(h);
+    lpc_status st = ensure_history(h, (long long)check_every + 2);
+    if (st != LPC_OK) return st;
+    long long done = 0;
+    double diff = INFINITY;
+    cudaError_t e = cudaSuccess;
+    while (done < max_iter) {
+        const long long chunk = (max_iter - done) < check_every ? (max_iter - done) : check_every;
+        const long long zero = 0;
+        e = cudaMemcpyAsync(h->dstep, &zero, 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e != cudaSuccess) break;
+        for (long long i = 0; i < chunk && st == LPC_OK; ++i) st = launch_one(h, h->wstream);
+        if (st != LPC_OK) return st;
+        done += chunk;
+        e = launch_maxdiff(h->rho[h->cur], h->rho[h->cur ^ 1], make_view(h, h->cur), h->scratch, h->wstream);
+        unsigned int bits = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, h->scratch, 4, cudaMemcpyDeviceToHost, h->wstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+        if (e != cudaSuccess) break;
+        float f;
+        memcpy(&f, &bits, 4);
+        diff = f;
+        if (diff < threshold) break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
+    // restart the propagation phase from the equilibrated populations
+    LatticeView v = make_view(h, h->cur ^ 1);   // out buffers = current
+    const long long minus_one = -1;
+    e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
+    if (e == cudaSuccess) {
+        // m = rho, mu = 0: reuse the init kernel with rho0 taken from the state
+        float* tmp = (float*)dalloc(h, (size_t)h->N * 4);
+        double* tmpd = (double*)dalloc(h, (size_t)h->N * 8);
+        if (!tmp || !tmpd) { dfree(h, tmp, (size_t)h->N * 4); dfree(h, tmpd, (size_t)h->N * 8); set_error("lattice_equilibrate: temporary allocation failed"); return LPC_ERR_OOM; }
+        e = launch_unpad(h->rho[h->cur], 4, make_view(h, h->cur), tmp, h->wstream);
+        std::vector<float> hf;
+        if (e == cudaSuccess) {
+            hf.resize((size_t)h->N);
+            e = cudaMemcpyAsync(hf.data(), tmp, (size_t)h->N * 4, cudaMemcpyDeviceToHost, h->wstream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+        }
+        std::vector<double> hd(hf.begin(), hf.end());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmpd, hd.data(), (size_t)h->N * 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess) e = launch_init_state(v, tmpd, LPC_INIT_UNIFORM, nullptr, h->solid, h->p.kT, h->scratch, h->wstream);
+        if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+        dfree(h, tmp, (size_t)h->N * 4);
+        dfree(h, tmpd, (size_t)h->N * 8);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
+    if (iters) *iters = done;
+    if (max_diff) *max_diff = diff;
+    return LPC_OK;
+}
+
+}  // extern "C"

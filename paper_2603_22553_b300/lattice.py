@@ -1,0 +1,217 @@
+"""Python handle around one device-resident lattice (C ABI ``lattice_*``).
+
+PyTorch supplies device memory (its caching allocator, through the
+``lpc_allocator`` hooks) and the CUDA stream; all lattice arithmetic runs in
+the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import binding as B
+
+
+class TorchAllocator:
+    """``lpc_allocator`` backed by PyTorch's CUDA caching allocator."""
+
+    def __init__(self, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                              int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._alloc_cb = B.ALLOC_FN(_alloc)
+        self._free_cb = B.FREE_FN(_free)
+        self.struct = B.lpc_allocator(self._alloc_cb, self._free_cb, None)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Lattice:
+    """A lattice on the GPU: create, step, query, checkpoint, destroy."""
+
+    def __init__(self, nx, ny, nz, F, omega, solid, *, periodic=(1, 1, 1), alpha=0.005,
+                 dt=5e-6, kT=1.0, rho0=None, weight_dtype=0, msd_axes=0, init=0, ghost=0,
+                 stream=None, allocator="torch"):
+        self.lib = B.load()
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.msd_axes = msd_axes
+        self.dt = dt
+        p = B.lpc_params(nx, ny, nz, (ctypes.c_int32 * 3)(*[int(v) for v in periodic]),
+                         float(alpha), float(dt), float(kT), int(weight_dtype), int(msd_axes),
+                         int(init), int(ghost))
+        F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+        om = np.ascontiguousarray(omega, dtype=np.float64).reshape(-1)
+        sol = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        if F.size != self.N or om.size != self.N or sol.size != self.N:
+            raise ValueError("field sizes do not match the lattice")
+        r0 = None
+        if rho0 is not None:
+            r0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
+            if r0.size != self.N:
+                raise ValueError("rho0 size does not match the lattice")
+        self._alloc = None
+        aptr = None
+        if allocator == "torch":
+            self._alloc = TorchAllocator()
+            aptr = ctypes.byref(self._alloc.struct)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        h = ctypes.c_void_p()
+        st = self.lib.lattice_create(ctypes.byref(p), _dp(F), _dp(om),
+                                     sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                     _dp(r0) if r0 is not None else None, aptr,
+                                     ctypes.c_void_p(self.stream), ctypes.byref(h))
+        B.check(st, self.lib)
+        self.h = h
+
+    @classmethod
+    def from_input(cls, inp, **kw):
+        """Create from an ``lpc_inputs.LatticeInput``."""
+        args = dict(periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
+                    rho0=inp.rho0, weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes)
+        args.update(kw)
+        return cls(inp.nx, inp.ny, inp.nz, inp.F, inp.omega, inp.solid, **args)
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lattice_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping --------------------------------------------------------------
+    def step(self, n):
+        B.check(self.lib.lattice_step_n(self.h, int(n)), self.lib)
+
+    def set_schedule(self, kernel, block_steps=1):
+        B.check(self.lib.lattice_set_schedule(self.h, int(kernel), int(block_steps)), self.lib)
+
+    def sync(self):
+        B.check(self.lib.lattice_sync(self.h), self.lib)
+
+    @property
+    def steps_done(self):
+        n = ctypes.c_int64()
+        B.check(self.lib.lattice_steps_done(self.h, ctypes.byref(n)), self.lib)
+        return n.value
+
+    def info(self):
+        i = B.lpc_info()
+        B.check(self.lib.lattice_info(self.h, ctypes.byref(i)), self.lib)
+        return {f: getattr(i, f) for f, _ in B.lpc_info._fields_}
+
+    def equilibrate(self, threshold, max_iter, check_every=100):
+        it = ctypes.c_int64()
+        d = ctypes.c_double()
+        B.check(self.lib.lattice_equilibrate(self.h, float(threshold), int(max_iter),
+                                             int(check_every), ctypes.byref(it), ctypes.byref(d)),
+                self.lib)
+        return it.value, d.value
+
+    # -- histories -------------------------------------------------------------
+    def fid(self, first=0, count=None):
+        """M(n) for n in [first, first+count) as complex128."""
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(2 * count)
+        B.check(self.lib.lattice_fid(self.h, int(first), int(count), _dp(out)), self.lib)
+        return out[0::2] + 1j * out[1::2]
+
+    def population(self, first=0, count=None):
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(count)
+        B.check(self.lib.lattice_population(self.h, int(first), int(count), _dp(out)), self.lib)
+        return out
+
+    def msd(self, axis, first=0, count=None):
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(count)
+        B.check(self.lib.lattice_msd(self.h, int(axis), int(first), int(count), _dp(out)), self.lib)
+        return out
+
+    # -- fields ----------------------------------------------------------------
+    def density(self):
+        out = np.empty(self.N, np.float32)
+        B.check(self.lib.lattice_density(self.h, out.ctypes.data_as(ctypes.c_void_p), 0), self.lib)
+        return out.reshape(self.shape)
+
+    def density_device(self):
+        """Densities as a torch CUDA tensor (copied on the lattice's stream)."""
+        import torch
+        t = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        B.check(self.lib.lattice_density(self.h, ctypes.c_void_p(t.data_ptr()), 1), self.lib)
+        return t
+
+    def magnetization(self):
+        out = np.empty(2 * self.N, np.float32)
+        B.check(self.lib.lattice_magnetization(self.h, out.ctypes.data_as(ctypes.c_void_p), 0),
+                self.lib)
+        return (out[0::2].astype(np.float64) + 1j * out[1::2]).reshape(self.shape)
+
+    def moment(self, axis):
+        out = np.empty(self.N, np.float32)
+        B.check(self.lib.lattice_moment(self.h, int(axis), out.ctypes.data_as(ctypes.c_void_p), 0),
+                self.lib)
+        return out.reshape(self.shape)
+
+    def weights(self):
+        """Stored hop weights widened to float: shape (6, nz, ny, nx)."""
+        out = np.empty(6 * self.N, np.float32)
+        B.check(self.lib.lattice_weights(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                self.lib)
+        return out.reshape((6,) + self.shape)
+
+    def rotation(self):
+        out = np.empty(2 * self.N, np.float32)
+        B.check(self.lib.lattice_rotation(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                self.lib)
+        return out.reshape(self.shape + (2,))
+
+    def solid_mask(self):
+        out = np.empty(self.N, np.uint8)
+        B.check(self.lib.lattice_solid(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+                self.lib)
+        return out.reshape(self.shape)
+
+    # -- checkpoint ------------------------------------------------------------
+    def get_state(self):
+        n = ctypes.c_size_t()
+        B.check(self.lib.lattice_state_size(self.h, ctypes.byref(n)), self.lib)
+        buf = ctypes.create_string_buffer(n.value)
+        B.check(self.lib.lattice_get_state(self.h, buf, n.value), self.lib)
+        return bytes(buf.raw)
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        B.check(self.lib.lattice_set_state(self.h, buf, len(blob)), self.lib)

@@ -1,0 +1,110 @@
+"""CPU checks of the C ABI: the in-tree library loads, exports every function
+that include/*.h declares, and rejects invalid arguments on the host before
+any device work (no GPU needed for these calls)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2603_22553_b300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b([a-z][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            name = m.group(1)
+            if name.startswith(("lattice_", "lpc_")):
+                names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_22553_b300 import build
+    build.build_library()
+    return B.load()
+
+
+def test_header_declares_the_north_star_calls():
+    names = declared_functions()
+    for n in ("lattice_create", "lattice_step_n", "lattice_fid", "lattice_density",
+              "lattice_msd", "lattice_destroy", "lpc_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(B.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), "missing export: " + n
+        assert n in B.SIGNATURES, "binding lacks " + n
+
+
+def test_version_and_error_string(lib):
+    assert b"sm_103a" in lib.lpc_version()
+    assert isinstance(lib.lpc_last_error(), bytes)
+
+
+def _params(**kw):
+    d = dict(nx=4, ny=4, nz=4, periodic=(1, 1, 1), alpha=0.5, dt=5e-6, kT=1.0, weight_dtype=0,
+             msd_axes=0, init=0, ghost=0)
+    d.update(kw)
+    per = (ctypes.c_int32 * 3)(*d.pop("periodic"))
+    return B.lpc_params(d["nx"], d["ny"], d["nz"], per, d["alpha"], d["dt"], d["kT"],
+                        d["weight_dtype"], d["msd_axes"], d["init"], d["ghost"])
+
+
+def _create(lib, p, F=None, om=None, solid=None, rho0=None):
+    N = p.nx * p.ny * p.nz if p.nx > 0 and p.ny > 0 and p.nz > 0 else 1
+    F = np.zeros(N) if F is None else F
+    om = np.zeros(N) if om is None else om
+    solid = np.zeros(N, np.uint8) if solid is None else solid
+    h = ctypes.c_void_p()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.lattice_create(ctypes.byref(p), dp(F), dp(om),
+                            solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                            dp(rho0) if rho0 is not None else None, None, None, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(nx=0), "edges"), (dict(alpha=0.0), "alpha"), (dict(alpha=1.5), "alpha"),
+    (dict(kT=0.0), "kT"), (dict(weight_dtype=3), "weight_dtype"), (dict(msd_axes=9), "msd_axes"),
+    (dict(init=7), "init"), (dict(ghost=9), "ghost"), (dict(periodic=(2, 1, 1)), "periodic"),
+])
+def test_invalid_parameters_rejected_on_host(lib, kw, msg):
+    st, h = _create(lib, _params(**kw))
+    assert st == B.LPC_ERR_INVALID
+    assert not h.value
+    assert msg in lib.lpc_last_error().decode()
+
+
+def test_non_finite_inputs_rejected(lib):
+    p = _params()
+    F = np.zeros(64)
+    F[5] = np.nan
+    st, _ = _create(lib, p, F=F)
+    assert st == B.LPC_ERR_INVALID and b"F" in lib.lpc_last_error()
+    # a NaN free energy on a solid site is ignored by validation (solid sites have no F)
+    om = np.zeros(64)
+    om[3] = np.inf
+    st, _ = _create(lib, p, om=om)
+    assert st == B.LPC_ERR_INVALID and b"omega" in lib.lpc_last_error()
+
+
+def test_null_handle_calls(lib):
+    assert lib.lattice_step_n(None, 1) == B.LPC_ERR_INVALID
+    assert lib.lattice_destroy(None) == B.LPC_OK
+    out = np.zeros(2)
+    assert lib.lattice_fid(None, 0, 1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == B.LPC_ERR_INVALID
+    assert lib.lattice_step_many(None, None, -1) == B.LPC_ERR_INVALID
