@@ -248,8 +248,9 @@ def run_ours(args):
     inp = wl["make"]()
     N = inp.n_sites
     sched = parse_schedule(args.schedule)
+    ghost = sched[1] if sched and sched[0] == B.LPC_KERNEL_TB else 0
 
-    lat = Lattice.from_input(inp)
+    lat = Lattice.from_input(inp, ghost=ghost)
     if sched:
         lat.set_schedule(*sched)
     info = lat.info()
@@ -304,7 +305,7 @@ def run_ours(args):
                "sample": "%d^3 periodic corner of the workload fields, %d steps, FP64 (%.1f s)" % (
                    wl["sub"], s, t)}
         # parity of the same sample on the GPU (FID relative L2 vs the exact oracle)
-        g = Lattice.from_input(sub)
+        g = Lattice.from_input(sub, ghost=ghost)
         if sched:
             g.set_schedule(*sched)
         g.step(s)
@@ -328,7 +329,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         lat = Lattice(inp.nx, inp.ny, inp.nz, Fp.numpy(), Op.numpy(), Sp.numpy(),
                       periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
-                      weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes)
+                      weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes, ghost=ghost)
         if sched:
             lat.set_schedule(*sched)
         for _ in range(args.steps):

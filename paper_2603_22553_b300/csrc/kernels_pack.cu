@@ -125,10 +125,18 @@ __global__ void k_init(LatticeView v, const double* __restrict__ rho0, int mode,
             else r = 1.0f;
         }
     }
+    // Both halves of the double buffer get the same values, so that ghost
+    // positions no kernel ever writes (across walls, pitch padding) hold
+    // zeros in either buffer: a zero hop weight times a stale NaN would be NaN.
     v.rho_out[pidx] = r;
     v.m_out[pidx] = make_float2(r, 0.0f);
+    const_cast<float*>(v.rho_in)[pidx] = r;
+    const_cast<float2*>(v.m_in)[pidx] = make_float2(r, 0.0f);
     for (int a = 0; a < 3; ++a)
-        if (v.msd_axes >> a & 1) v.mu_out[a][pidx] = 0.0f;
+        if (v.msd_axes >> a & 1) {
+            v.mu_out[a][pidx] = 0.0f;
+            const_cast<float*>(v.mu_in[a])[pidx] = 0.0f;
+        }
 }
 
 // Sums of the current state (M, P) into history entry *step + 1, using the

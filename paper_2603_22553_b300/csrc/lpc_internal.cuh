@@ -152,21 +152,19 @@ __device__ __forceinline__ void store_images(T* base, const LatticeView& v, int 
             base[zoff + (long long)py * v.Xp + px] = val;
 }
 
-// Block reduction of per-warp FP64 accumulators, partial store and the
-// final fixed-order reduction by the last block to finish.  `acc` holds the
-// warp's sums in lane 0.  Writes the history entry for `levels` consecutive
-// steps starting at *v.step.
+// Final reduction of per-warp FP64 sums held in shared memory as
+// smem[(level * NW + warp) * kNumSums + q]: each block combines its warps in
+// a fixed order into per-block partials, and the last block to finish sums
+// the partials in a fixed order (lanes stride over blocks, then an FP64
+// butterfly) and writes the history entries of `levels` consecutive steps
+// starting at *v.step.
 template <int NW>
-__device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int levels,
-                             double* smem /* NW*kNumSums*levels */) {
+__device__ void block_finish_smem(const LatticeView& v, int levels, double* smem) {
+    __syncthreads();
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (lane == 0)
-        for (int l = 0; l < levels; ++l)
-            for (int q = 0; q < kNumSums; ++q) smem[(l * NW + warp) * kNumSums + q] = acc[l][q];
-    __syncthreads();
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid < levels * kNumSums) {
         const int l = tid / kNumSums, q = tid % kNumSums;
@@ -181,7 +179,6 @@ __device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // one warp per (level, quantity): lanes stride over blocks, then butterfly
     const long long n0 = *v.step;
     for (int job = warp; job < levels * kNumSums; job += NW) {
         const int l = job / kNumSums, q = job % kNumSums;
@@ -201,6 +198,18 @@ __device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int 
         *v.step = n0 + levels;
         *v.counter = 0u;
     }
+}
+
+// Same, starting from per-warp sums in registers (lane 0 of every warp).
+template <int NW>
+__device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int levels,
+                             double* smem /* NW*kNumSums*levels */) {
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int l = 0; l < levels; ++l)
+            for (int q = 0; q < kNumSums; ++q) smem[(l * NW + warp) * kNumSums + q] = acc[l][q];
+    block_finish_smem<NW>(v, levels, smem);
 }
 
 // Host side --------------------------------------------------------------------
@@ -230,5 +239,18 @@ cudaError_t launch_pad(const void* src_dev, int elem_bytes, const LatticeView& v
 cudaError_t launch_weights_f32(const LatticeView& v, int wdtype, float* dst_dev, cudaStream_t st);
 cudaError_t launch_maxdiff(const float* a, const float* b, const LatticeView& v, double* out2,
                            cudaStream_t st);
+
+// Temporally blocked kernel (K steps per launch, TMA-staged planes).
+struct TBMaps;
+bool tb_supported(const LatticeView& v, int wdtype, int K);
+cudaError_t tb_prepare(int wdtype, int K, int msd);
+bool tb_encode_maps(const LatticeView& v, int wdtype, int H, TBMaps* maps);
+int tb_box_rows(const LatticeView& v, int wdtype, int K);
+cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
+                      cudaStream_t st);
+int tb_grid(const LatticeView& v, int wdtype, int K);
+size_t tb_maps_size();
+TBMaps* tb_maps_new();
+void tb_maps_delete(TBMaps* m);
 
 }  // namespace lpc

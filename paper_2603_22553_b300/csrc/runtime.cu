@@ -75,6 +75,8 @@ struct lpc_lattice {
     long long steps = 0;
     int kernel = LPC_KERNEL_STEP1;
     int kdepth = 1;
+    TBMaps* maps[2] = {nullptr, nullptr};   // TMA tensor maps per input parity
+    int maps_K = 0;
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -175,11 +177,48 @@ lpc_status ensure_history(lpc_lattice* h, long long needed) {
     return LPC_OK;
 }
 
-lpc_status launch_one(lpc_lattice* h, cudaStream_t st) {
+lpc_status ensure_maps(lpc_lattice* h) {
+    if (h->maps[0] && h->maps_K == h->kdepth) return LPC_OK;
+    for (int par = 0; par < 2; ++par) {
+        if (!h->maps[par]) h->maps[par] = tb_maps_new();
+        if (!h->maps[par]) { set_error("tensor map allocation failed"); return LPC_ERR_OOM; }
+        LatticeView v = make_view(h, par);
+        const int H = tb_box_rows(v, h->p.weight_dtype, h->kdepth);
+        if (H <= 0 || !tb_encode_maps(v, h->p.weight_dtype, H, h->maps[par])) {
+            set_error("TMA tensor map encoding failed");
+            return LPC_ERR_CUDA;
+        }
+    }
+    h->maps_K = h->kdepth;
+    return LPC_OK;
+}
+
+// One launch: a TB block of kdepth steps (tb = true) or one step.
+lpc_status launch_one(lpc_lattice* h, cudaStream_t st, bool tb = false) {
     LatticeView v = make_view(h, h->cur);
-    cudaError_t e = launch_step1(v, h->p.weight_dtype, st);
+    cudaError_t e;
+    if (tb) {
+        lpc_status s = ensure_maps(h);
+        if (s != LPC_OK) return s;
+        e = launch_tb(v, h->p.weight_dtype, h->kdepth, *h->maps[h->cur], h->counter + 1, st);
+    } else {
+        e = launch_step1(v, h->p.weight_dtype, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     h->cur ^= 1;
+    return LPC_OK;
+}
+
+// Device error word (set by kernels whose bounded waits ran out).
+lpc_status check_device_error(lpc_lattice* h) {
+    unsigned int err = 0;
+    cudaError_t e = cudaMemcpy(&err, h->counter + 1, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "error word read");
+    if (err != 0) {
+        cudaMemset(h->counter, 0, 8);   // completion counter and error word
+        set_error("a device wait exceeded its time limit (kernel returned early)");
+        return (lpc_status)err;
+    }
     return LPC_OK;
 }
 
@@ -192,7 +231,9 @@ lpc_status build_graph(lpc_lattice* h, int parity) {
     const int save = h->cur;
     h->cur = parity;
     lpc_status st = LPC_OK;
-    for (int i = 0; i < kGraphLen && st == LPC_OK; ++i) st = launch_one(h, h->wstream);
+    const bool tb = h->kernel == LPC_KERNEL_TB;
+    if (tb) st = ensure_maps(h);
+    for (int i = 0; i < kGraphLen && st == LPC_OK; ++i) st = launch_one(h, h->wstream, tb);
     h->cur = save;
     e = cudaStreamEndCapture(h->wstream, &g);
     if (st != LPC_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -227,6 +268,7 @@ void release_all(lpc_lattice* h) {
     dfree(h, h->counter, 256);
     dfree(h, h->scratch, 8 * 1024);
     if (h->ustream) cudaStreamSynchronize(h->ustream);
+    for (int i = 0; i < 2; ++i) if (h->maps[i]) tb_maps_delete(h->maps[i]);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->wstream) cudaStreamDestroy(h->wstream);
@@ -355,8 +397,21 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
         drop_graphs(h);
         return LPC_OK;
     }
-    set_error("lattice_set_schedule: kernel not available in this build");
-    (void)block_steps;
+    if (kernel == LPC_KERNEL_TB) {
+        cudaSetDevice(h->device);
+        if (!tb_supported(make_view(h, 0), h->p.weight_dtype, block_steps) ||
+            tb_box_rows(make_view(h, 0), h->p.weight_dtype, block_steps) <= 0) {
+            set_error("lattice_set_schedule: TB needs 1 <= block_steps <= min(4, ghost)");
+            return LPC_ERR_INVALID;
+        }
+        cudaError_t e = tb_prepare(h->p.weight_dtype, block_steps, h->p.msd_axes);
+        if (e != cudaSuccess) return cuda_fail(e, "lattice_set_schedule");
+        h->kernel = LPC_KERNEL_TB;
+        h->kdepth = block_steps;
+        drop_graphs(h);
+        return LPC_OK;
+    }
+    set_error("lattice_set_schedule: unknown kernel");
     return LPC_ERR_INVALID;
 }
 
@@ -367,20 +422,26 @@ lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
     Entry en(h);
     lpc_status st = ensure_history(h, h->steps + n + 1);
     if (st != LPC_OK) return st;
-    long long left = n;
-    while (left >= kGraphLen) {
+    const bool tb = h->kernel == LPC_KERNEL_TB;
+    const long long per = tb ? h->kdepth : 1;     // steps per launch
+    long long launches = n / per;
+    long long rest = n % per;                    // remainder: one-step launches
+    while (launches >= kGraphLen) {
         if (!h->graph[h->cur]) {
             st = build_graph(h, h->cur);
             if (st != LPC_OK) return st;
         }
         cudaError_t e = cudaGraphLaunch(h->graph[h->cur], h->wstream);
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-        left -= kGraphLen;     // kGraphLen is even: parity unchanged
+        launches -= kGraphLen;     // kGraphLen is even: parity unchanged
     }
-    while (left > 0) {
-        st = launch_one(h, h->wstream);
+    for (; launches > 0; --launches) {
+        st = launch_one(h, h->wstream, tb);
         if (st != LPC_OK) return st;
-        --left;
+    }
+    for (; rest > 0; --rest) {
+        st = launch_one(h, h->wstream, false);
+        if (st != LPC_OK) return st;
     }
     h->steps += n;
     return LPC_OK;
@@ -400,7 +461,8 @@ lpc_status lattice_sync(lpc_lattice* h) {
     cudaSetDevice(h->device);
     cudaError_t e = cudaStreamSynchronize(h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->ustream);
-    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_sync");
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_sync");
+    return check_device_error(h);
 }
 
 lpc_status lattice_steps_done(lpc_lattice* h, int64_t* n) {
@@ -440,6 +502,7 @@ lpc_status lattice_fid(lpc_lattice* h, int64_t first, int64_t count, double* out
     if (s != LPC_OK || count == 0) return s;
     cudaSetDevice(h->device);
     cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) { lpc_status ds = check_device_error(h); if (ds != LPC_OK) return ds; }
     if (e == cudaSuccess) e = cudaMemcpy(out, h->histM + first, sizeof(double2) * count, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_fid");
 }
