@@ -504,8 +504,13 @@ cudaError_t tb_prepare(int wdtype, int K, int msd) {
     static bool attr_set[2][5][8] = {};
     bool& done = attr_set[wdtype == LPC_WEIGHTS_BF16][K][msd & 7];
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(tb_kernel(wdtype, K, msd), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         device_props().max_smem_optin);
+    void* fn = tb_kernel(wdtype, K, msd);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    // the opt-in limit covers static + dynamic shared memory
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             device_props().max_smem_optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done = true;
     return e;
 }
