@@ -235,6 +235,35 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes);
 lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_iter,
                                int32_t check_every, int64_t* iters, double* max_diff);
 
+/*
+ * One time step that allocates no device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory where they advance the lattice (host codes whose device
+ * memory is reserved once through their own pool, plain C hosts without
+ * allocator hooks).  The caller owns every buffer; all are device memory in
+ * plain C order [z][y][x] (no ghost padding), N = nx*ny*nz:
+ *   w        [6][N] float: packed out-weights w_k (k = +x, -x, +y, -y, +z,
+ *            -z), zero across walls, as lattice_weights returns them.
+ *   R        [N] (re, im) float pairs: rotation factors (lattice_rotation).
+ *   rho_in / m_in    state at step n (m as (re, im) float pairs).
+ *   rho_out / m_out  state at step n+1; must not alias the inputs.
+ *   sums     3 doubles written with M(n+1) re, M(n+1) im, P(n+1).
+ *   periodic[3]      1 = periodic, 0 = wall, per axis.
+ *   stream   cudaStream_t (NULL = default stream); the call is asynchronous.
+ * The result equals lattice_step_n by one step (same per-site arithmetic).
+ * Scratch: per-plane partial sums and a completion counter in a fixed
+ * device array of this library (about 98 KB, held by every GPU that loads
+ * the library until exit); hence nz <= 4096, and larger nz is rejected with
+ * LPC_ERR_INVALID.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress), so make a first call before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race and
+ * give wrong sums, so order them.  No MSD moments.  Errors: LPC_ERR_INVALID
+ * (sizes, NULL or aliased buffers), LPC_ERR_CUDA.
+ */
+lpc_status lpc_step_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* periodic,
+                            const float* w, const float* R, const float* rho_in, const float* m_in,
+                            float* rho_out, float* m_out, double* sums, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lpc_last_error(void);
 

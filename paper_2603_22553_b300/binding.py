@@ -78,6 +78,8 @@ SIGNATURES = {
     "lattice_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
     "lattice_equilibrate": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                                            _I64P, _DP]),
+    "lpc_step_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)] + [ctypes.c_void_p] * 8),
     "lpc_last_error": (ctypes.c_char_p, []),
     "lpc_version": (ctypes.c_char_p, []),
 }
