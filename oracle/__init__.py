@@ -53,7 +53,14 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_SO)
+        _lib = _bind(_SO)
+    return _lib
+
+
+def _bind(path):
+    """Load a compiled oracle library from ``path`` and declare its signatures."""
+    if True:
+        lib = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         u8p = ctypes.POINTER(ctypes.c_uint8)
         ip = ctypes.POINTER(ctypes.c_int)
@@ -71,8 +78,7 @@ def _load():
         lib.or_round_bf16.argtypes = [ctypes.c_double]
         lib.or_round_bf16.restype = ctypes.c_double
         lib.or_max_threads.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+    return lib
 
 
 def _dp(a):

@@ -1,0 +1,86 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a temporary copy of the C oracle (a dropped
+term, a wrong sign or index, a transposed operand), builds it, binds it in
+place of the real oracle and runs the pin tests of test_oracle_pins.py
+against it: at least one pin must fail.  The real oracle is untouched.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lpc_oracle.c")
+
+MUTATIONS = {
+    "stay term ignores the out-flow": ("s[i] = 1.0 - out;", "s[i] = 1.0;"),
+    "Metropolis exponent sign": ("(dE > 0.0) ? exp(-dE) : 1.0", "(dE > 0.0) ? exp(dE) : 1.0"),
+    "gather from the wrong side": ("neighbour(x, y, z, k ^ 1, nx, ny, nz, periodic)",
+                                   "neighbour(x, y, z, k, nx, ny, nz, periodic)"),
+    "conjugated rotation": ("m2[2 * i + 1] = c * mi + sn * mr;", "m2[2 * i + 1] = c * mi - sn * mr;"),
+    "attempt factor 1/3": ("alpha / 6.0", "alpha / 3.0"),
+    "displacement sign": ("double d = (k & 1) ? -1.0 : 1.0;", "double d = (k & 1) ? 1.0 : -1.0;"),
+    "dMSD drift term sign": ("2.0 * (wp - wm)", "2.0 * (wp + wm)"),
+    "walls treated as periodic": ("if (!periodic[a]) return -1;", "if (0) return -1;"),
+    "transposed site index": ("return ((int64_t)z * ny + y) * nx + x;", "return ((int64_t)z * nx + x) * ny + y;"),
+    "FID sums rho": ("sr += m[2 * i];", "sr += rho[i];"),
+    "solid target accepted": ("if (j >= 0 && !solid[i] && !solid[j])", "if (j >= 0 && !solid[i])"),
+    "temperature dropped": ("double dE = (F[j] - F[i]) / kT;", "double dE = (F[j] - F[i]);"),
+    "moment hop without rho": ("ua[a] += wk * (mu[a * N + j] + (a == axis ? d * rho[j] : 0.0));",
+                               "ua[a] += wk * mu[a * N + j];"),
+}
+
+
+def _pin_calls():
+    """(name, callable) for every pin, with its parametrisations expanded."""
+    calls = [
+        ("detailed balance", lambda: [pins.test_weights_detailed_balance_and_walls(p)
+                                      for p in [(1, 1, 1), (0, 1, 1), (1, 0, 0)]]),
+        ("conservation", lambda: [pins.test_conservation(p) for p in [(1, 1, 1), (0, 1, 0)]]),
+        ("boltzmann stationary", lambda: [pins.test_boltzmann_start_is_stationary(p)
+                                          for p in [(1, 1, 1), (1, 0, 1)]]),
+        ("boltzmann at kT", lambda: [pins.test_boltzmann_stationary_at_temperature(t) for t in (0.7, 2.5)]),
+        ("uniform closed form", lambda: [pins.test_uniform_closed_form(a) for a in (0.3, 1.0)]),
+        ("omega zero", pins.test_zero_omega_gives_m_equal_rho),
+        ("single line", pins.test_uniform_omega_single_spectral_line),
+        ("dense matrix", lambda: [pins.test_dense_matrix_power(p, s) for p, s in
+                                  [((1, 1, 1), 41), ((0, 1, 1), 42), ((1, 1, 0), 43)]]),
+        ("chain brute force", pins.test_msd_chain_with_walls_bruteforce),
+        ("3d brute force", lambda: [pins.test_msd_3d_bruteforce(p) for p in [(1, 1, 1), (0, 1, 0)]]),
+        ("one-step MSD", pins.test_one_step_msd_eq5),
+        ("Kohn", lambda: [pins.test_kohn_identity_eq4(a) for a in (0, 2)]),
+    ]
+    return calls
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation anchor not found: " + old
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-ffp-contract=off", "-o", str(so), str(path), "-lm"])
+    return str(so)
+
+
+def test_real_oracle_passes_all_pins():
+    for name, fn in _pin_calls():
+        fn()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_each_mutation_fails_a_pin(name, tmp_path, monkeypatch):
+    old, new = MUTATIONS[name]
+    so = _build_mutant(tmp_path, old, new)
+    monkeypatch.setattr(oracle, "_lib", oracle._bind(so))
+    failed = []
+    for pin, fn in _pin_calls():
+        try:
+            fn()
+        except (AssertionError, ValueError, FloatingPointError):
+            failed.append(pin)
+    assert failed, "no pin caught the mutation: " + name

@@ -112,6 +112,20 @@ def test_boltzmann_start_is_stationary(periodic):
     assert rho_eq[inp.solid == 0].mean() == pytest.approx(1.0, rel=1e-13)
 
 
+@pytest.mark.parametrize("kT", [0.7, 2.5])
+def test_boltzmann_stationary_at_temperature(kT):
+    """Eq. 1-2 with kT != 1: rho ∝ exp(-F/kT) is stationary, exp(-F) is not."""
+    inp = lpc_inputs.random_case((5, 6, 7), 25, periodic=(1, 1, 0), F_sd=1.0, alpha=0.9)
+    inp.kT = kT
+    pk = oracle.pack_input(inp)
+    rho_eq = oracle.boltzmann(inp.F, inp.solid, kT=kT)
+    r = oracle.run(pk, rho_eq, 1, msd_axes=0)
+    assert np.max(np.abs(r.rho - rho_eq)) <= 1e-14 * rho_eq.max()
+    wrong = oracle.boltzmann(inp.F, inp.solid, kT=1.0)
+    r2 = oracle.run(pk, wrong, 1, msd_axes=0)
+    assert np.max(np.abs(r2.rho - wrong)) > 1e-6 * wrong.max()
+
+
 def test_boltzmann_eq2_against_direct_formula():
     inp = lpc_inputs.random_case((3, 4, 5), 23)
     rho = oracle.boltzmann(inp.F, inp.solid, kT=1.0, mean_rho=2.0)
