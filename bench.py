@@ -55,12 +55,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS) + ["serving_stream"])
     ap.add_argument("--block", type=int, default=64, help="lattice steps per bench step")
     ap.add_argument("--schedule", default="auto", help="auto | step1 | tb:K")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-step-scale", type=float, default=0.25)
+    ap.add_argument("--serve-slots", type=int, default=48)
+    ap.add_argument("--serve-quantum", type=int, default=250)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -248,7 +253,7 @@ def run_ours(args):
     inp = wl["make"]()
     N = inp.n_sites
     sched = parse_schedule(args.schedule)
-    ghost = sched[1] if sched and sched[0] == B.LPC_KERNEL_TB else 0
+    ghost = (sched[1] + 1) // 2 * 2 if sched and sched[0] == B.LPC_KERNEL_TB else 0
 
     lat = Lattice.from_input(inp, ghost=ghost)
     if sched:
@@ -375,10 +380,65 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    """Served stream: continuous batching vs one-at-a-time plain solves.
+
+    The request stream is the 1000-request recipe (edges log-uniform in
+    [24, 192], steps uniform in [1000, 20000], Poisson arrivals at 50/s),
+    truncated to ``--serve-requests`` requests with step counts scaled by
+    ``--serve-step-scale`` so that both passes fit in a few minutes.  Fields
+    are generated before the timed passes.
+    """
+    import torch
+
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.serve import GpuEngine, Server, serve_sequential, summary
+
+    torch.cuda.set_device(0)
+    B.load()
+    reqs = lpc_inputs.request_stream()[:args.serve_requests]
+    for r in reqs:
+        r.steps = max(10, int(round(r.steps * args.serve_step_scale)))
+    cache = {r.rid: r.lattice() for r in reqs}
+
+    class CachedEngine(GpuEngine):
+        def create(self, req):
+            inp = cache[req.rid]
+            with self.torch.cuda.stream(self.create_stream):
+                return self.L.Lattice.from_input(inp, stream=self.create_stream.cuda_stream)
+
+    eng = CachedEngine(keep_fid=True)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    warm = [lpc_inputs.Request(10 ** 6 + i, 0.0, 24, 20, 7) for i in range(2)]
+    for w in warm:
+        cache[w.rid] = w.lattice()
+    Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(warm)
+    torch.cuda.synchronize()
+    recs = Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(reqs)
+    torch.cuda.synchronize()
+    s_batch = summary(recs)
+    seq = serve_sequential(eng, reqs)
+    s_seq = summary(seq)
+    same = all(np.allclose(a.fid, b.fid, rtol=1e-5, atol=1e-5 * abs(b.fid[0])) for a, b in zip(recs, seq))
+    line = {"metric": "site-updates/s (served aggregate)", "value": s_batch["aggregate_site_updates_per_s"],
+            "unit": "site-updates/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32",
+            "config": {"workload": "serving_stream", "requests": len(reqs),
+                       "step_scale": args.serve_step_scale, "slots": args.serve_slots,
+                       "quantum": args.serve_quantum, "hbm_budget_gb": args.serve_budget_gb},
+            "served": s_batch, "one_at_a_time": s_seq,
+            "speedup_vs_one_at_a_time": s_batch["aggregate_site_updates_per_s"] / s_seq["aggregate_site_updates_per_s"],
+            "fid_same_as_one_at_a_time_1e-5": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving_stream":
+        return run_serving(args)
     return run_ours(args)
 
 

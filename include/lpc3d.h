@@ -86,7 +86,9 @@ typedef struct {
  *   init          initial population when rho0 is NULL: LPC_INIT_UNIFORM
  *                 (1 on pore sites) or LPC_INIT_BOLTZMANN (Eq. 2 with
  *                 mean 1 over pore sites).
- *   ghost         ghost-layer width in x and y (1..8), 0 = automatic; the
+ *   ghost         ghost-layer width in x and y: 0 = automatic (4 when nx and
+ *                 ny >= 48, else 2) or an even width 2..8 (even, so that the
+ *                 two-site vector loads of the step kernels stay aligned); the
  *                 temporally blocked kernel needs ghost >= its block depth.
  */
 typedef struct {
@@ -136,6 +138,14 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
                           const uint8_t* solid, const double* rho0, const lpc_allocator* a,
                           void* stream, lpc_lattice** out);
 
+/*
+ * Device bytes lattice_create would hold for these parameters, plus the
+ * history of `steps` steps and the transient input copies of create (used to
+ * admit requests by HBM footprint).  No device work.  LPC_ERR_INVALID on bad
+ * parameters.
+ */
+lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes);
+
 /* Release every device buffer of the lattice.  NULL-safe. */
 lpc_status lattice_destroy(lpc_lattice* h);
 
@@ -149,16 +159,37 @@ lpc_status lattice_destroy(lpc_lattice* h);
 lpc_status lattice_step_n(lpc_lattice* h, int64_t n);
 
 /*
- * Advance several lattices; lattice i by n[i] steps.  Lattices that share a
- * stream are advanced together in batched launches (one launch covers the
- * tiles of every lattice in the group), so many small lattices fill the
- * GPU.  Each lattice's results are identical to lattice_step_n on it alone.
+ * Advance several lattices (all on one device); lattice i by n[i] steps.
+ * Each step is one batched launch over the work items of up to 48 lattices
+ * (grouped by weight type and MSD mask), so many small lattices fill the
+ * GPU together.  States are bit-identical to lattice_step_n; the per-step
+ * sums agree with it to FP32 rounding and are bit-identical whether a
+ * lattice is advanced alone or with any other lattices.  The launches wait
+ * for the work queued on every lattice's stream; later calls on these
+ * lattices (queries included) are ordered after them.  Work the caller
+ * queues on its own stream is ordered after them only through
+ * lattice_sync or a query.  Errors: LPC_ERR_INVALID (NULL or repeated
+ * handle, negative n, lattices on different devices), LPC_ERR_OOM,
+ * LPC_ERR_CUDA.
  */
 lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count);
 
 /* Choose the step kernel: LPC_KERNEL_AUTO / STEP1 / TB, with TB block
  * depth k (1..ghost).  LPC_ERR_INVALID if the combination is impossible. */
 lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps);
+
+/*
+ * Autotune the step schedule of this lattice (kernel and time-block depth):
+ * times `trial_launches` launches
+ * of every schedule its ghost width allows (one-step kernel; TB with depth
+ * 1..min(4, ghost)) with CUDA events, keeps the fastest and restores the
+ * lattice's state, step counter and history afterwards (results are as if
+ * no trial had run).  kernel / block_steps / rate (nullable) receive the
+ * choice and its site updates per second.  Errors: LPC_ERR_INVALID,
+ * LPC_ERR_OOM (state snapshot), LPC_ERR_CUDA.
+ */
+lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* kernel,
+                            int32_t* block_steps, double* rate);
 
 /* Wait for all queued work of the lattice. */
 lpc_status lattice_sync(lpc_lattice* h);

@@ -58,10 +58,13 @@ SIGNATURES = {
                                       ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
                                       ctypes.POINTER(_H)]),
     "lattice_destroy": (ctypes.c_int, [_H]),
+    "lattice_footprint": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.c_int64, _I64P]),
     "lattice_step_n": (ctypes.c_int, [_H, ctypes.c_int64]),
     "lattice_step_many": (ctypes.c_int, [ctypes.POINTER(_H), _I64P, ctypes.c_int32]),
     "lattice_set_schedule": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
     "lattice_sync": (ctypes.c_int, [_H]),
+    "lattice_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), _DP]),
     "lattice_steps_done": (ctypes.c_int, [_H, _I64P]),
     "lattice_info": (ctypes.c_int, [_H, ctypes.POINTER(lpc_info)]),
     "lattice_fid": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _DP]),

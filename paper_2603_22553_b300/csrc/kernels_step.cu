@@ -1,130 +1,263 @@
-// One time step per launch (the "step1" schedule).
+// One time step per launch (the "step1" schedule) and its batched form.
 //
-// A block of 32 x 8 threads owns a 32 x 8 column of (x, y) sites and walks a
-// chunk of z planes; each thread keeps the state and the hop weights of the
-// planes below, at and above its site in registers, so only the four in-plane
-// neighbours are re-read (from L1/L2).  Blocks loop over (x-tile, y-tile,
-// z-chunk) work items with a grid of SM count x resident blocks.  Every warp
-// reduces its 32-site row of each plane in FP32 (fixed butterfly) and
-// accumulates the row sums in FP64; blocks then combine in FP64 and the last
-// block writes the step's M, P and dMSD into the device history.
+// A block of 32 x 8 threads owns a 32 x 8 tile of (x, y) columns (one site
+// per thread, a warp per row) and walks a chunk of z planes.  Each thread
+// keeps the state and out-weights of the planes below, at and above its
+// site in registers and prefetches ahead: the state and -z weight of the
+// plane two above, the remaining weights and R of the plane above (register
+// sets rotate through a 4-way unrolled loop, so no moves).  x neighbours come
+// from the neighbouring lanes by shuffles (the row's end lanes prefetch the
+// column just outside the row); y neighbours are read from L1 (rows of the
+// same block) or L2.  All offsets are 32-bit (padded lattices hold fewer
+// than 2^31 sites), so a load costs one address operation.  HBM traffic is
+// one read of state, weights and R per site and one write of the state.
+//
+// Blocks loop over (x-tile, y-tile, z-chunk) work items.  Each thread sums
+// its sites of an item in FP32; one warp butterfly per item turns thread
+// sums into FP64 per-warp sums; blocks combine in FP64 and the last block
+// writes the step's M, P and dMSD into the device history.
 #include "lpc_internal.cuh"
 
 namespace lpc {
 
 namespace {
 
-constexpr int BX = 32, BY = 8, NWARP = BX * BY / 32;
+constexpr int BX = 32, BY = 8;             // threads per block: lanes x rows
+constexpr int TX = BX, TY = BY;            // tile 32 x 8 sites
+constexpr int NWARP = BY;
+
+// Per-array base pointers of one launch (weights as 6 plane pointers).
+template <typename WT>
+struct Ptrs {
+    const float* rho;
+    const float2* m;
+    const float* mu[3];
+    const WT* w[6];
+    const float2* R;
+};
+
+template <typename WT>
+__device__ __forceinline__ Ptrs<WT> make_ptrs(const LatticeView& v) {
+    Ptrs<WT> P;
+    P.rho = v.rho_in;
+    P.m = v.m_in;
+    for (int a = 0; a < 3; ++a) P.mu[a] = v.mu_in[a];
+    const WT* W = static_cast<const WT*>(v.w);
+    for (int k = 0; k < 6; ++k) P.w[k] = W + (long long)k * v.Np;
+    P.R = v.R;
+    return P;
+}
+
+// One plane of a thread's column (and, for the row's end lanes, of the column
+// just outside the row: h*).
+template <int MSD>
+struct Pl {
+    float r;
+    float2 m;
+    float w[6];
+    float mu[3];
+    float hr, hw;
+    float2 hm;
+    float hmu[3];
+};
+
+struct Col {
+    int o;                    // padded offset of the site in its plane
+    int lane, x, y;
+    bool load, site;          // thread loads; the site is a lattice site
+    int halo;                 // -1: lane 0 loads x-1, +1: lane 31 loads x+1, 0: none
+};
+
+// early part: state, -z out-weight, end lanes' outside column
+template <typename WT, int MSD>
+__device__ __forceinline__ void load_early(Pl<MSD>& P, const Ptrs<WT>& A, int zo, const Col& c) {
+    if (!c.load) return;
+    const int i = zo + c.o;
+    P.r = __ldg(A.rho + i);
+    P.m = __ldg(A.m + i);
+    P.w[5] = ldw<WT>(A.w[5] + i);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (MSD >> a & 1) P.mu[a] = __ldg(A.mu[a] + i);
+    if (c.halo != 0) {
+        const int j = i + c.halo;
+        P.hr = __ldg(A.rho + j);
+        P.hm = __ldg(A.m + j);
+        P.hw = ldw<WT>((c.halo < 0 ? A.w[0] : A.w[1]) + j);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (MSD >> a & 1) P.hmu[a] = __ldg(A.mu[a] + j);
+    }
+}
+
+// late part: out-weights +x, -x, +y, -y, +z
+template <typename WT, int MSD>
+__device__ __forceinline__ void load_late(Pl<MSD>& P, const Ptrs<WT>& A, int zo, const Col& c) {
+    if (!c.load) return;
+    const int i = zo + c.o;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) P.w[k] = ldw<WT>(A.w[k] + i);
+}
+
+template <int MSD>
+__device__ __forceinline__ void zero_pl(Pl<MSD>& P) {
+    P.r = 0.f;
+    P.m = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P.w[k] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { P.mu[a] = 0.f; P.hmu[a] = 0.f; }
+    P.hr = P.hw = 0.f;
+    P.hm = make_float2(0.f, 0.f);
+}
+
+// Plane z: prefetch (early part of z+2 into pnn, late part and R of z+1),
+// exchange x neighbours, update, store, accumulate.
+template <typename WT, int MSD>
+__device__ __forceinline__ void do_plane(const LatticeView& v, const Ptrs<WT>& A, const Col& c, int z, int z1,
+                                         int plane, const Pl<MSD>& pb, const Pl<MSD>& pc, Pl<MSD>& pn,
+                                         Pl<MSD>& pnn, const float2& Rc, float2& Rn, float* part) {
+    if (z + 1 < z1) {
+        int z2 = z + 2;
+        while (z2 >= v.nz) z2 -= v.nz;
+        const int zn = z + 1 >= v.nz ? z + 1 - v.nz : z + 1;
+        load_early<WT, MSD>(pnn, A, z2 * plane, c);
+        load_late<WT, MSD>(pn, A, zn * plane, c);
+        if (c.load) Rn = __ldg(A.R + zn * plane + c.o);
+    }
+    const unsigned FULL = 0xffffffffu;
+    SiteIn q;
+    // the +x hop into this site comes from x-1 (lane-1), the -x hop from x+1
+    q.r[0] = __shfl_up_sync(FULL, pc.r, 1);
+    q.m[0].x = __shfl_up_sync(FULL, pc.m.x, 1);
+    q.m[0].y = __shfl_up_sync(FULL, pc.m.y, 1);
+    q.win[0] = __shfl_up_sync(FULL, pc.w[0], 1);
+    q.r[1] = __shfl_down_sync(FULL, pc.r, 1);
+    q.m[1].x = __shfl_down_sync(FULL, pc.m.x, 1);
+    q.m[1].y = __shfl_down_sync(FULL, pc.m.y, 1);
+    q.win[1] = __shfl_down_sync(FULL, pc.w[1], 1);
+    float xm_mu[3], xp_mu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (MSD >> a & 1) {
+            xm_mu[a] = __shfl_up_sync(FULL, pc.mu[a], 1);
+            xp_mu[a] = __shfl_down_sync(FULL, pc.mu[a], 1);
+        }
+    if (c.lane == 0) {
+        q.r[0] = pc.hr; q.m[0] = pc.hm; q.win[0] = pc.hw;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (MSD >> a & 1) xm_mu[a] = pc.hmu[a];
+    }
+    if (c.lane == BX - 1) {
+        q.r[1] = pc.hr; q.m[1] = pc.hm; q.win[1] = pc.hw;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (MSD >> a & 1) xp_mu[a] = pc.hmu[a];
+    }
+    if (!c.site) return;
+    const int zo = z * plane;
+    const int i = zo + c.o;
+    // y neighbours: +y hop from y-1, -y hop from y+1 (L1 / L2)
+    q.r[2] = __ldg(A.rho + i - v.Xp);
+    q.m[2] = __ldg(A.m + i - v.Xp);
+    q.win[2] = ldw<WT>(A.w[2] + i - v.Xp);
+    q.r[3] = __ldg(A.rho + i + v.Xp);
+    q.m[3] = __ldg(A.m + i + v.Xp);
+    q.win[3] = ldw<WT>(A.w[3] + i + v.Xp);
+    // z neighbours from the register pipeline
+    q.r[4] = pb.r; q.m[4] = pb.m; q.win[4] = pb.w[4];
+    q.r[5] = pn.r; q.m[5] = pn.m; q.win[5] = pn.w[5];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q.wout[k] = pc.w[k];
+    q.rc = pc.r;
+    q.mc = pc.m;
+    q.R = Rc;
+    const float s = stay_weight(pc.w);
+    float ro;
+    float2 mo;
+    site_rho_m(q, s, ro, mo);
+    const long long zoff = (long long)zo;
+    store_images(v.rho_out, v, c.x, c.y, zoff, ro);
+    store_images(v.m_out, v, c.x, c.y, zoff, mo);
+    part[0] += mo.x;
+    part[1] += mo.y;
+    part[2] += ro;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(MSD >> a & 1)) continue;
+        const float nb[6] = {xm_mu[a], xp_mu[a], __ldg(A.mu[a] + i - v.Xp), __ldg(A.mu[a] + i + v.Xp),
+                             pb.mu[a], pn.mu[a]};
+        const float mo_a = site_mu(q.win, q.r, nb, s, pc.mu[a], a);
+        store_images(v.mu_out[a], v, c.x, c.y, zoff, mo_a);
+        part[3 + a] += site_dmsd(pc.w, pc.mu[a], pc.r, a);
+    }
+}
+
+// One work item: the 32 x 8 tile (x-tile, y-tile) over planes
+// [zc*cz, zc*cz+cz).  Adds this thread's site sums to part[] (FP32).
+template <typename WT, int MSD>
+__device__ __forceinline__ void step1_item(const LatticeView& v, int cz, int tiles_x, int tiles_y,
+                                           int item, float* part) {
+    const Ptrs<WT> A = make_ptrs<WT>(v);
+    const int plane = v.Xp * v.Yp;
+    const int tx = item % tiles_x;
+    const int rest = item / tiles_x;
+    const int tyi = rest % tiles_y;
+    const int zc = rest / tiles_y;
+    Col c;
+    c.lane = threadIdx.x;
+    c.x = tx * TX + threadIdx.x;
+    c.y = tyi * TY + threadIdx.y;
+    // a thread loads if its site is a lattice site or the ghost column right
+    // of the lattice (the -x hop source of the previous lane's site)
+    c.load = c.x <= v.nx && c.y < v.ny;
+    c.site = c.x < v.nx && c.y < v.ny;
+    c.halo = 0;
+    if (c.load && c.lane == 0) c.halo = -1;
+    if (c.site && c.lane == BX - 1) c.halo = 1;
+    c.o = (c.y + v.G) * v.Xp + (c.x + v.G);
+    const int z0 = zc * cz;
+    const int z1 = min(z0 + cz, v.nz);
+
+    Pl<MSD> P0, P1, P2, P3;
+    zero_pl(P0); zero_pl(P1); zero_pl(P2); zero_pl(P3);
+    float2 R0 = make_float2(1.f, 0.f), R1 = R0;
+    {
+        const int zb = z0 == 0 ? v.nz - 1 : z0 - 1;
+        const int zn = z0 + 1 >= v.nz ? z0 + 1 - v.nz : z0 + 1;
+        load_early<WT, MSD>(P0, A, zb * plane, c);          // below: state, w4
+        if (c.load) P0.w[4] = ldw<WT>(A.w[4] + zb * plane + c.o);
+        load_early<WT, MSD>(P1, A, z0 * plane, c);          // this plane: everything
+        load_late<WT, MSD>(P1, A, z0 * plane, c);
+        load_early<WT, MSD>(P2, A, zn * plane, c);          // above: early part
+        if (c.load) R0 = __ldg(A.R + z0 * plane + c.o);
+    }
+    // register sets rotate (below, at, above, prefetch): 0 1 2 3 -> 1 2 3 0 ...
+    for (int z = z0; z < z1; z += 4) {
+        do_plane<WT, MSD>(v, A, c, z, z1, plane, P0, P1, P2, P3, R0, R1, part);
+        if (z + 1 >= z1) break;
+        do_plane<WT, MSD>(v, A, c, z + 1, z1, plane, P1, P2, P3, P0, R1, R0, part);
+        if (z + 2 >= z1) break;
+        do_plane<WT, MSD>(v, A, c, z + 2, z1, plane, P2, P3, P0, P1, R0, R1, part);
+        if (z + 3 >= z1) break;
+        do_plane<WT, MSD>(v, A, c, z + 3, z1, plane, P3, P0, P1, P2, R1, R0, part);
+    }
+}
 
 template <typename WT, int MSD>
-__global__ void __launch_bounds__(BX * BY, MSD ? 3 : 4)
+__global__ void __launch_bounds__(BX * BY, 2)
 k_step1(LatticeView v, int cz, int tiles_x, int tiles_y, int n_items) {
     __shared__ double smem[NWARP * kNumSums];
-    const WT* W = static_cast<const WT*>(v.w);
-    const long long Np = v.Np;
-    const long long plane = (long long)v.Xp * v.Yp;
     const int lane = threadIdx.x;
     double acc[1][kNumSums] = {{0, 0, 0, 0, 0, 0}};
-
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int tx = item % tiles_x;
-        const int rest = item / tiles_x;
-        const int tyi = rest % tiles_y;
-        const int zc = rest / tiles_y;
-        const int x = tx * BX + lane;
-        const int y = tyi * BY + threadIdx.y;
-        const int z0 = zc * cz;
-        const int z1 = min(z0 + cz, v.nz);
-        const bool act = x < v.nx && y < v.ny;
-        const long long col = (long long)(y + v.G) * v.Xp + (x + v.G);
-
-        // registers: b = plane below, c = this plane, n = plane above
-        float rb = 0.f, rc = 0.f, w4b = 0.f;
-        float2 mb = make_float2(0.f, 0.f), mc = mb;
-        float mub[3] = {0.f, 0.f, 0.f}, muc[3] = {0.f, 0.f, 0.f};
-        float wc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (act) {
-            const int zb = z0 == 0 ? v.nz - 1 : z0 - 1;
-            const long long ib = zb * plane + col, ic = z0 * plane + col;
-            rb = __ldg(v.rho_in + ib);
-            mb = __ldg(v.m_in + ib);
-            rc = __ldg(v.rho_in + ic);
-            mc = __ldg(v.m_in + ic);
+        float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        step1_item<WT, MSD>(v, cz, tiles_x, tiles_y, item, part);
+        // one FP32 warp reduction per item, accumulated in FP64 by lane 0
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (MSD >> a & 1) { mub[a] = __ldg(v.mu_in[a] + ib); muc[a] = __ldg(v.mu_in[a] + ic); }
-            w4b = ldw<WT>(W + 4 * Np + ib);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) wc[k] = ldw<WT>(W + k * Np + ic);
-        }
-        for (int z = z0; z < z1; ++z) {
-            const int zn = z + 1 == v.nz ? 0 : z + 1;
-            const long long ic = z * plane + col, in = zn * plane + col;
-            float vals[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float rn = 0.f;
-            float2 mn = make_float2(0.f, 0.f);
-            float mun[3] = {0.f, 0.f, 0.f};
-            float wn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (act) {
-                rn = __ldg(v.rho_in + in);
-                mn = __ldg(v.m_in + in);
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    if (MSD >> a & 1) mun[a] = __ldg(v.mu_in[a] + in);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) wn[k] = ldw<WT>(W + k * Np + in);
-
-                // sources of the hops into this site: k = +x from x-1, -x from
-                // x+1, +y from y-1, -y from y+1, +z from below, -z from above
-                const long long src[4] = {ic - 1, ic + 1, ic - v.Xp, ic + v.Xp};
-                SiteIn q;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    q.win[k] = ldw<WT>(W + k * Np + src[k]);
-                    q.r[k] = __ldg(v.rho_in + src[k]);
-                    q.m[k] = __ldg(v.m_in + src[k]);
-                }
-                q.win[4] = w4b; q.r[4] = rb; q.m[4] = mb;
-                q.win[5] = wn[5]; q.r[5] = rn; q.m[5] = mn;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) q.wout[k] = wc[k];
-                q.rc = rc;
-                q.mc = mc;
-                q.R = __ldg(v.R + ic);
-                const float s = stay_weight(wc);
-                float ro;
-                float2 mo;
-                site_rho_m(q, s, ro, mo);
-                const long long zoff = z * plane;
-                store_images(v.rho_out, v, x, y, zoff, ro);
-                store_images(v.m_out, v, x, y, zoff, mo);
-                vals[0] = mo.x;
-                vals[1] = mo.y;
-                vals[2] = ro;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (!(MSD >> a & 1)) continue;
-                    float nbm[6];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) nbm[k] = __ldg(v.mu_in[a] + src[k]);
-                    nbm[4] = mub[a];
-                    nbm[5] = mun[a];
-                    const float mo_a = site_mu(q.win, q.r, nbm, s, muc[a], a);
-                    store_images(v.mu_out[a], v, x, y, zoff, mo_a);
-                    vals[3 + a] = site_dmsd(wc, muc[a], rc, a);
-                }
-            }
-#pragma unroll
-            for (int qq = 0; qq < kNumSums; ++qq) {
-                if (qq >= 3 && !(MSD >> (qq - 3) & 1)) continue;
-                const float t = warp_sum_f32(vals[qq]);
-                if (lane == 0) acc[0][qq] += (double)t;
-            }
-            rb = rc; mb = mc; rc = rn; mc = mn; w4b = wc[4];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) { mub[a] = muc[a]; muc[a] = mun[a]; }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) wc[k] = wn[k];
+        for (int qq = 0; qq < kNumSums; ++qq) {
+            if (qq >= 3 && !(MSD >> (qq - 3) & 1)) continue;
+            const float t = warp_sum_f32(part[qq]);
+            if (lane == 0) acc[0][qq] += (double)t;
         }
     }
     block_finish<NWARP>(v, acc, 1, smem);
@@ -149,8 +282,8 @@ struct Step1Shape {
 
 Step1Shape step1_shape(const LatticeView& v, int wdtype) {
     Step1Shape s;
-    s.tiles_x = (v.nx + BX - 1) / BX;
-    s.tiles_y = (v.ny + BY - 1) / BY;
+    s.tiles_x = (v.nx + TX - 1) / TX;
+    s.tiles_y = (v.ny + TY - 1) / TY;
     static int occ_cache[2][8] = {{0}};
     int& occ = occ_cache[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][v.msd_axes & 7];
     if (occ == 0) {
@@ -160,8 +293,8 @@ Step1Shape step1_shape(const LatticeView& v, int wdtype) {
     const long long resident = (long long)device_props().sm_count * occ;
     // z chunks: enough work items for ~8 waves, chunks of 8..64 planes
     const long long xy = (long long)s.tiles_x * s.tiles_y;
-    long long want = resident * 8;
-    long long nchunks = (want + xy - 1) / xy;
+    const long long want = resident * 8;
+    const long long nchunks = (want + xy - 1) / xy;
     int cz = (int)((v.nz + nchunks - 1) / nchunks);
     if (cz > 64) cz = 64;
     if (cz < 8) cz = 8;
@@ -184,6 +317,114 @@ cudaError_t launch_step1(const LatticeView& v, int wdtype, cudaStream_t st) {
     int cz = s.cz, tx = s.tiles_x, ty = s.tiles_y, ni = s.n_items;
     void* args[] = {&vv, &cz, &tx, &ty, &ni};
     return cudaLaunchKernel(fn, dim3(s.grid), dim3(BX, BY), args, 0, st);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: many lattices advance one step in one launch.
+//
+// Work items are the same 32 x 8 x cz tiles as above, with a fixed cz per
+// lattice (kBatchCZ), listed lattice after lattice.  Each item's sums are
+// combined in the block in a fixed order and stored in the lattice's own
+// partials buffer at the item's index; the block that completes a lattice's
+// last item sums that lattice's item partials in item order.  A lattice's
+// results therefore do not depend on which other lattices share the launch.
+
+namespace {
+
+template <typename WT, int MSD>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_step_batch(const __grid_constant__ BatchParams bp) {
+    __shared__ double wsum[NWARP][kNumSums];
+    __shared__ unsigned int last;
+    const int lane = threadIdx.x;
+    const int warp = threadIdx.y;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int gi = blockIdx.x; gi < bp.total_items; gi += gridDim.x) {
+        int lo_ = 0, hi_ = bp.count - 1;          // lattice of this item
+        while (lo_ < hi_) {
+            const int mid = (lo_ + hi_ + 1) >> 1;
+            if (bp.e[mid].item0 <= gi) lo_ = mid;
+            else hi_ = mid - 1;
+        }
+        const BatchEntry& E = bp.e[lo_];
+        const int li = gi - E.item0;
+        float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        step1_item<WT, MSD>(E.v, E.cz, E.tiles_x, E.tiles_y, li, part);
+#pragma unroll
+        for (int qq = 0; qq < kNumSums; ++qq) {
+            const float t = warp_sum_f32(part[qq]);
+            if (lane == 0) wsum[warp][qq] = (double)t;
+        }
+        __syncthreads();
+        if (tid < kNumSums) {
+            double sacc = 0.0;
+            for (int w = 0; w < NWARP; ++w) sacc += wsum[w][tid];
+            E.v.partials[(long long)li * kNumSums + tid] = sacc;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last = atomicAdd(E.v.counter, 1u) == (unsigned)E.n_items - 1u;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            const long long n = *E.v.step;
+            if (warp < kNumSums) {
+                const int q = warp;
+                double sacc = 0.0;
+                for (int b = lane; b < E.n_items; b += 32) sacc += __ldcg(&E.v.partials[(long long)b * kNumSums + q]);
+                sacc = warp_sum_f64(sacc);
+                if (lane == 0) {
+                    if (q == 0) E.v.histM[n + 1].x = sacc;
+                    else if (q == 1) E.v.histM[n + 1].y = sacc;
+                    else if (q == 2) E.v.histP[n + 1] = sacc;
+                    else if (MSD >> (q - 3) & 1) E.v.histD[(long long)(q - 3) * E.v.cap + n] = sacc;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                *E.v.step = n + 1;
+                *E.v.counter = 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename WT, int MSD>
+void* batch_fn() { return reinterpret_cast<void*>(&k_step_batch<WT, MSD>); }
+
+void* batch_kernel(int wdtype, int msd) {
+    static void* tab[2][8] = {
+        {batch_fn<float, 0>(), batch_fn<float, 1>(), batch_fn<float, 2>(), batch_fn<float, 3>(),
+         batch_fn<float, 4>(), batch_fn<float, 5>(), batch_fn<float, 6>(), batch_fn<float, 7>()},
+        {batch_fn<__nv_bfloat16, 0>(), batch_fn<__nv_bfloat16, 1>(), batch_fn<__nv_bfloat16, 2>(),
+         batch_fn<__nv_bfloat16, 3>(), batch_fn<__nv_bfloat16, 4>(), batch_fn<__nv_bfloat16, 5>(),
+         batch_fn<__nv_bfloat16, 6>(), batch_fn<__nv_bfloat16, 7>()}};
+    return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
+}
+
+}  // namespace
+
+int batch_items(const LatticeView& v, int* tiles_x, int* tiles_y, int* cz) {
+    *tiles_x = (v.nx + TX - 1) / TX;
+    *tiles_y = (v.ny + TY - 1) / TY;
+    *cz = v.nz < kBatchCZ ? v.nz : kBatchCZ;
+    return *tiles_x * *tiles_y * ((v.nz + *cz - 1) / *cz);
+}
+
+cudaError_t launch_batch(const BatchParams& bp, int wdtype, int msd, cudaStream_t st) {
+    void* fn = batch_kernel(wdtype, msd);
+    static int occ_cache[2][8] = {{0}};
+    int& occ = occ_cache[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
+    if (occ == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BX * BY, 0);
+        if (occ < 1) occ = 1;
+    }
+    int grid = device_props().sm_count * occ;
+    if (grid > bp.total_items) grid = bp.total_items;
+    if (grid < 1) return cudaSuccess;
+    void* args[] = {const_cast<BatchParams*>(&bp)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(BX, BY), args, 0, st);
 }
 
 }  // namespace lpc

@@ -30,9 +30,10 @@ namespace lpc {
 namespace {
 
 constexpr int kW = 32;      // box width (one warp per row)
-constexpr int kNW = 8;      // warps per CTA
+constexpr int kNW = 16;     // warps per CTA
 constexpr int kP = 2;       // prefetch distance in planes
-constexpr int kS0 = kP + 3; // level-0 state slots
+constexpr int kS0 = kP + 4; // level-0 state slots (planes t-4 .. t+P-1 live)
+constexpr int kRing = 4;    // planes per intermediate-level ring
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t sa(const void* p) {
@@ -117,7 +118,7 @@ __host__ __device__ inline TBLayout tb_layout(int H, int K, int nmsd, int wb, in
     L.state_slot = plane * (12 + 4 * (size_t)nmsd);
     L.static_slot = plane * (6 * (size_t)wb + 8);
     L.off_lj = (size_t)kS0 * L.state_slot;
-    L.off_st = L.off_lj + 3 * (size_t)(K - 1) * L.state_slot;
+    L.off_st = L.off_lj + kRing * (size_t)(K - 1) * L.state_slot;
     L.off_bar = L.off_st + (size_t)SS * L.static_slot;
     L.off_red = L.off_bar + ((size_t)(kS0 + SS) * 8 + 15) / 16 * 16;
     L.total = L.off_red + (size_t)kNW * K * kNumSums * 8 + 128;
@@ -150,7 +151,7 @@ k_step_tb(const __grid_constant__ TBMaps maps, LatticeView v, TBGeom g) {
     // TMA destinations must be 128-byte aligned: round the dynamic base up
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc3(MSD);
-    constexpr int SS = K + kP + 2;
+    constexpr int SS = 2 * K + kP + 2;   // static planes t-2K-2 .. t+P-1 live
     const int H = g.H, G = g.G, TX = g.TX, TY = g.TY;
     const int plane = H * kW;
     const TBLayout L = tb_layout(H, K, NMSD, (int)sizeof(WT), SS);
@@ -167,7 +168,7 @@ k_step_tb(const __grid_constant__ TBMaps maps, LatticeView v, TBGeom g) {
     for (int i = tid; i < kNW * K * kNumSums; i += kNW * 32) red[i] = 0.0;
     __syncthreads();
 
-    // axis index of the k-th enabled MSD component
+    // axis index of the n-th enabled MSD component
     int axis_of[3] = {0, 0, 0};
     {
         int n = 0;
@@ -177,7 +178,7 @@ k_step_tb(const __grid_constant__ TBMaps maps, LatticeView v, TBGeom g) {
 
     unsigned int issued_base = 0;    // planes loaded by this CTA before the current item
     bool failed = false;
-    int fail_t = 0, fail_T = 0;
+    int fail_t = 0, fail_NQ = 0;
     const long long zplane = (long long)v.Xp * v.Yp;
 
     for (int item = blockIdx.x; item < g.n_items; item += gridDim.x) {
@@ -189,7 +190,8 @@ k_step_tb(const __grid_constant__ TBMaps maps, LatticeView v, TBGeom g) {
         const int z0 = zc * g.cz;
         const int z1 = min(z0 + g.cz, v.nz);
         const int CZ = z1 - z0;
-        const int T = CZ + 2 * K;
+        const int NQ = CZ + 2 * K;      // input planes of this item
+        const int T = CZ + 3 * K;       // iterations (level j lags 2j planes)
 
         auto issue = [&](int q) {
             const unsigned int l = issued_base + q;
@@ -212,153 +214,176 @@ k_step_tb(const __grid_constant__ TBMaps maps, LatticeView v, TBGeom g) {
 
         if (tid == 0) {
             fence_proxy_async();
-            for (int q = 0; q < kP && q < T; ++q) issue(q);
+            for (int q = 0; q < kP && q < NQ; ++q) issue(q);
         }
+        // per-thread FP32 sums of each level over this item's core sites
+        float part[K][kNumSums];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int qq = 0; qq < kNumSums; ++qq) part[j][qq] = 0.f;
 
         for (int t = 0; t < T; ++t) {
-            if (tid == 0 && t + kP < T) {
+            if (tid == 0 && t + kP < NQ) {
                 fence_proxy_async();
                 issue(t + kP);
             }
-            const unsigned int l = issued_base + t;
-            bool ok = mbar_wait_bounded(&bar_s[l % kS0], (l / kS0) & 1u);
-            ok = ok && mbar_wait_bounded(&bar_w[l % SS], (l / SS) & 1u);
+            // this iteration reads input planes up to t-1
+            bool ok = true;
+            if (t >= 1 && t - 1 < NQ) {
+                const unsigned int l = issued_base + (t - 1);
+                ok = mbar_wait_bounded(&bar_s[l % kS0], (l / kS0) & 1u);
+                ok = ok && mbar_wait_bounded(&bar_w[l % SS], (l / SS) & 1u);
+            }
+            // tasks of this iteration: (level j, row) for every active level;
+            // level j computes plane q = t - 2j, so no level reads a plane
+            // written in the same iteration
+            int cnt[K];
+            int ntask = 0;
+#pragma unroll
+            for (int j = 1; j <= K; ++j) {
+                const int q = t - 2 * j;
+                cnt[j - 1] = (q >= j && q <= NQ - 1 - j) ? TY + 2 * (K - j) : 0;
+                ntask += cnt[j - 1];
+            }
+            for (int task = warp; task < ntask; task += kNW) {
+                int j = 1, r = task;
+#pragma unroll
+                for (int jj = 0; jj < K - 1; ++jj)
+                    if (j == jj + 1 && r >= cnt[jj]) { r -= cnt[jj]; j = jj + 2; }
+                const int lo = G - K + j;
+                r += lo;                                  // box row
+                const int q = t - 2 * j;                  // chunk-relative plane
+                Slot in[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const int qq = q - 1 + d;
+                    unsigned char* base;
+                    if (j == 1) base = smem + (size_t)((issued_base + qq) % kS0) * L.state_slot;
+                    else base = smem + L.off_lj + ((size_t)(j - 2) * kRing + (qq % kRing)) * L.state_slot;
+                    in[d] = slot_at(base, L.state_slot, plane, NMSD);
+                }
+                const WT* ws[3];
+                const float2* Rq = nullptr;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    unsigned char* bp = smem + L.off_st + (size_t)((issued_base + q - 1 + d) % SS) * L.static_slot;
+                    ws[d] = reinterpret_cast<const WT*>(bp);
+                    if (d == 1) Rq = reinterpret_cast<const float2*>(bp + (size_t)plane * 6 * sizeof(WT));
+                }
+                const int hic = G + TX + K - j;           // end column of this level
+                const int zl = z0 - K + q;                // lattice plane (unwrapped)
+                const bool core_plane = zl >= z0 && zl < z1;
+                const bool active_c = lane >= lo && lane < hic;
+                const bool core_c = lane >= G && lane < G + TX && (x0 + lane - G) < v.nx;
+                const int o = r * kW + lane;
+                SiteIn qi;
+                float wo[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) wo[k] = lds_w<WT>(ws[1] + k * plane + o);
+                qi.rc = in[1].r[o];
+                qi.mc = in[1].m[o];
+                qi.r[0] = __shfl_up_sync(0xffffffffu, qi.rc, 1);
+                qi.m[0].x = __shfl_up_sync(0xffffffffu, qi.mc.x, 1);
+                qi.m[0].y = __shfl_up_sync(0xffffffffu, qi.mc.y, 1);
+                qi.win[0] = __shfl_up_sync(0xffffffffu, wo[0], 1);
+                qi.r[1] = __shfl_down_sync(0xffffffffu, qi.rc, 1);
+                qi.m[1].x = __shfl_down_sync(0xffffffffu, qi.mc.x, 1);
+                qi.m[1].y = __shfl_down_sync(0xffffffffu, qi.mc.y, 1);
+                qi.win[1] = __shfl_down_sync(0xffffffffu, wo[1], 1);
+                qi.r[2] = in[1].r[o - kW];
+                qi.m[2] = in[1].m[o - kW];
+                qi.win[2] = lds_w<WT>(ws[1] + 2 * plane + o - kW);
+                qi.r[3] = in[1].r[o + kW];
+                qi.m[3] = in[1].m[o + kW];
+                qi.win[3] = lds_w<WT>(ws[1] + 3 * plane + o + kW);
+                qi.r[4] = in[0].r[o];
+                qi.m[4] = in[0].m[o];
+                qi.win[4] = lds_w<WT>(ws[0] + 4 * plane + o);
+                qi.r[5] = in[2].r[o];
+                qi.m[5] = in[2].m[o];
+                qi.win[5] = lds_w<WT>(ws[2] + 5 * plane + o);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) qi.wout[k] = wo[k];
+                qi.R = Rq[o];
+                const float s = stay_weight(wo);
+                float ro;
+                float2 mo;
+                site_rho_m(qi, s, ro, mo);
+                float muo[3] = {0.f, 0.f, 0.f}, dms[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int n = 0; n < NMSD; ++n) {
+                    const int a = axis_of[n];
+                    const float muc = in[1].mu[n][o];
+                    float nb[6];
+                    nb[0] = __shfl_up_sync(0xffffffffu, muc, 1);
+                    nb[1] = __shfl_down_sync(0xffffffffu, muc, 1);
+                    nb[2] = in[1].mu[n][o - kW];
+                    nb[3] = in[1].mu[n][o + kW];
+                    nb[4] = in[0].mu[n][o];
+                    nb[5] = in[2].mu[n][o];
+                    muo[n] = site_mu(qi.win, qi.r, nb, s, muc, a);
+                    dms[n] = site_dmsd(wo, muc, qi.rc, a);
+                }
+                const bool core = core_plane && core_c && r >= G && r < G + TY && (y0 + r - G) < v.ny;
+                if (active_c) {
+                    if (j < K) {
+                        Slot out = slot_at(smem + L.off_lj + ((size_t)(j - 1) * kRing + (q % kRing)) * L.state_slot,
+                                           L.state_slot, plane, NMSD);
+                        out.r[o] = ro;
+                        out.m[o] = mo;
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) out.mu[n][o] = muo[n];
+                    } else if (core) {
+                        const int x = x0 + lane - G, y = y0 + r - G;
+                        const long long zoff = (long long)zl * zplane;
+                        store_images(v.rho_out, v, x, y, zoff, ro);
+                        store_images(v.m_out, v, x, y, zoff, mo);
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo[n]);
+                    }
+                }
+                if (core) {
+#pragma unroll
+                    for (int jj = 0; jj < K; ++jj)
+                        if (jj == j - 1) {
+                            part[jj][0] += mo.x;
+                            part[jj][1] += mo.y;
+                            part[jj][2] += ro;
+#pragma unroll
+                            for (int n = 0; n < NMSD; ++n) part[jj][3 + axis_of[n]] += dms[n];
+                        }
+                }
+            }
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 fail_t = t;
-                fail_T = T;
+                fail_NQ = NQ;
                 break;
-            }
-#pragma unroll 1
-            for (int j = 1; j <= K; ++j) {
-                if (t >= 2 * j) {
-                    const int q = t - j;          // chunk-relative plane of this level
-                    // inputs: level j-1 at planes q-1, q, q+1
-                    Slot in[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const int qq = q - 1 + d;
-                        unsigned char* base;
-                        if (j == 1) base = smem + (size_t)((issued_base + qq) % kS0) * L.state_slot;
-                        else base = smem + L.off_lj + ((size_t)(j - 2) * 3 + (qq % 3)) * L.state_slot;
-                        in[d] = slot_at(base, L.state_slot, plane, NMSD);
-                    }
-                    const WT* ws[3];
-                    const float2* Rq = nullptr;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        unsigned char* b = smem + L.off_st + (size_t)((issued_base + q - 1 + d) % SS) * L.static_slot;
-                        ws[d] = reinterpret_cast<const WT*>(b);
-                        if (d == 1) Rq = reinterpret_cast<const float2*>(b + (size_t)plane * 6 * sizeof(WT));
-                    }
-                    Slot out = slot_at(smem + L.off_lj + ((size_t)(j - 1) * 3 + (q % 3)) * L.state_slot,
-                                       L.state_slot, plane, NMSD);
-                    const int lo = G - K + j;                  // first row / column of this level
-                    const int hir = G + TY + K - j;           // end row
-                    const int hic = G + TX + K - j;           // end column
-                    const int zl = z0 - K + q;                // lattice plane (unwrapped)
-                    const bool core_plane = zl >= z0 && zl < z1;
-                    const bool active_c = lane >= lo && lane < hic;
-                    const bool core_c = lane >= G && lane < G + TX && (x0 + lane - G) < v.nx;
-                    for (int r = warp; r < H; r += kNW) {
-                        if (r < lo || r >= hir) continue;      // warp-uniform
-                        const int o = r * kW + lane;
-                        SiteIn qi;
-                        float wo[6];
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) wo[k] = lds_w<WT>(ws[1] + k * plane + o);
-                        qi.rc = in[1].r[o];
-                        qi.mc = in[1].m[o];
-                        qi.r[0] = __shfl_up_sync(0xffffffffu, qi.rc, 1);
-                        qi.m[0].x = __shfl_up_sync(0xffffffffu, qi.mc.x, 1);
-                        qi.m[0].y = __shfl_up_sync(0xffffffffu, qi.mc.y, 1);
-                        qi.win[0] = __shfl_up_sync(0xffffffffu, wo[0], 1);
-                        qi.r[1] = __shfl_down_sync(0xffffffffu, qi.rc, 1);
-                        qi.m[1].x = __shfl_down_sync(0xffffffffu, qi.mc.x, 1);
-                        qi.m[1].y = __shfl_down_sync(0xffffffffu, qi.mc.y, 1);
-                        qi.win[1] = __shfl_down_sync(0xffffffffu, wo[1], 1);
-                        qi.r[2] = in[1].r[o - kW];
-                        qi.m[2] = in[1].m[o - kW];
-                        qi.win[2] = lds_w<WT>(ws[1] + 2 * plane + o - kW);
-                        qi.r[3] = in[1].r[o + kW];
-                        qi.m[3] = in[1].m[o + kW];
-                        qi.win[3] = lds_w<WT>(ws[1] + 3 * plane + o + kW);
-                        qi.r[4] = in[0].r[o];
-                        qi.m[4] = in[0].m[o];
-                        qi.win[4] = lds_w<WT>(ws[0] + 4 * plane + o);
-                        qi.r[5] = in[2].r[o];
-                        qi.m[5] = in[2].m[o];
-                        qi.win[5] = lds_w<WT>(ws[2] + 5 * plane + o);
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) qi.wout[k] = wo[k];
-                        qi.R = Rq[o];
-                        const float s = stay_weight(wo);
-                        float ro;
-                        float2 mo;
-                        site_rho_m(qi, s, ro, mo);
-                        float muo[3] = {0.f, 0.f, 0.f}, dms[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int n = 0; n < NMSD; ++n) {
-                            const int a = axis_of[n];
-                            const float muc = in[1].mu[n][o];
-                            float nb[6];
-                            nb[0] = __shfl_up_sync(0xffffffffu, muc, 1);
-                            nb[1] = __shfl_down_sync(0xffffffffu, muc, 1);
-                            nb[2] = in[1].mu[n][o - kW];
-                            nb[3] = in[1].mu[n][o + kW];
-                            nb[4] = in[0].mu[n][o];
-                            nb[5] = in[2].mu[n][o];
-                            muo[n] = site_mu(qi.win, qi.r, nb, s, muc, a);
-                            dms[n] = site_dmsd(wo, muc, qi.rc, a);
-                        }
-                        const bool core = core_plane && core_c && r >= G && r < G + TY && (y0 + r - G) < v.ny;
-                        if (active_c) {
-                            if (j < K) {
-                                out.r[o] = ro;
-                                out.m[o] = mo;
-#pragma unroll
-                                for (int n = 0; n < NMSD; ++n) out.mu[n][o] = muo[n];
-                            } else if (core) {
-                                const int x = x0 + lane - G, y = y0 + r - G;
-                                const long long zoff = (long long)zl * zplane;
-                                store_images(v.rho_out, v, x, y, zoff, ro);
-                                store_images(v.m_out, v, x, y, zoff, mo);
-#pragma unroll
-                                for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo[n]);
-                            }
-                        }
-                        if (core_plane && r >= G && r < G + TY) {     // warp-uniform
-                            float vals[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                            if (core) {
-                                vals[0] = mo.x;
-                                vals[1] = mo.y;
-                                vals[2] = ro;
-#pragma unroll
-                                for (int n = 0; n < NMSD; ++n) vals[3 + axis_of[n]] = dms[n];
-                            }
-                            double* acc = red + ((size_t)(j - 1) * kNW + warp) * kNumSums;
-#pragma unroll
-                            for (int qq = 0; qq < kNumSums; ++qq) {
-                                if (qq >= 3 && !(MSD >> (qq - 3) & 1)) continue;
-                                const float tsum = warp_sum_f32(vals[qq]);
-                                if (lane == 0) acc[qq] += (double)tsum;
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
             }
         }
         if (failed) break;
-        issued_base += (unsigned int)T;
+        // one FP32 warp reduction per level and quantity per item, FP64 per warp
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            double* acc = red + ((size_t)j * kNW + warp) * kNumSums;
+#pragma unroll
+            for (int qq = 0; qq < kNumSums; ++qq) {
+                if (qq >= 3 && !(MSD >> (qq - 3) & 1)) continue;
+                const float tsum = warp_sum_f32(part[j][qq]);
+                if (lane == 0) acc[qq] += (double)tsum;
+            }
+        }
+        issued_base += (unsigned int)NQ;
     }
 
     if (failed) {
         // record the timeout, then wait (bounded) for the copies still in flight
         if (tid == 0) {
             atomicExch(g.err, (unsigned int)LPC_ERR_TIMEOUT);
-            const int last = min(fail_t + kP, fail_T);
-            for (int q = fail_t; q < last; ++q) {
+            const int first = fail_t >= 1 ? fail_t - 1 : 0;
+            const int last = min(fail_t + kP, fail_NQ);
+            for (int q = first; q < last; ++q) {
                 const unsigned int l = issued_base + q;
                 mbar_wait_bounded(&bar_s[l % kS0], (l / kS0) & 1u);
                 mbar_wait_bounded(&bar_w[l % SS], (l / SS) & 1u);
@@ -439,7 +464,7 @@ bool tb_supported(const LatticeView& v, int wdtype, int K) {
 int tb_plan(const LatticeView& v, int wdtype, int K, TBGeom* out) {
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     const int nmsd = popc3(v.msd_axes);
-    const int SS = K + kP + 2;
+    const int SS = 2 * K + kP + 2;
     const int A = tb_align(wdtype);
     TBGeom g{};
     g.G = v.G;

@@ -240,6 +240,22 @@ cudaError_t launch_weights_f32(const LatticeView& v, int wdtype, float* dst_dev,
 cudaError_t launch_maxdiff(const float* a, const float* b, const LatticeView& v, double* out2,
                            cudaStream_t st);
 
+// Batched one-step launches over many lattices.
+constexpr int kMaxBatch = 48;        // lattices per launch (kernel parameter space)
+constexpr int kBatchCZ = 16;         // planes per work item in batched launches
+struct BatchEntry {
+    LatticeView v;
+    int item0;                       // first global item of this lattice
+    int n_items, tiles_x, tiles_y, cz;
+};
+struct BatchParams {
+    int count;
+    int total_items;
+    BatchEntry e[kMaxBatch];
+};
+int batch_items(const LatticeView& v, int* tiles_x, int* tiles_y, int* cz);
+cudaError_t launch_batch(const BatchParams& bp, int wdtype, int msd, cudaStream_t st);
+
 // Temporally blocked kernel (K steps per launch, TMA-staged planes).
 struct TBMaps;
 bool tb_supported(const LatticeView& v, int wdtype, int K);

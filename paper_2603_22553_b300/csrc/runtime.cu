@@ -295,7 +295,7 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     if (p->weight_dtype != LPC_WEIGHTS_F32 && p->weight_dtype != LPC_WEIGHTS_BF16) { set_error("lattice_create: weight_dtype must be 0 (FP32) or 1 (BF16)"); return LPC_ERR_INVALID; }
     if (p->msd_axes < 0 || p->msd_axes > 7) { set_error("lattice_create: msd_axes must be a mask of 1, 2, 4"); return LPC_ERR_INVALID; }
     if (p->init != LPC_INIT_UNIFORM && p->init != LPC_INIT_BOLTZMANN) { set_error("lattice_create: init must be 0 or 1"); return LPC_ERR_INVALID; }
-    if (p->ghost < 0 || p->ghost > kMaxGhost) { set_error("lattice_create: ghost must be in 0..8"); return LPC_ERR_INVALID; }
+    if (p->ghost < 0 || p->ghost > kMaxGhost || (p->ghost & 1)) { set_error("lattice_create: ghost must be 0 (automatic) or even in 2..8"); return LPC_ERR_INVALID; }
     for (int i = 0; i < 3; ++i)
         if (p->periodic[i] != 0 && p->periodic[i] != 1) { set_error("lattice_create: periodic flags must be 0 or 1"); return LPC_ERR_INVALID; }
     if (a && (!a->alloc || !a->free)) { set_error("lattice_create: allocator needs alloc and free"); return LPC_ERR_INVALID; }
@@ -309,11 +309,17 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     h->N = N;
     cudaGetDevice(&h->device);
     int G = p->ghost;
-    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 1;
+    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 2;
     h->G = G;
     h->Xp = ((p->nx + 2 * G) + 7) / 8 * 8;
     h->Yp = p->ny + 2 * G;
     h->Np = (long long)h->Xp * h->Yp * p->nz;
+    if (h->Np > 2147483647LL) {
+        // the kernels address the padded arrays with 32-bit offsets
+        delete h;
+        set_error("lattice_create: more than 2^31-1 sites including the ghost layers");
+        return LPC_ERR_INVALID;
+    }
     h->ustream = (cudaStream_t)stream;
     if (a) { h->alloc = *a; h->user_alloc = true; }
 
@@ -379,6 +385,30 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     }
     h->steps = 0;
     *out = h;
+    return LPC_OK;
+}
+
+lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes) {
+    if (!p || !bytes || steps < 0) { set_error("lattice_footprint: bad arguments"); return LPC_ERR_INVALID; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->ghost < 0 || p->ghost > kMaxGhost || (p->ghost & 1) ||
+        p->msd_axes < 0 || p->msd_axes > 7) {
+        set_error("lattice_footprint: bad parameters");
+        return LPC_ERR_INVALID;
+    }
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    int G = p->ghost;
+    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 2;
+    const long long Xp = ((p->nx + 2 * G) + 7) / 8 * 8, Yp = p->ny + 2 * G;
+    const long long Np = Xp * Yp * p->nz;
+    int na = 0;
+    for (int a = 0; a < 3; ++a) na += p->msd_axes >> a & 1;
+    const long long wb = p->weight_dtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    long long cap = steps + 1 < 1024 ? 1024 : steps + 1;
+    long long b = Np * (2 * 4 + 2 * 8 + 2 * 4 * na + 6 * wb + 8) + N;
+    b += (long long)device_props().sm_count * 32 * kMaxTB * kNumSums * 8 + 256 + 8 * 1024;
+    b += (long long)history_bytes(cap);
+    b += 16 * N;    // transient copies of F and omega during create
+    *bytes = b;
     return LPC_OK;
 }
 
@@ -449,10 +479,155 @@ lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
 
 lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count) {
     if (count < 0 || (count > 0 && (!hs || !n))) { set_error("lattice_step_many: bad arguments"); return LPC_ERR_INVALID; }
+    if (count == 0) return LPC_OK;
+    long long max_n = 0;
     for (int i = 0; i < count; ++i) {
-        lpc_status s = lattice_step_n(hs[i], n[i]);
-        if (s != LPC_OK) return s;
+        if (!hs[i] || n[i] < 0) { set_error("lattice_step_many: NULL handle or negative step count"); return LPC_ERR_INVALID; }
+        if (hs[i]->device != hs[0]->device) { set_error("lattice_step_many: lattices on different devices"); return LPC_ERR_INVALID; }
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) { set_error("lattice_step_many: a lattice appears twice"); return LPC_ERR_INVALID; }
+        if (n[i] > max_n) max_n = n[i];
     }
+    lpc_lattice* h0 = hs[0];
+    cudaSetDevice(h0->device);
+    cudaStream_t bs = h0->wstream;
+    // order the batch stream after every lattice's caller stream
+    for (int i = 0; i < count; ++i) {
+        lpc_status st = ensure_history(hs[i], hs[i]->steps + n[i] + 1);
+        if (st != LPC_OK) return st;
+        cudaEventRecord(hs[i]->ev_in, hs[i]->ustream);
+        cudaStreamWaitEvent(bs, hs[i]->ev_in, 0);
+        cudaEventRecord(hs[i]->ev_in, hs[i]->wstream);
+        cudaStreamWaitEvent(bs, hs[i]->ev_in, 0);
+    }
+    // lattices whose item partials do not fit their buffer step alone
+    std::vector<int> alone;
+    std::vector<int> batched;
+    for (int i = 0; i < count; ++i) {
+        int tx, ty, cz;
+        const int items = batch_items(make_view(hs[i], hs[i]->cur), &tx, &ty, &cz);
+        if ((size_t)items * kNumSums > hs[i]->partials_doubles) alone.push_back(i);
+        else batched.push_back(i);
+    }
+    static thread_local BatchParams bp;
+    lpc_status status = LPC_OK;
+    for (long long s = 0; s < max_n && status == LPC_OK; ++s) {
+        // one launch per (weight type, MSD mask) group and per kMaxBatch lattices
+        for (int wd = 0; wd < 2 && status == LPC_OK; ++wd)
+            for (int msd = 0; msd < 8 && status == LPC_OK; ++msd) {
+                bp.count = 0;
+                bp.total_items = 0;
+                auto flush = [&]() -> lpc_status {
+                    if (bp.count == 0) return LPC_OK;
+                    cudaError_t e = launch_batch(bp, wd, msd, bs);
+                    bp.count = 0;
+                    bp.total_items = 0;
+                    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "batched step launch");
+                };
+                for (int i : batched) {
+                    lpc_lattice* h = hs[i];
+                    if (n[i] <= s || h->p.weight_dtype != wd || h->p.msd_axes != msd) continue;
+                    BatchEntry& E = bp.e[bp.count];
+                    E.v = make_view(h, h->cur);
+                    E.n_items = batch_items(E.v, &E.tiles_x, &E.tiles_y, &E.cz);
+                    E.item0 = bp.total_items;
+                    bp.total_items += E.n_items;
+                    h->cur ^= 1;
+                    if (++bp.count == kMaxBatch) status = flush();
+                    if (status != LPC_OK) break;
+                }
+                if (status == LPC_OK) status = flush();
+            }
+        for (int i : alone)
+            if (status == LPC_OK && n[i] > s) status = launch_one(hs[i], bs, false);
+    }
+    for (int i = 0; i < count; ++i) hs[i]->steps += n[i];
+    // every lattice's private stream continues after the batch (queries and
+    // later calls synchronise on it); callers' streams are left free so that
+    // new lattices can be created while a batch runs
+    cudaEventRecord(h0->ev_out, bs);
+    for (int i = 0; i < count; ++i)
+        if (hs[i]->wstream != bs) cudaStreamWaitEvent(hs[i]->wstream, h0->ev_out, 0);
+    return status;
+}
+
+lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* kernel, int32_t* block_steps,
+                            double* rate) {
+    if (!h || trial_launches < 1) { set_error("lattice_autotune: bad arguments"); return LPC_ERR_INVALID; }
+    Entry en(h);
+    const size_t Np = (size_t)h->Np;
+    int na = 0;
+    for (int a = 0; a < 3; ++a) na += h->p.msd_axes >> a & 1;
+    // snapshot of the current state (the trials advance it)
+    const size_t snap_bytes = Np * (12 + 4 * (size_t)na);
+    char* snap = (char*)dalloc(h, snap_bytes);
+    if (!snap) { set_error("lattice_autotune: snapshot allocation failed"); return LPC_ERR_OOM; }
+    const int cur0 = h->cur;
+    const long long steps0 = h->steps;
+    const int kernel0 = h->kernel, k0 = h->kdepth;
+    cudaError_t e = cudaMemcpyAsync(snap, h->rho[cur0], Np * 4, cudaMemcpyDeviceToDevice, h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + Np * 4, h->m[cur0], Np * 8, cudaMemcpyDeviceToDevice, h->wstream);
+    for (int a = 0, n = 0; a < 3 && e == cudaSuccess; ++a)
+        if (h->p.msd_axes >> a & 1)
+            e = cudaMemcpyAsync(snap + Np * (12 + 4 * (size_t)n++), h->mu[cur0][a], Np * 4, cudaMemcpyDeviceToDevice, h->wstream);
+    if (e != cudaSuccess) { dfree(h, snap, snap_bytes); return cuda_fail(e, "lattice_autotune: snapshot"); }
+    // the trials write history entries after steps0; make room for them
+    const int maxk = h->G < 4 ? h->G : 4;
+    lpc_status st = ensure_history(h, steps0 + (long long)(trial_launches + 2) * maxk + 2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best_kernel = LPC_KERNEL_STEP1, best_k = 1;
+    double best = -1.0;
+    for (int cand = 0; cand <= maxk && st == LPC_OK; ++cand) {
+        const bool tb = cand > 0;
+        const int K = tb ? cand : 1;
+        if (tb && !tb_supported(make_view(h, 0), h->p.weight_dtype, K)) continue;
+        if (tb) {
+            h->kernel = LPC_KERNEL_TB;
+            h->kdepth = K;
+            if (tb_prepare(h->p.weight_dtype, K, h->p.msd_axes) != cudaSuccess) continue;
+        } else {
+            h->kernel = LPC_KERNEL_STEP1;
+            h->kdepth = 1;
+        }
+        for (int i = 0; i < 2 && st == LPC_OK; ++i) st = launch_one(h, h->wstream, tb);
+        cudaEventRecord(e0, h->wstream);
+        for (int i = 0; i < trial_launches && st == LPC_OK; ++i) st = launch_one(h, h->wstream, tb);
+        cudaEventRecord(e1, h->wstream);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { st = cuda_fail(e, "lattice_autotune: trial"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double r = (double)h->N * K * trial_launches / (ms * 1e-3);
+        if (r > best) { best = r; best_kernel = h->kernel; best_k = K; }
+        // the device step counter advanced; put it back for the next trial
+        const long long s0 = steps0;
+        cudaMemcpyAsync(h->dstep, &s0, 8, cudaMemcpyHostToDevice, h->wstream);
+        cudaStreamSynchronize(h->wstream);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the state into the buffer that was current
+    h->cur = cur0;
+    e = cudaMemcpyAsync(h->rho[cur0], snap, Np * 4, cudaMemcpyDeviceToDevice, h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->m[cur0], snap + Np * 4, Np * 8, cudaMemcpyDeviceToDevice, h->wstream);
+    for (int a = 0, n = 0; a < 3 && e == cudaSuccess; ++a)
+        if (h->p.msd_axes >> a & 1)
+            e = cudaMemcpyAsync(h->mu[cur0][a], snap + Np * (12 + 4 * (size_t)n++), Np * 4, cudaMemcpyDeviceToDevice, h->wstream);
+    const long long s0 = steps0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &s0, 8, cudaMemcpyHostToDevice, h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+    dfree(h, snap, snap_bytes);
+    h->steps = steps0;
+    if (st != LPC_OK) { h->kernel = kernel0; h->kdepth = k0; drop_graphs(h); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_autotune: restore");
+    h->kernel = best_kernel;
+    h->kdepth = best_k;
+    drop_graphs(h);
+    if (kernel) *kernel = best_kernel;
+    if (block_steps) *block_steps = best_k;
+    if (rate) *rate = best;
     return LPC_OK;
 }
 

@@ -41,6 +41,17 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def step_many(lattices, steps):
+    """Advance lattice i by steps[i] in batched launches (``lattice_step_many``)."""
+    lats = list(lattices)
+    if not lats:
+        return
+    lib = lats[0].lib
+    hs = (ctypes.c_void_p * len(lats))(*[l.h.value for l in lats])
+    ns = (ctypes.c_int64 * len(lats))(*[int(s) for s in steps])
+    B.check(lib.lattice_step_many(hs, ns, len(lats)), lib)
+
+
 class Lattice:
     """A lattice on the GPU: create, step, query, checkpoint, destroy."""
 
@@ -51,6 +62,7 @@ class Lattice:
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.msd_axes = msd_axes
+        self.weight_dtype = int(weight_dtype)
         self.dt = dt
         p = B.lpc_params(nx, ny, nz, (ctypes.c_int32 * 3)(*[int(v) for v in periodic]),
                          float(alpha), float(dt), float(kT), int(weight_dtype), int(msd_axes),
@@ -117,6 +129,16 @@ class Lattice:
 
     def sync(self):
         B.check(self.lib.lattice_sync(self.h), self.lib)
+
+    def autotune(self, trial_launches=6):
+        """Time every schedule the ghost width allows and keep the fastest
+        (``lattice_autotune``; the lattice's state is restored)."""
+        k = ctypes.c_int32()
+        d = ctypes.c_int32()
+        r = ctypes.c_double()
+        B.check(self.lib.lattice_autotune(self.h, int(trial_launches), ctypes.byref(k), ctypes.byref(d),
+                                          ctypes.byref(r)), self.lib)
+        return {"kernel": k.value, "block_steps": d.value, "rate": r.value}
 
     @property
     def steps_done(self):

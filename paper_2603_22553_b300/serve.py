@@ -1,0 +1,227 @@
+"""Serving loop: lattice solves of different sizes and lengths as they arrive.
+
+Continuous batching on one GPU:
+* requests enter a FIFO queue at their arrival times;
+* a request is admitted when its device footprint (``lattice_footprint``:
+  state, weights, history and create-time transients) fits the HBM budget
+  beside the resident lattices and an active slot is free; a preparation
+  thread builds its fields and creates the lattice (its state then stays
+  resident on the device until it finishes);
+* every round advances all resident lattices together by up to ``quantum``
+  steps with ``lattice_step_many`` (batched launches: one launch per step
+  covers the work items of every resident lattice), so work of requests that
+  arrived at different times overlaps on the device;
+* a lattice that has done its steps has its FID read back and is destroyed,
+  which frees its slot and memory for the next admission.
+
+Latency = finish - arrival; aggregate throughput = sum(sites * steps) / makespan.
+``serve_sequential`` is the comparator: the same stream solved one at a time
+with plain ``lattice_step_n``.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import dataclasses
+import queue
+import threading
+import time
+
+import numpy as np
+
+from . import binding as B
+
+
+@dataclasses.dataclass
+class Record:
+    rid: int
+    edge: int
+    steps: int
+    sites: int
+    arrival: float
+    admit: float = float("nan")
+    finish: float = float("nan")
+    fid: np.ndarray | None = None
+
+    @property
+    def latency(self):
+        return self.finish - self.arrival
+
+
+def footprint(edge, steps, weight_dtype=0, msd_axes=0):
+    """Device bytes a cubic lattice of this edge would hold (C ABI query)."""
+    lib = B.load()
+    p = B.lpc_params(edge, edge, edge, (ctypes.c_int32 * 3)(1, 1, 1), 0.005, 5e-6, 1.0,
+                     int(weight_dtype), int(msd_axes), 0, 0)
+    out = ctypes.c_int64()
+    B.check(lib.lattice_footprint(ctypes.byref(p), int(steps), ctypes.byref(out)), lib)
+    return out.value
+
+
+class GpuEngine:
+    """Creates, advances and reads lattices through the C ABI."""
+
+    def __init__(self, keep_fid=True):
+        import torch
+        from . import lattice as L
+        self.L = L
+        self.torch = torch
+        self.keep_fid = keep_fid
+        self.create_stream = torch.cuda.Stream()
+
+    def footprint(self, req):
+        return footprint(req.edge, req.steps)
+
+    def create(self, req):
+        inp = req.lattice()
+        with self.torch.cuda.stream(self.create_stream):
+            lat = self.L.Lattice.from_input(inp, stream=self.create_stream.cuda_stream)
+        return lat
+
+    def step_many(self, lats, steps):
+        self.L.step_many(lats, steps)
+
+    def finish(self, lat):
+        fid = lat.fid() if self.keep_fid else None
+        lat.close()
+        return fid
+
+
+class Server:
+    """Continuous-batching server over an engine (GPU or a test fake)."""
+
+    def __init__(self, engine, hbm_budget, max_active=48, quantum=250, prefetch=4):
+        self.engine = engine
+        self.budget = int(hbm_budget)
+        self.max_active = int(max_active)
+        self.quantum = int(quantum)
+        self.prefetch = int(prefetch)
+
+    def run(self, requests, realtime=True):
+        """Serve ``requests`` (sorted by arrival); returns the list of Records."""
+        eng = self.engine
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        recs = {r.rid: Record(r.rid, r.edge, r.steps, r.edge ** 3, r.arrival_s) for r in reqs}
+        fp = {r.rid: eng.footprint(r) for r in reqs}
+        for r in reqs:
+            if fp[r.rid] > self.budget:
+                raise ValueError("request %d needs %d bytes, above the HBM budget" % (r.rid, fp[r.rid]))
+        arrivals = collections.deque(reqs)
+        pending = collections.deque()        # arrived, not admitted
+        ready = queue.Queue()                # created lattices
+        work = queue.Queue()                 # admitted requests to prepare
+        active = []                          # [req, lattice, remaining]
+        used = 0
+        preparing = 0
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0) if realtime else None
+        vclock = [0.0]
+        now = clock if realtime else (lambda: vclock[0])
+        errors = []
+
+        def preparer():
+            while True:
+                req = work.get()
+                if req is None:
+                    return
+                try:
+                    ready.put((req, eng.create(req)))
+                except Exception as e:   # surfaced to the caller below
+                    errors.append(e)
+                    ready.put((req, None))
+
+        threads = [threading.Thread(target=preparer, daemon=True) for _ in range(max(1, self.prefetch))]
+        for th in threads:
+            th.start()
+        done = 0
+        try:
+            while done < len(reqs):
+                t = now()
+                while arrivals and arrivals[0].arrival_s <= t:
+                    pending.append(arrivals.popleft())
+                # admission by footprint and free slots (FIFO: no overtaking)
+                while (pending and len(active) + preparing < self.max_active
+                       and used + fp[pending[0].rid] <= self.budget):
+                    req = pending.popleft()
+                    used += fp[req.rid]
+                    preparing += 1
+                    recs[req.rid].admit = now()
+                    work.put(req)
+                # lattices whose creation finished join the batch
+                block = not active and preparing > 0
+                while True:
+                    try:
+                        req, lat = ready.get(block=block, timeout=60.0 if block else None)
+                    except queue.Empty:
+                        break
+                    block = False
+                    preparing -= 1
+                    if lat is None:
+                        raise errors[-1]
+                    active.append([req, lat, req.steps])
+                if not active:
+                    if arrivals and preparing == 0:
+                        if realtime:
+                            time.sleep(max(0.0, min(0.002, arrivals[0].arrival_s - now())))
+                        else:
+                            vclock[0] = max(vclock[0], arrivals[0].arrival_s)
+                    continue
+                n = [min(self.quantum, a[2]) for a in active]
+                eng.step_many([a[1] for a in active], n)
+                if not realtime:
+                    vclock[0] += sum(a[0].edge ** 3 * k for a, k in zip(active, n)) * 1e-11
+                for a, k in zip(active, n):
+                    a[2] -= k
+                still = []
+                for a in active:
+                    if a[2] == 0:
+                        fid = eng.finish(a[1])
+                        rec = recs[a[0].rid]
+                        rec.finish = now()
+                        rec.fid = fid
+                        used -= fp[a[0].rid]
+                        done += 1
+                    else:
+                        still.append(a)
+                active = still
+        finally:
+            for _ in threads:
+                work.put(None)
+        return [recs[r.rid] for r in reqs]
+
+
+def serve_sequential(engine, requests, realtime=True):
+    """One request at a time in arrival order with plain lattice_step_n."""
+    reqs = sorted(requests, key=lambda r: r.arrival_s)
+    out = []
+    t0 = time.perf_counter()
+    vclock = 0.0
+    for r in reqs:
+        now = (time.perf_counter() - t0) if realtime else vclock
+        if now < r.arrival_s:
+            if realtime:
+                time.sleep(r.arrival_s - now)
+            else:
+                vclock = r.arrival_s
+        rec = Record(r.rid, r.edge, r.steps, r.edge ** 3, r.arrival_s)
+        rec.admit = (time.perf_counter() - t0) if realtime else vclock
+        lat = engine.create(r)
+        lat.step(r.steps)
+        rec.fid = engine.finish(lat)
+        if realtime:
+            rec.finish = time.perf_counter() - t0
+        else:
+            vclock += r.edge ** 3 * r.steps * 1e-11
+            rec.finish = vclock
+        out.append(rec)
+    return out
+
+
+def summary(records):
+    lat = np.array([r.latency for r in records])
+    work = float(sum(r.sites * r.steps for r in records))
+    t_start = min(r.arrival for r in records)
+    t_end = max(r.finish for r in records)
+    return {"requests": len(records), "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "makespan_s": t_end - t_start,
+            "site_updates": work, "aggregate_site_updates_per_s": work / (t_end - t_start)}

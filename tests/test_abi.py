@@ -80,7 +80,8 @@ def _create(lib, p, F=None, om=None, solid=None, rho0=None):
 @pytest.mark.parametrize("kw,msg", [
     (dict(nx=0), "edges"), (dict(alpha=0.0), "alpha"), (dict(alpha=1.5), "alpha"),
     (dict(kT=0.0), "kT"), (dict(weight_dtype=3), "weight_dtype"), (dict(msd_axes=9), "msd_axes"),
-    (dict(init=7), "init"), (dict(ghost=9), "ghost"), (dict(periodic=(2, 1, 1)), "periodic"),
+    (dict(init=7), "init"), (dict(ghost=9), "ghost"), (dict(ghost=3), "ghost"),
+    (dict(periodic=(2, 1, 1)), "periodic"),
 ])
 def test_invalid_parameters_rejected_on_host(lib, kw, msg):
     st, h = _create(lib, _params(**kw))

@@ -25,10 +25,10 @@ CASES = [
     # shape (nz, ny, nx), periodic, msd mask, weight dtype, K, ghost
     ((12, 30, 61), (1, 1, 1), 0, 0, 2, 2),
     ((9, 41, 50), (0, 1, 1), 1, 0, 2, 2),
-    ((10, 26, 33), (1, 0, 1), 7, 0, 3, 3),
+    ((10, 26, 33), (1, 0, 1), 7, 0, 3, 4),
     ((7, 35, 70), (1, 1, 0), 2, 1, 4, 4),
     ((16, 20, 24), (1, 1, 1), 5, 1, 2, 4),
-    ((5, 9, 13), (1, 1, 1), 0, 0, 1, 1),
+    ((5, 9, 13), (1, 1, 1), 0, 0, 1, 2),
     ((3, 50, 100), (0, 0, 1), 6, 1, 3, 4),
 ]
 
@@ -96,7 +96,7 @@ def test_stale_allocator_memory_with_walls():
     junk = torch.full((64 << 20,), float("nan"), device="cuda")
     del junk
     inp = lpc_inputs.random_case((9, 40, 70), 102, periodic=(0, 1, 0), alpha=0.5, msd_axes=1)
-    for sched, G in (((B.LPC_KERNEL_STEP1, 1), 1), ((B.LPC_KERNEL_TB, 2), 2)):
+    for sched, G in (((B.LPC_KERNEL_STEP1, 1), 2), ((B.LPC_KERNEL_TB, 2), 2)):
         junk = torch.full((64 << 20,), float("nan"), device="cuda")
         del junk
         g = _run(inp, 40, sched, G)
@@ -104,3 +104,28 @@ def test_stale_allocator_memory_with_walls():
         o = H.oracle_run(inp, 40, oracle.MODE_F32)
         H.compare(g, o, 1, tol=1e-5)
         g["lattice"].close()
+
+
+def test_autotune_restores_state_and_caches(tmp_path):
+    """Autotuning mid-run leaves the results as if no trial had run, and the
+    JSON cache replays the same choice."""
+    from paper_2603_22553_b300 import autotune
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case((24, 40, 70), 321, periodic=(1, 0, 1), alpha=0.6, msd_axes=1)
+    ref = Lattice.from_input(inp, ghost=4)
+    ref.step(30)
+    lat = Lattice.from_input(inp, ghost=4)
+    lat.step(10)
+    path = str(tmp_path / "tune.json")
+    c1 = autotune.choose(lat, trial_launches=3, path=path)
+    assert not c1["cached"] and c1["kernel"] in (B.LPC_KERNEL_STEP1, B.LPC_KERNEL_TB)
+    assert lat.steps_done == 10
+    lat.step(20)
+    assert np.array_equal(lat.density(), ref.density())
+    assert np.allclose(lat.fid(), ref.fid(), rtol=1e-6, atol=1e-6 * abs(ref.fid()[0]))
+    assert np.allclose(lat.msd(0)[1:], ref.msd(0)[1:], rtol=1e-5)
+    other = Lattice.from_input(inp, ghost=4)
+    c2 = autotune.choose(other, path=path)
+    assert c2["cached"] and c2["kernel"] == c1["kernel"] and c2["block_steps"] == c1["block_steps"]
+    for l in (ref, lat, other):
+        l.close()
