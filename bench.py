@@ -139,7 +139,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("kernels_step.cu", "kernels_tb.cu", "lpc_internal.cuh"):
+    for name in ("kernels_step.cu", "kernels_tb.cu", "kernels_tma1.cu", "tma_ptx.cuh", "lpc_internal.cuh"):
         p = os.path.join(ROOT, "paper_2603_22553_b300", "csrc", name)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -147,13 +147,16 @@ def kernel_source_hash():
 
 
 def measured_traffic(kernel, workload, sites):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/), or
+    None when the kernel source changed since the counters were taken.  A
+    capture of a smaller lattice of the same kernel is scaled by the number
+    of sites (the traffic of these kernels is proportional to the sites)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[kernel][workload]
+        entries = d[kernel]
+        e = entries.get(workload) or next(iter(entries.values()))
     except Exception:
         return None
     if e.get("source_hash") != kernel_source_hash():
@@ -289,7 +292,10 @@ def run_ours(args):
         ms = float(t.item())
     lattice_steps = args.steps * args.block
     value = ws * N * lattice_steps / (ms / 1e3)
-    kernel_name = "step_tb" if info["kernel"] == B.LPC_KERNEL_TB else "step1"
+    if info["kernel"] == B.LPC_KERNEL_TB:
+        kernel_name = "k_step_tma1" if info["block_steps"] == 1 else "k_step_tb"
+    else:
+        kernel_name = "k_step1"
     launches = args.steps * (args.block // max(1, info["block_steps"]))
     bpu = info["bytes_per_site_update"]
     per_launch_ms = ms / launches

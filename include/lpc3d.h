@@ -86,8 +86,8 @@ typedef struct {
  *   init          initial population when rho0 is NULL: LPC_INIT_UNIFORM
  *                 (1 on pore sites) or LPC_INIT_BOLTZMANN (Eq. 2 with
  *                 mean 1 over pore sites).
- *   ghost         ghost-layer width in x and y: 0 = automatic (4 when nx and
- *                 ny >= 48, else 2) or an even width 2..8 (even, so that the
+ *   ghost         ghost-layer width in x and y: 0 = automatic (2) or an
+ *                 even width 2..8 (even, so that the
  *                 two-site vector loads of the step kernels stay aligned); the
  *                 temporally blocked kernel needs ghost >= its block depth.
  */
@@ -174,8 +174,11 @@ lpc_status lattice_step_n(lpc_lattice* h, int64_t n);
  */
 lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count);
 
-/* Choose the step kernel: LPC_KERNEL_AUTO / STEP1 / TB, with TB block
- * depth k (1..ghost).  LPC_ERR_INVALID if the combination is impossible. */
+/* Choose the step kernel: LPC_KERNEL_AUTO (the default: the TMA-fed
+ * one-step kernel for lattices of at least 2^18 sites with nx >= 32 and
+ * ny >= 16, else the register-pipelined one), STEP1, or TB with block depth
+ * k (1..min(4, ghost); k = 1 is the TMA-fed one-step kernel).
+ * LPC_ERR_INVALID if the combination is impossible. */
 lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps);
 
 /*

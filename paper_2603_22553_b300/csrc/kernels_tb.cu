@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include "lpc_internal.cuh"
+#include "tma_ptx.cuh"
 
 namespace lpc {
 
@@ -34,70 +35,11 @@ constexpr int kNW = 16;     // warps per CTA
 constexpr int kP = 2;       // prefetch distance in planes
 constexpr int kS0 = kP + 4; // level-0 state slots (planes t-4 .. t+P-1 live)
 constexpr int kRing = 4;    // planes per intermediate-level ring
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t sa(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(sa(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity) {
-    if (mbar_try_wait(b, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(b, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(sa(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-__device__ __forceinline__ void tma4(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z, int c) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(sa(bar)), "r"(x), "r"(y), "r"(z), "r"(c)
-        : "memory");
-}
-
-template <typename WT> __device__ __forceinline__ float lds_w(const WT* p);
-template <> __device__ __forceinline__ float lds_w<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float lds_w<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __uint_as_float(static_cast<unsigned int>(*reinterpret_cast<const unsigned short*>(p)) << 16);
-}
 
 constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
 
 }  // namespace
 
-// Tensor maps of one input buffer parity (kernel parameter, __grid_constant__).
-struct TBMaps {
-    CUtensorMap rho, m, mu[3], w, R;
-};
 
 // Geometry of one TB launch (identical in host and device).
 struct TBGeom {
@@ -426,6 +368,8 @@ void* tb_kernel(int wdtype, int K, int msd) {
     return wdtype == LPC_WEIGHTS_BF16 ? tb_fn_k<__nv_bfloat16>(K, msd) : tb_fn_k<float>(K, msd);
 }
 
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -439,23 +383,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
+bool tma_encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
             const cuuint64_t* strides, const cuuint32_t* box) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-}  // namespace
 
 // Column alignment of a TMA box start: 16 bytes of the narrowest element.
 static int tb_align(int wdtype) { return wdtype == LPC_WEIGHTS_BF16 ? 8 : 4; }
 
 bool tb_supported(const LatticeView& v, int wdtype, int K) {
+    if (K == 1) return v.G >= 1 && encode_fn() != nullptr;
     if (K < 1 || K > 4 || K > v.G) return false;
     const int TX = (kW - 2 * v.G) / tb_align(wdtype) * tb_align(wdtype);
     return TX >= tb_align(wdtype) && encode_fn() != nullptr;
@@ -493,37 +437,38 @@ int tb_plan(const LatticeView& v, int wdtype, int K, TBGeom* out) {
     return (int)tb_layout(H, K, nmsd, wb, SS).total;
 }
 
-bool tb_encode_maps(const LatticeView& v, int wdtype, int H, TBMaps* maps) {
+bool tb_encode_maps(const LatticeView& v, int wdtype, int W, int H, TBMaps* maps) {
     const cuuint64_t Xp = (cuuint64_t)v.Xp, Yp = (cuuint64_t)v.Yp, nz = (cuuint64_t)v.nz;
     const cuuint32_t Hb = (cuuint32_t)H;
     bool ok = true;
     {
         const cuuint64_t dims[3] = {Xp, Yp, nz};
         const cuuint64_t str[2] = {Xp * 4, Xp * Yp * 4};
-        const cuuint32_t box[3] = {(cuuint32_t)kW, Hb, 1};
-        ok = ok && encode(&maps->rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.rho_in, dims, str, box);
+        const cuuint32_t box[3] = {(cuuint32_t)W, Hb, 1};
+        ok = ok && tma_encode(&maps->rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.rho_in, dims, str, box);
         for (int a = 0, n = 0; a < 3; ++a)
-            if (v.msd_axes >> a & 1) ok = ok && encode(&maps->mu[n++], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.mu_in[a], dims, str, box);
+            if (v.msd_axes >> a & 1) ok = ok && tma_encode(&maps->mu[n++], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.mu_in[a], dims, str, box);
     }
     {
         const cuuint64_t dims[3] = {2 * Xp, Yp, nz};
         const cuuint64_t str[2] = {2 * Xp * 4, 2 * Xp * Yp * 4};
-        const cuuint32_t box[3] = {(cuuint32_t)(2 * kW), Hb, 1};
-        ok = ok && encode(&maps->m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.m_in, dims, str, box);
-        ok = ok && encode(&maps->R, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.R, dims, str, box);
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * W), Hb, 1};
+        ok = ok && tma_encode(&maps->m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.m_in, dims, str, box);
+        ok = ok && tma_encode(&maps->R, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.R, dims, str, box);
     }
     {
         const cuuint64_t e = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
         const cuuint64_t dims[4] = {Xp, Yp, nz, 6};
         const cuuint64_t str[3] = {Xp * e, Xp * Yp * e, (cuuint64_t)v.Np * e};
-        const cuuint32_t box[4] = {(cuuint32_t)kW, Hb, 1, 6};
-        ok = ok && encode(&maps->w, wdtype == LPC_WEIGHTS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+        const cuuint32_t box[4] = {(cuuint32_t)W, Hb, 1, 6};
+        ok = ok && tma_encode(&maps->w, wdtype == LPC_WEIGHTS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                           4, v.w, dims, str, box);
     }
     return ok;
 }
 
 cudaError_t tb_prepare(int wdtype, int K, int msd) {
+    if (K == 1) return t1_prepare(wdtype, msd);
     // opt in to the large dynamic shared memory once per kernel (host only,
     // called before any stream capture)
     static bool attr_set[2][5][8] = {};
@@ -542,6 +487,7 @@ cudaError_t tb_prepare(int wdtype, int K, int msd) {
 
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st) {
+    if (K == 1) return launch_tma1(v, wdtype, maps, err, st);
     TBGeom g;
     const int smem = tb_plan(v, wdtype, K, &g);
     if (smem < 0) return cudaErrorInvalidConfiguration;
@@ -557,10 +503,17 @@ cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& map
     return cudaLaunchKernel(fn, dim3(grid), dim3(kNW * 32), args, (size_t)smem, st);
 }
 
-int tb_box_rows(const LatticeView& v, int wdtype, int K) {
+bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H) {
+    if (K == 1) {                 // warp-specialised one-step kernel
+        *W = t1_box_width(v.G, wdtype);
+        *H = t1_box_rows(v, wdtype);
+        return true;
+    }
     TBGeom g;
-    if (tb_plan(v, wdtype, K, &g) < 0) return 0;
-    return g.H;
+    if (tb_plan(v, wdtype, K, &g) < 0) return false;
+    *W = kW;
+    *H = g.H;
+    return true;
 }
 
 size_t tb_maps_size() { return sizeof(TBMaps); }

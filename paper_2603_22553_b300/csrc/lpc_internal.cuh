@@ -260,8 +260,13 @@ cudaError_t launch_batch(const BatchParams& bp, int wdtype, int msd, cudaStream_
 struct TBMaps;
 bool tb_supported(const LatticeView& v, int wdtype, int K);
 cudaError_t tb_prepare(int wdtype, int K, int msd);
-bool tb_encode_maps(const LatticeView& v, int wdtype, int H, TBMaps* maps);
-int tb_box_rows(const LatticeView& v, int wdtype, int K);
+bool tb_encode_maps(const LatticeView& v, int wdtype, int W, int H, TBMaps* maps);
+bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H);
+cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
+                        cudaStream_t st);
+cudaError_t t1_prepare(int wdtype, int msd);
+int t1_box_width(int G, int wdtype);
+int t1_box_rows(const LatticeView& v, int wdtype);
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st);
 int tb_grid(const LatticeView& v, int wdtype, int K);

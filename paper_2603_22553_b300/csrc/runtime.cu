@@ -183,8 +183,9 @@ lpc_status ensure_maps(lpc_lattice* h) {
         if (!h->maps[par]) h->maps[par] = tb_maps_new();
         if (!h->maps[par]) { set_error("tensor map allocation failed"); return LPC_ERR_OOM; }
         LatticeView v = make_view(h, par);
-        const int H = tb_box_rows(v, h->p.weight_dtype, h->kdepth);
-        if (H <= 0 || !tb_encode_maps(v, h->p.weight_dtype, H, h->maps[par])) {
+        int W = 0, H = 0;
+        if (!tb_box_dims(v, h->p.weight_dtype, h->kdepth, &W, &H) ||
+            !tb_encode_maps(v, h->p.weight_dtype, W, H, h->maps[par])) {
             set_error("TMA tensor map encoding failed");
             return LPC_ERR_CUDA;
         }
@@ -243,6 +244,21 @@ lpc_status build_graph(lpc_lattice* h, int parity) {
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     h->graph_len = kGraphLen;
     return LPC_OK;
+}
+
+// Default schedule: the TMA-fed one-step kernel for lattices large enough to
+// fill its tiles, else the register-pipelined one-step kernel.
+void auto_schedule(lpc_lattice* h) {
+    const bool big = h->p.nx >= 32 && h->p.ny >= 16 && h->N >= (1LL << 18);
+    if (big && tb_supported(make_view(h, 0), h->p.weight_dtype, 1) &&
+        tb_prepare(h->p.weight_dtype, 1, h->p.msd_axes) == cudaSuccess) {
+        h->kernel = LPC_KERNEL_TB;
+        h->kdepth = 1;
+    } else {
+        h->kernel = LPC_KERNEL_STEP1;
+        h->kdepth = 1;
+    }
+    drop_graphs(h);
 }
 
 bool finite_all(const double* a, const uint8_t* solid, long long n, bool pore_only) {
@@ -309,7 +325,7 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     h->N = N;
     cudaGetDevice(&h->device);
     int G = p->ghost;
-    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 2;
+    if (G == 0) G = 2;
     h->G = G;
     h->Xp = ((p->nx + 2 * G) + 7) / 8 * 8;
     h->Yp = p->ny + 2 * G;
@@ -384,6 +400,7 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
         return st;
     }
     h->steps = 0;
+    auto_schedule(h);
     *out = h;
     return LPC_OK;
 }
@@ -397,7 +414,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     }
     const long long N = (long long)p->nx * p->ny * p->nz;
     int G = p->ghost;
-    if (G == 0) G = (p->nx >= 48 && p->ny >= 48) ? 4 : 2;
+    if (G == 0) G = 2;
     const long long Xp = ((p->nx + 2 * G) + 7) / 8 * 8, Yp = p->ny + 2 * G;
     const long long Np = Xp * Yp * p->nz;
     int na = 0;
@@ -422,15 +439,20 @@ lpc_status lattice_destroy(lpc_lattice* h) {
 
 lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps) {
     if (!h) { set_error("lattice_set_schedule: NULL handle"); return LPC_ERR_INVALID; }
-    if (kernel == LPC_KERNEL_AUTO || kernel == LPC_KERNEL_STEP1) {
+    if (kernel == LPC_KERNEL_AUTO) {
+        auto_schedule(h);
+        return LPC_OK;
+    }
+    if (kernel == LPC_KERNEL_STEP1) {
         h->kernel = LPC_KERNEL_STEP1; h->kdepth = 1;
         drop_graphs(h);
         return LPC_OK;
     }
     if (kernel == LPC_KERNEL_TB) {
         cudaSetDevice(h->device);
+        int bw = 0, bh = 0;
         if (!tb_supported(make_view(h, 0), h->p.weight_dtype, block_steps) ||
-            tb_box_rows(make_view(h, 0), h->p.weight_dtype, block_steps) <= 0) {
+            !tb_box_dims(make_view(h, 0), h->p.weight_dtype, block_steps, &bw, &bh)) {
             set_error("lattice_set_schedule: TB needs 1 <= block_steps <= min(4, ghost)");
             return LPC_ERR_INVALID;
         }

@@ -1,0 +1,114 @@
+"""Parity at the full workload sizes.
+
+* 512^3 monolith (the benchmark workload, in the schedule bench.py times):
+  after n steps the value at a site depends only on the sites within L1
+  distance n and on their hop weights, which depend on sites one further
+  out.  The FP64 oracle run on a box of half-width n + 2 around a sampled
+  site (walls on the box faces) therefore gives that site's exact value;
+  sampled sites, including ones near the periodic faces, are compared one by
+  one.  Conservation and |M| <= P(0) hold at any size.
+* Precision sweep on the 64^3 corner of the same fields, 20 000 steps: FP32
+  and BF16 hop weights against the FP64 oracle with exact weights and with
+  its own rounding of the weights; the spectrum error equals the FID error
+  (the DFT is unitary up to sqrt(N)).
+"""
+import numpy as np
+import pytest
+
+import lpc_inputs
+import oracle
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def monolith512():
+    return lpc_inputs.monolith(edge=512)
+
+
+def _box(a, z, y, x, r):
+    idx = [np.arange(c - r, c + r + 1) for c in (z, y, x)]
+    return a.take(idx[0], axis=0, mode="wrap").take(idx[1], axis=1, mode="wrap").take(idx[2], axis=2, mode="wrap")
+
+
+def test_monolith_512_sampled_sites(monolith512):
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = monolith512
+    n = 6
+    lat = Lattice.from_input(inp)          # default schedule, as benchmarked
+    lat.step(n)
+    rho = lat.density()
+    m = lat.magnetization()
+    P = lat.population()
+    M = lat.fid()
+    assert np.max(np.abs(P / P[0] - 1.0)) <= 1e-5
+    assert np.all(np.abs(M) <= P[0] * (1 + 1e-6))
+    rng = np.random.default_rng(11)
+    pts = [(0, 0, 0), (511, 511, 511), (0, 255, 511), (3, 508, 1), (256, 0, 300)]
+    pts += [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(35)]
+    r = n + 2
+    worst = 0.0
+    for (z, y, x) in pts:
+        Fb = _box(inp.F, z, y, x, r)
+        Ob = _box(inp.omega, z, y, x, r)
+        Sb = _box(inp.solid, z, y, x, r)
+        e = 2 * r + 1
+        pk = oracle.pack(e, e, e, (0, 0, 0), inp.alpha, inp.dt, inp.kT, Fb, Ob, Sb, oracle.MODE_F32)
+        res = oracle.run(pk, (Sb == 0).astype(np.float64), n, msd_axes=0)
+        ref_r = res.rho[r, r, r]
+        ref_m = res.m[r, r, r]
+        scale = max(1.0, abs(ref_r))
+        err = max(abs(rho[z, y, x] - ref_r), abs(m[z, y, x] - ref_m)) / scale
+        worst = max(worst, err)
+    assert worst <= 1e-5, worst
+    lat.close()
+
+
+def test_monolith_512_schedules_agree(monolith512):
+    """The one-step kernels (register-pipelined and TMA-fed) give bit-identical
+    states and FID within FP32 rounding at full size."""
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = monolith512
+    a = Lattice.from_input(inp)
+    a.set_schedule(B.LPC_KERNEL_TB, 1)
+    a.step(5)
+    da, ma, Ma = a.density(), a.magnetization(), a.fid()
+    a.close()
+    b = Lattice.from_input(inp)
+    b.set_schedule(B.LPC_KERNEL_STEP1, 1)
+    b.step(5)
+    assert np.array_equal(da, b.density())
+    assert np.array_equal(ma, b.magnetization())
+    assert np.allclose(Ma, b.fid(), rtol=1e-6, atol=1e-6 * abs(Ma[0]))
+    b.close()
+
+
+def test_precision_sweep_64_subvolume(monolith512):
+    """FP32 state with FP32 or BF16 weights, 20 000 steps, vs the FP64 oracle."""
+    sub = lpc_inputs.LatticeInput("monolith_sub64", 64, 64, 64, (1, 1, 1), monolith512.alpha,
+                                  monolith512.dt, monolith512.kT,
+                                  np.ascontiguousarray(monolith512.F[:64, :64, :64]),
+                                  np.ascontiguousarray(monolith512.omega[:64, :64, :64]),
+                                  np.ascontiguousarray(monolith512.solid[:64, :64, :64]), None, 20000,
+                                  0, 0)
+    steps = 20000
+    exact = H.oracle_run(sub, steps, oracle.MODE_EXACT)
+    report = {}
+    for wdt, mode in ((0, oracle.MODE_F32), (1, oracle.MODE_BF16)):
+        sub.weight_dtype = wdt
+        g = H.gpu_run(sub, steps)
+        matched = H.oracle_run(sub, steps, mode)
+        e_matched = H.rel_l2(g["M"], matched.M)
+        e_exact = H.rel_l2(g["M"], exact.M)
+        _, S_g = oracle.spectrum(g["M"], sub.dt)
+        _, S_o = oracle.spectrum(matched.M, sub.dt)
+        e_spec = H.rel_l2(S_g, S_o)
+        report[wdt] = (e_matched, e_exact, e_spec)
+        assert e_matched <= 1e-4 and e_spec <= 1e-4
+        assert H.rel_l2(g["rho"], matched.rho) <= 1e-4
+        if wdt == 0:
+            assert e_exact <= 1e-4
+        g["lattice"].close()
+    print("precision sweep (FID matched, FID exact, spectrum):", report)

@@ -30,6 +30,8 @@ CASES = [
     ((16, 20, 24), (1, 1, 1), 5, 1, 2, 4),
     ((5, 9, 13), (1, 1, 1), 0, 0, 1, 2),
     ((3, 50, 100), (0, 0, 1), 6, 1, 3, 4),
+    ((6, 7, 45), (1, 1, 1), 1, 0, 1, 2),          # depth 1, small tile shape
+    ((9, 70, 40), (1, 0, 1), 7, 1, 1, 4),         # depth 1, big tile, all moments
 ]
 
 
@@ -55,13 +57,14 @@ def test_tb_bit_identical_to_one_step(case):
     b["lattice"].close()
 
 
-@pytest.mark.parametrize("K", [2, 4])
+@pytest.mark.parametrize("K", [1, 2, 4])
 def test_tb_graph_replay_long_run(K):
     """More than 32 launches: the captured graph of TB launches is replayed."""
     inp = lpc_inputs.random_case((20, 40, 57), 310 + K, periodic=(1, 0, 1), alpha=0.5, msd_axes=1)
     steps = 70 * K + 1
-    a = _run(inp, steps, (B.LPC_KERNEL_TB, K), K)
-    b = _run(inp, steps, (B.LPC_KERNEL_STEP1, 1), K)
+    G = max(2, K)
+    a = _run(inp, steps, (B.LPC_KERNEL_TB, K), G)
+    b = _run(inp, steps, (B.LPC_KERNEL_STEP1, 1), G)
     assert np.array_equal(a["rho"], b["rho"])
     assert np.array_equal(a["m"], b["m"])
     o = H.oracle_run(inp, steps, oracle.MODE_F32)
@@ -96,7 +99,7 @@ def test_stale_allocator_memory_with_walls():
     junk = torch.full((64 << 20,), float("nan"), device="cuda")
     del junk
     inp = lpc_inputs.random_case((9, 40, 70), 102, periodic=(0, 1, 0), alpha=0.5, msd_axes=1)
-    for sched, G in (((B.LPC_KERNEL_STEP1, 1), 2), ((B.LPC_KERNEL_TB, 2), 2)):
+    for sched, G in (((B.LPC_KERNEL_STEP1, 1), 2), ((B.LPC_KERNEL_TB, 1), 2), ((B.LPC_KERNEL_TB, 2), 2)):
         junk = torch.full((64 << 20,), float("nan"), device="cuda")
         del junk
         g = _run(inp, 40, sched, G)
