@@ -169,10 +169,15 @@ def oracle_sample(inp_sub, seconds, nthreads=0):
     import oracle
     pk = oracle.pack_input(inp_sub, oracle.MODE_EXACT)
     rho0 = inp_sub.uniform_rho0()
-    t0 = time.perf_counter()
-    oracle.run(pk, rho0, 10, msd_axes=inp_sub.msd_axes, nthreads=nthreads)
-    t_probe = time.perf_counter() - t0
-    steps = max(10, int(10 * seconds / max(t_probe, 1e-3)))
+    n_probe, t_probe = 10, 0.0
+    while True:        # probe until the per-step cost is measured over >= 0.5 s
+        t0 = time.perf_counter()
+        oracle.run(pk, rho0, n_probe, msd_axes=inp_sub.msd_axes, nthreads=nthreads)
+        t_probe = time.perf_counter() - t0
+        if t_probe >= 0.5 or n_probe * inp_sub.n_sites > 1e11:
+            break
+        n_probe *= 4
+    steps = max(10, int(n_probe * seconds / max(t_probe, 1e-3)))
     t0 = time.perf_counter()
     res = oracle.run(pk, rho0, steps, msd_axes=inp_sub.msd_axes, nthreads=nthreads)
     t = time.perf_counter() - t0
