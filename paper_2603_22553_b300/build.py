@@ -33,6 +33,12 @@ def _nvcc():
     return "nvcc"
 
 
+def _extra_flags():
+    """Extra nvcc flags from LPC3D_NVCC_EXTRA (tuning macros); a change of
+    them rebuilds every object."""
+    return os.environ.get("LPC3D_NVCC_EXTRA", "").split()
+
+
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
@@ -42,7 +48,7 @@ def _compile(src, verbose=False):
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
-    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + _extra_flags() + ["-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -58,6 +64,10 @@ def build_library(verbose=False, force=False):
     """Compile and link ``liblpc3d.so``; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags = " ".join(_extra_flags())
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     if force:
         for s in srcs:
             o = os.path.join(BUILD, os.path.basename(s) + ".o")
@@ -65,6 +75,8 @@ def build_library(verbose=False, force=False):
                 os.remove(o)
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    with open(stamp, "w") as f:
+        f.write(flags)
     newest = max(os.path.getmtime(o) for o in objs)
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not force:
         return LIB

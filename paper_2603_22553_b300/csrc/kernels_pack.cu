@@ -248,6 +248,65 @@ cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const
     return cudaGetLastError();
 }
 
+namespace {
+
+// Gather form of the static data, read from the padded hop-weight planes:
+// win_k(x) = w_k(x - e_k) for the source of each of the six incoming hops
+// (plane k at the neighbour the kernels' gather reads: x-1, x+1, y-1, y+1,
+// z-1, z+1 for k = 0..5; ghosts hold the periodic images, zero behind
+// walls; z wraps, the hop across a z wall being zero), the stay weight with
+// the same FP32 sum as the step kernels, R, and the out-weight pair of every
+// MSD axis.  Positions x >= nx of the unpadded pitch get zeros.
+template <typename WT>
+__global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __restrict__ gs,
+                              float2* __restrict__ gR, float2* __restrict__ gdm) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= v.Ns) return;
+    const int x = (int)(g % v.Xs);
+    const long long t = g / v.Xs;
+    const int y = (int)(t % v.ny);
+    const int z = (int)(t / v.ny);
+    const WT* W = static_cast<const WT*>(v.w);
+    if (x >= v.nx) {
+        for (int k = 0; k < 6; ++k) win[k * v.Ns + g] = round_weight<WT>(0.0);
+        gs[g] = 0.0f;
+        gR[g] = make_float2(0.0f, 0.0f);
+        for (int a = 0; a < 3; ++a)
+            if (v.msd_axes >> a & 1) gdm[a * v.Ns + g] = make_float2(0.0f, 0.0f);
+        return;
+    }
+    const long long zplane = (long long)v.Xp * v.Yp;
+    const long long p = (long long)z * zplane + (long long)(y + v.G) * v.Xp + (x + v.G);
+    const long long pzm = p + (long long)((z == 0 ? v.nz - 1 : z - 1) - z) * zplane;
+    const long long pzp = p + (long long)((z == v.nz - 1 ? 0 : z + 1) - z) * zplane;
+    const long long src[6] = {p - 1, p + 1, p - v.Xp, p + v.Xp, pzm, pzp};
+    float wo[6];
+    for (int k = 0; k < 6; ++k) {
+        win[k * v.Ns + g] = W[k * v.Np + src[k]];
+        wo[k] = ldw<WT>(W + k * v.Np + p);
+    }
+    gs[g] = stay_weight(wo);
+    gR[g] = v.R[p];
+    for (int a = 0; a < 3; ++a)
+        if (v.msd_axes >> a & 1) gdm[a * v.Ns + g] = make_float2(wo[2 * a], wo[2 * a + 1]);
+}
+
+}  // namespace
+
+// Pitch of the gather-form arrays: rows start on 256-byte boundaries.
+int gather_pitch(int nx) { return (nx + 63) / 64 * 64; }
+
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, float2* dm,
+                               cudaStream_t st) {
+    const int B = 256;
+    const long long g = (v.Ns + B - 1) / B;
+    if (wdtype == LPC_WEIGHTS_BF16)
+        k_gather_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, static_cast<__nv_bfloat16*>(win), s, R, dm);
+    else
+        k_gather_pack<float><<<(unsigned)g, B, 0, st>>>(v, static_cast<float*>(win), s, R, dm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
                               const double* F, const uint8_t* solid, double kT, double* scratch,
                               cudaStream_t st) {

@@ -399,7 +399,7 @@ bool tma_encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* 
 static int tb_align(int wdtype) { return wdtype == LPC_WEIGHTS_BF16 ? 8 : 4; }
 
 bool tb_supported(const LatticeView& v, int wdtype, int K) {
-    if (K == 1) return v.G >= 1 && encode_fn() != nullptr;
+    if (K == 1) return t1_supported(v, wdtype);
     if (K < 1 || K > 4 || K > v.G) return false;
     const int TX = (kW - 2 * v.G) / tb_align(wdtype) * tb_align(wdtype);
     return TX >= tb_align(wdtype) && encode_fn() != nullptr;
@@ -504,11 +504,6 @@ cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& map
 }
 
 bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H) {
-    if (K == 1) {                 // warp-specialised one-step kernel
-        *W = t1_box_width(v.G, wdtype);
-        *H = t1_box_rows(v, wdtype);
-        return true;
-    }
     TBGeom g;
     if (tb_plan(v, wdtype, K, &g) < 0) return false;
     *W = kW;

@@ -1,22 +1,31 @@
 // One time step per launch fed by TMA with warp specialisation (the TB
 // schedule at block depth 1).
 //
-// A CTA owns a core tile of 32 x TY (x, y) columns (TY = NC consumer warps x
-// RPW rows per warp) and walks z-chunks of it.  A producer warp streams,
-// plane by plane, a W x (TY + 2) box (W = 32 + 2G rounded up to 16 bytes: the
-// core plus the G-wide ghost bands in x; one halo row above and below) of the
-// state (rho, m, mu), the six hop-weight planes (one 4-D box) and R into a
-// ring of S shared-memory slots with cp.async.bulk.tensor; each slot has a
-// "full" mbarrier (TMA transaction bytes) and an "empty" mbarrier (one
-// arrival per consumer warp).  Consumer warps wait for the plane above,
-// update their rows from shared memory (all six neighbours are in the ring:
-// x and y in the slot of the plane, z above from the ring and z below from
-// registers) and release the plane.  No block-wide barrier is needed inside the loop,
-// and the ring keeps up to S planes of HBM reads in flight without holding
-// registers.  Tile shapes 32 x 32, 32 x 16 (one CTA per SM) or 32 x 8 (two
-// per SM): the largest whose ring holds six planes.  Ring positions advance as
-// cursors (no divisions in the loop).  Per-site arithmetic is the shared
-// site function, so states are bit-identical to the other kernels.
+// Work items are (z-chunk, tile) pairs, tile index fastest, taken from a
+// global queue (one atomic per item) by a persistent grid of one CTA per SM,
+// so that CTAs that run slower take fewer items and neighbouring tiles are
+// in flight at the same time.  A tile is 64 x TY (x, y) sites: TY consumer
+// warps, one row each, two neighbouring x sites per lane.  An item streams
+// the planes za-1 .. zb of its z-chunk.
+//
+// A producer lane fills two rings of shared-memory slots with
+// cp.async.bulk.tensor:
+//   state  (S1 slots): rho, m, mu of one plane, W = 64 + 2G columns
+//          (rounded up to 16 bytes, from the aligned ghost column of a
+//          128-byte-aligned row) x TY + 2 rows: the x and y neighbours that
+//          the gather reads;
+//   static (S2 slots): the gather form of the static data of one plane's
+//          core (in-weights of the six incoming hops, stay weight, rotation,
+//          MSD out-weights), 64 x TY, no halo, rows on 256-byte boundaries.
+// Each slot has a "full" mbarrier (TMA transaction bytes) and an "empty"
+// mbarrier (one arrival per consumer warp); state slots carry a header with
+// the item, so the consumers follow the producer through the queue.  A
+// consumer warp waits for the static data of the centre plane and the state
+// of the plane above, updates its two sites per lane (the plane below is
+// kept in registers) and releases both.  A header with a negative tile ends
+// the launch.  Per-site arithmetic is the shared site function with the same
+// FP32 in-weights and stay weight, so states are bit-identical to the other
+// kernels.
 //
 // Every wait is bounded (clock64 budget); on expiry the kernel records
 // LPC_ERR_TIMEOUT in the lattice's error word, waits (bounded) for its
@@ -24,19 +33,21 @@
 #include "lpc_internal.cuh"
 #include "tma_ptx.cuh"
 
+#ifndef LPC_T1_MIN_DEPTH
+#define LPC_T1_MIN_DEPTH 3
+#endif
+#ifndef LPC_T1_ITEMS_PER_CTA
+#define LPC_T1_ITEMS_PER_CTA 40
+#endif
+
 namespace lpc {
 
 namespace {
 
-template <typename WT> __device__ __forceinline__ float sw(const WT* p);
-template <> __device__ __forceinline__ float sw<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float sw<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __uint_as_float(static_cast<unsigned int>(*reinterpret_cast<const unsigned short*>(p)) << 16);
-}
-
+constexpr int kTX = 64;      // core columns of a tile
 constexpr int popc(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
 
-// Position in the slot ring: slot index and the parity of its barrier phase.
+// Position in a slot ring: slot index and the parity of its barrier phase.
 struct Cursor {
     int slot;
     unsigned int ph;
@@ -45,67 +56,102 @@ struct Cursor {
     }
 };
 
+// Two consecutive in-weights in shared memory as floats.
+template <typename WT> __device__ __forceinline__ float2 lds_w2(const WT* p);
+template <> __device__ __forceinline__ float2 lds_w2<float>(const float* p) {
+    return *reinterpret_cast<const float2*>(p);
+}
+template <> __device__ __forceinline__ float2 lds_w2<__nv_bfloat16>(const __nv_bfloat16* p) {
+    const unsigned int u = *reinterpret_cast<const unsigned int*>(p);
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
 }  // namespace
 
 struct T1Geom {
-    int W, S, cz;
-    int tiles_x, tiles_y, n_items;
-    int slot_bytes, tx_bytes;
+    int W, TY, S1, S2;
+    int tiles_x, tiles, cz, n_items;
+    int slot1, slot2;           // bytes of a state / static slot
+    int tx1, tx2;               // transaction bytes of a state / static load
     unsigned int* err;
+    unsigned int* work;
 };
 
 namespace {
 
-// slot layout (each part starts on a 128-byte boundary, as TMA requires):
-//   rho [H][W] f32 | m [H][W] f32x2 | mu_n [H][W] f32 | w [6][H][W] WT |
-//   R [H][W] f32x2
-struct T1Slot {
-    int m, mu[3], w, R, bytes;
+// state slot:  rho [TY+2][W] f32 | m [TY+2][W] f32x2 | mu_n [TY+2][W] f32
+// static slot: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2 | dm_n [TY][64] f32x2
+// (each part on a 128-byte boundary, as TMA requires)
+struct T1Slots {
+    int m, mu[3], bytes1;
+    int s, R, dm[3], bytes2;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
-__host__ __device__ inline T1Slot t1_slot(int W, int H, int nmsd, int wb) {
-    T1Slot L;
-    const int HW = H * W;
-    int off = up128(HW * 4);
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb) {
+    T1Slots L;
+    const int H = TY + 2;
+    int off = up128(H * W * 4);
     L.m = off;
-    off += up128(HW * 8);
+    off += up128(H * W * 8);
     for (int n = 0; n < 3; ++n) {
         L.mu[n] = off;
-        if (n < nmsd) off += up128(HW * 4);
+        if (n < nmsd) off += up128(H * W * 4);
     }
-    L.w = off;
-    off += up128(HW * 6 * wb);
+    L.bytes1 = off;
+    const int C = TY * kTX;
+    off = up128(6 * C * wb);
+    L.s = off;
+    off += up128(C * 4);
     L.R = off;
-    off += up128(HW * 8);
-    L.bytes = off;
+    off += up128(C * 8);
+    for (int n = 0; n < 3; ++n) {
+        L.dm[n] = off;
+        if (n < nmsd) off += up128(C * 8);
+    }
+    L.bytes2 = off;
     return L;
 }
 
-template <typename WT, int MSD, int NC, int RPW>
-__global__ void __launch_bounds__((NC + 1) * 32, NC > 8 ? 1 : 2)
+struct SlotHdr {
+    int tile, za, n, pad;
+};
+
+template <typename WT, int MSD, int NC>
+__global__ void __launch_bounds__((NC + 1) * 32, 1)
 k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc(MSD);
-    constexpr int TY = NC * RPW;              // core rows
-    constexpr int H = TY + 2;                 // box rows
-    const int W = g.W, S = g.S, HW = H * W;
-    const T1Slot SL = t1_slot(W, H, NMSD, (int)sizeof(WT));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * g.slot_bytes);
-    uint64_t* empty = full + S;
-    double* red = reinterpret_cast<double*>(empty + S);          // [NC+1][kNumSums]
+    constexpr int TY = NC;                    // one core row per consumer warp
+    const int W = g.W, S1 = g.S1, S2 = g.S2;
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT));
+    unsigned char* ring1 = smem;
+    unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
+    uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
+    uint64_t* empty1 = full1 + S1;
+    uint64_t* full2 = empty1 + S1;
+    uint64_t* empty2 = full2 + S2;
+    SlotHdr* hdr = reinterpret_cast<SlotHdr*>(empty2 + S2);        // [S1]
+    double* red = reinterpret_cast<double*>(hdr + S1);             // [NC+1][kNumSums]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(red + (NC + 1) * kNumSums);
-    volatile unsigned int* issued = reinterpret_cast<volatile unsigned int*>(abort_flag + 1);
+    volatile unsigned int* issued1 = reinterpret_cast<volatile unsigned int*>(abort_flag + 1);
+    volatile unsigned int* issued2 = issued1 + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = v.G;
+    const int nz = v.nz;
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NC);
+        for (int s = 0; s < S1; ++s) {
+            mbar_init(&full1[s], 1);
+            mbar_init(&empty1[s], NC);
+        }
+        for (int s = 0; s < S2; ++s) {
+            mbar_init(&full2[s], 1);
+            mbar_init(&empty2[s], NC);
         }
         *abort_flag = 0;
-        *issued = 0;
+        *issued1 = 0;
+        *issued2 = 0;
         fence_mbar_init();
     }
     for (int i = tid; i < (NC + 1) * kNumSums; i += (NC + 1) * 32) red[i] = 0.0;
@@ -117,176 +163,225 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         for (int a = 0; a < 3; ++a)
             if (MSD >> a & 1) axis_of[n++] = a;
     }
-    const long long zplane = (long long)v.Xp * v.Yp;
 
     if (warp == NC) {
-        // ---------------- producer warp: one elected lane issues the copies
+        // ---------------- producer warp: one elected lane takes items and issues the copies
         if (lane == 0) {
             bool ok = true;
-            Cursor c{0, 0u};
-            unsigned int n_loads = 0;
-            for (int item = blockIdx.x; item < g.n_items && ok; item += gridDim.x) {
-                const int tx = item % g.tiles_x;
-                const int rest = item / g.tiles_x;
-                const int ty = rest % g.tiles_y;
-                const int zc = rest / g.tiles_y;
-                const int bx = tx * 32, by = ty * TY - 1 + G;   // box origin (padded)
-                const int z0 = zc * g.cz;
-                const int CZ = min(g.cz, v.nz - z0);
-                int z = z0 - 1 < 0 ? v.nz - 1 : z0 - 1;
-                for (int i = 0; i < CZ + 2; ++i) {
-                    // the slot's previous plane must be released by every consumer
-                    if (n_loads >= (unsigned)S) ok = mbar_wait_bounded(&empty[c.slot], c.ph ^ 1u);
-                    if (!ok || *abort_flag) { ok = false; break; }
-                    unsigned char* st = smem + (size_t)c.slot * g.slot_bytes;
-                    uint64_t* fb = &full[c.slot];
-                    fence_proxy_async();
-                    mbar_expect_tx(fb, (uint32_t)g.tx_bytes);
+            Cursor c1{0, 0u}, c2{0, 0u};
+            unsigned int n1 = 0, n2 = 0;
+            // one state load (plane z of the item) with its header
+            auto state_load = [&](int z, const SlotHdr& h, int bx, int by) -> bool {
+                if (n1 >= (unsigned)S1 && !mbar_wait_bounded(&empty1[c1.slot], c1.ph ^ 1u)) return false;
+                if (*abort_flag) return false;
+                hdr[c1.slot] = h;
+                unsigned char* st = ring1 + (size_t)c1.slot * g.slot1;
+                uint64_t* fb = &full1[c1.slot];
+                fence_proxy_async();
+                if (h.tile < 0) {
+                    mbar_arrive(fb);                  // end marker: no copy
+                } else {
+                    mbar_expect_tx(fb, (uint32_t)g.tx1);
                     tma3(st, &maps.rho, fb, bx, by, z);
                     tma3(st + SL.m, &maps.m, fb, 2 * bx, by, z);
 #pragma unroll
                     for (int n = 0; n < NMSD; ++n) tma3(st + SL.mu[n], &maps.mu[n], fb, bx, by, z);
-                    tma4(st + SL.w, &maps.w, fb, bx, by, z, 0);
-                    tma3(st + SL.R, &maps.R, fb, 2 * bx, by, z);
-                    *issued = ++n_loads;
-                    c.next(S);
-                    if (++z == v.nz) z = 0;
                 }
+                *issued1 = ++n1;
+                c1.next(S1);
+                return true;
+            };
+            for (;;) {
+                const int item = (int)atomicAdd(g.work, 1u);
+                if (item >= g.n_items) break;
+                const int tile = item % g.tiles;
+                const int za = (item / g.tiles) * g.cz;
+                const int n = min(g.cz, nz - za);
+                const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+                const int bx = tx * kTX;                 // padded column of the state box
+                const int by = ty * TY + G - 1;          // padded row of y0 - 1
+                const int sx = tx * kTX, sy = ty * TY;   // gather-form box origin
+                const SlotHdr h{tile, za, n, 0};
+                ok = state_load(za == 0 ? nz - 1 : za - 1, h, bx, by) && state_load(za, h, bx, by);
+                for (int q = 0; q < n && ok; ++q) {
+                    // static data of centre za + q, then the state of the plane above it
+                    if (n2 >= (unsigned)S2) ok = mbar_wait_bounded(&empty2[c2.slot], c2.ph ^ 1u);
+                    if (!ok || *abort_flag) { ok = false; break; }
+                    {
+                        unsigned char* st = ring2 + (size_t)c2.slot * g.slot2;
+                        uint64_t* fb = &full2[c2.slot];
+                        const int z = za + q;
+                        fence_proxy_async();
+                        mbar_expect_tx(fb, (uint32_t)g.tx2);
+                        tma4(st, &maps.gwin, fb, sx, sy, z, 0);
+                        tma3(st + SL.s, &maps.gs, fb, sx, sy, z);
+                        tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
+#pragma unroll
+                        for (int m = 0; m < NMSD; ++m) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
+                        *issued2 = ++n2;
+                        c2.next(S2);
+                    }
+                    const int za1 = za + q + 1;
+                    ok = state_load(za1 == nz ? 0 : za1, h, bx, by);
+                }
+                if (!ok) break;
             }
+            if (ok) ok = state_load(0, SlotHdr{-1, 0, 0, 0}, 0, 0);
             if (!ok) *abort_flag = 1;
         }
     } else {
-        // ---------------- consumer warps: rows warp + 1 + j*NC of the box
-        // A thread keeps its own column of the plane below in registers (the
-        // only part of that plane the update reads), so it holds just two
-        // slots (this plane and the one above) and releases a plane as soon
-        // as it has been the centre.
+        // ---------------- consumer warps: core row `warp`, sites x0 + 2 lane + {0, 1}
         float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool ok = true;
-        Cursor wait_c{0, 0u};          // next load to wait for
-        for (int item = blockIdx.x; item < g.n_items && ok; item += gridDim.x) {
-            const int tx = item % g.tiles_x;
-            const int rest = item / g.tiles_x;
-            const int ty = rest % g.tiles_y;
-            const int zc = rest / g.tiles_y;
-            const int x = tx * 32 + lane;
-            const int z0 = zc * g.cz;
-            const int CZ = min(g.cz, v.nz - z0);
-            // per-row facts of this item
-            bool site[RPW], inner[RPW];
-            int y[RPW], o[RPW];
-            long long col[RPW];
-#pragma unroll
-            for (int j = 0; j < RPW; ++j) {
-                y[j] = ty * TY + warp + j * NC;
-                site[j] = x < v.nx && y[j] < v.ny;
-                inner[j] = x >= G && x < v.nx - G && y[j] >= G && y[j] < v.ny - G;
-                col[j] = (long long)(y[j] + G) * v.Xp + (x + G) + (long long)z0 * zplane;
-                o[j] = (warp + 1 + j * NC) * W + G + lane;
-            }
-            // plane 0 of the item: keep this thread's column as "below"
-            float br[RPW], bw4[RPW], bmu[RPW][3];
-            float2 bm[RPW];
-            ok = mbar_wait_bounded(&full[wait_c.slot], wait_c.ph);
+        Cursor w1{0, 0u}, w2{0, 0u};
+        const int o = (warp + 1) * W + G + 2 * lane;     // site 0 in the state arrays
+        const int os = warp * kTX + 2 * lane;            // site 0 in the static arrays
+        const int C = TY * kTX;
+        const long long zplane = (long long)v.Xp * v.Yp;
+        for (;;) {
+            ok = mbar_wait_bounded(&full1[w1.slot], w1.ph);
             if (!ok) break;
+            const SlotHdr h = hdr[w1.slot];
+            if (h.tile < 0) break;                       // end of the queue
+            const int tx = h.tile % g.tiles_x, ty = h.tile / g.tiles_x;
+            const int x = tx * kTX + 2 * lane;
+            const int y = ty * TY + warp;
+            const bool ok_y = y < v.ny;
+            const bool site0 = ok_y && x < v.nx;
+            const bool site1 = ok_y && x + 1 < v.nx;
+            const bool inner = x >= G && x + 1 < v.nx - G && y >= G && y < v.ny - G;
+            const long long col = (long long)(y + G) * v.Xp + (x + G);
+            // plane za-1: keep this lane's two columns as "below"
+            float2 br, bmu[3];
+            float4 bm;
             {
-                const unsigned char* s0 = smem + (size_t)wait_c.slot * g.slot_bytes;
+                const unsigned char* s0 = ring1 + (size_t)w1.slot * g.slot1;
+                br = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(s0) + o);
+                bm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(s0 + SL.m) + o);
 #pragma unroll
-                for (int j = 0; j < RPW; ++j) {
-                    br[j] = reinterpret_cast<const float*>(s0)[o[j]];
-                    bm[j] = reinterpret_cast<const float2*>(s0 + SL.m)[o[j]];
-                    bw4[j] = sw<WT>(reinterpret_cast<const WT*>(s0 + SL.w) + 4 * HW + o[j]);
-#pragma unroll
-                    for (int n = 0; n < NMSD; ++n) bmu[j][n] = reinterpret_cast<const float*>(s0 + SL.mu[n])[o[j]];
-                }
+                for (int n = 0; n < NMSD; ++n)
+                    bmu[n] = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(s0 + SL.mu[n]) + o);
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[wait_c.slot]);
-                wait_c.next(S);
+                if (lane == 0) mbar_arrive(&empty1[w1.slot]);
+                w1.next(S1);
             }
-            // plane 1: the first centre
-            ok = mbar_wait_bounded(&full[wait_c.slot], wait_c.ph);
-            int center = wait_c.slot;
-            wait_c.next(S);
-            for (int q = 0; q < CZ && ok; ++q) {
-                const int above = wait_c.slot;
-                ok = mbar_wait_bounded(&full[above], wait_c.ph);
-                wait_c.next(S);
+            // plane za: the first centre
+            ok = mbar_wait_bounded(&full1[w1.slot], w1.ph);
+            int center = w1.slot;
+            w1.next(S1);
+            for (int q = 0; q < h.n && ok; ++q) {
+                const int z = h.za + q;
+                const int sslot = w2.slot;
+                ok = mbar_wait_bounded(&full2[sslot], w2.ph);
+                w2.next(S2);
+                const int above = w1.slot;
+                ok = ok && mbar_wait_bounded(&full1[above], w1.ph);
+                w1.next(S1);
                 if (!ok || *abort_flag) { ok = false; break; }
-                const unsigned char* sc = smem + (size_t)center * g.slot_bytes;
-                const unsigned char* sa_ = smem + (size_t)above * g.slot_bytes;
+                const unsigned char* sc = ring1 + (size_t)center * g.slot1;
+                const unsigned char* sv = ring1 + (size_t)above * g.slot1;
+                const unsigned char* ss = ring2 + (size_t)sslot * g.slot2;
                 const float* rc = reinterpret_cast<const float*>(sc);
-                const float* ra = reinterpret_cast<const float*>(sa_);
                 const float2* mc = reinterpret_cast<const float2*>(sc + SL.m);
-                const float2* ma = reinterpret_cast<const float2*>(sa_ + SL.m);
-                const WT* wc = reinterpret_cast<const WT*>(sc + SL.w);
-                const WT* wa = reinterpret_cast<const WT*>(sa_ + SL.w);
-                const float2* Rc = reinterpret_cast<const float2*>(sc + SL.R);
+                const float2 r_c = *reinterpret_cast<const float2*>(rc + o);
+                const float4 m_c = *reinterpret_cast<const float4*>(mc + o);
+                const float r_l = rc[o - 1], r_r = rc[o + 2];
+                const float2 r_u = *reinterpret_cast<const float2*>(rc + o - W);
+                const float2 r_d = *reinterpret_cast<const float2*>(rc + o + W);
+                const float2 r_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv) + o);
+                const float2 m_l = mc[o - 1], m_r = mc[o + 2];
+                const float4 m_u = *reinterpret_cast<const float4*>(mc + o - W);
+                const float4 m_d = *reinterpret_cast<const float4*>(mc + o + W);
+                const float4 m_a = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(sv + SL.m) + o);
+                const WT* win = reinterpret_cast<const WT*>(ss);
+                const float2 sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
+                const float4 Rp = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.R) + os);
+                float2 muc[3];
 #pragma unroll
-                for (int j = 0; j < RPW; ++j) {
-                    const int oj = o[j];
-                    SiteIn qi;
-                    float wo[6];
+                for (int n = 0; n < NMSD; ++n)
+                    muc[n] = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sc + SL.mu[n]) + o);
+
+                SiteIn q0, q1;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) wo[k] = sw<WT>(wc + k * HW + oj);
-                    qi.rc = rc[oj];
-                    qi.mc = mc[oj];
-                    float muc[3];
-#pragma unroll
-                    for (int n = 0; n < NMSD; ++n) muc[n] = reinterpret_cast<const float*>(sc + SL.mu[n])[oj];
-                    if (site[j]) {
-                        qi.r[0] = rc[oj - 1];  qi.m[0] = mc[oj - 1];  qi.win[0] = sw<WT>(wc + 0 * HW + oj - 1);
-                        qi.r[1] = rc[oj + 1];  qi.m[1] = mc[oj + 1];  qi.win[1] = sw<WT>(wc + 1 * HW + oj + 1);
-                        qi.r[2] = rc[oj - W];  qi.m[2] = mc[oj - W];  qi.win[2] = sw<WT>(wc + 2 * HW + oj - W);
-                        qi.r[3] = rc[oj + W];  qi.m[3] = mc[oj + W];  qi.win[3] = sw<WT>(wc + 3 * HW + oj + W);
-                        qi.r[4] = br[j];       qi.m[4] = bm[j];       qi.win[4] = bw4[j];
-                        qi.r[5] = ra[oj];      qi.m[5] = ma[oj];      qi.win[5] = sw<WT>(wa + 5 * HW + oj);
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) qi.wout[k] = wo[k];
-                        qi.R = Rc[oj];
-                        const float s_ = stay_weight(wo);
-                        float ro;
-                        float2 mo;
-                        site_rho_m(qi, s_, ro, mo);
-                        const long long zoff = (long long)(z0 + q) * zplane;
-                        if (inner[j]) {
-                            const long long p = col[j] + (long long)q * zplane;
-                            v.rho_out[p] = ro;
-                            v.m_out[p] = mo;
-                        } else {
-                            store_images(v.rho_out, v, x, y[j], zoff, ro);
-                            store_images(v.m_out, v, x, y[j], zoff, mo);
-                        }
-                        part[0] += mo.x;
-                        part[1] += mo.y;
-                        part[2] += ro;
-#pragma unroll
-                        for (int n = 0; n < NMSD; ++n) {
-                            const int a = axis_of[n];
-                            const float* uc = reinterpret_cast<const float*>(sc + SL.mu[n]);
-                            const float* ua = reinterpret_cast<const float*>(sa_ + SL.mu[n]);
-                            const float nb[6] = {uc[oj - 1], uc[oj + 1], uc[oj - W], uc[oj + W], bmu[j][n], ua[oj]};
-                            const float muo = site_mu(qi.win, qi.r, nb, s_, muc[n], a);
-                            store_images(v.mu_out[a], v, x, y[j], zoff, muo);
-                            part[3 + a] += site_dmsd(wo, muc[n], qi.rc, a);
-                        }
-                    }
-                    // this plane is the next one's "below"
-                    br[j] = qi.rc;
-                    bm[j] = qi.mc;
-                    bw4[j] = wo[4];
-#pragma unroll
-                    for (int n = 0; n < NMSD; ++n) bmu[j][n] = muc[n];
+                for (int k = 0; k < 6; ++k) {
+                    const float2 wk = lds_w2<WT>(win + k * C + os);
+                    q0.win[k] = wk.x;
+                    q1.win[k] = wk.y;
                 }
-                // the centre plane is no longer needed by this warp
+                q0.r[0] = r_l;   q0.r[1] = r_c.y; q0.r[2] = r_u.x; q0.r[3] = r_d.x; q0.r[4] = br.x; q0.r[5] = r_a.x;
+                q1.r[0] = r_c.x; q1.r[1] = r_r;   q1.r[2] = r_u.y; q1.r[3] = r_d.y; q1.r[4] = br.y; q1.r[5] = r_a.y;
+                q0.m[0] = m_l;                         q1.m[0] = make_float2(m_c.x, m_c.y);
+                q0.m[1] = make_float2(m_c.z, m_c.w);   q1.m[1] = m_r;
+                q0.m[2] = make_float2(m_u.x, m_u.y);   q1.m[2] = make_float2(m_u.z, m_u.w);
+                q0.m[3] = make_float2(m_d.x, m_d.y);   q1.m[3] = make_float2(m_d.z, m_d.w);
+                q0.m[4] = make_float2(bm.x, bm.y);     q1.m[4] = make_float2(bm.z, bm.w);
+                q0.m[5] = make_float2(m_a.x, m_a.y);   q1.m[5] = make_float2(m_a.z, m_a.w);
+                q0.rc = r_c.x; q0.mc = make_float2(m_c.x, m_c.y); q0.R = make_float2(Rp.x, Rp.y);
+                q1.rc = r_c.y; q1.mc = make_float2(m_c.z, m_c.w); q1.R = make_float2(Rp.z, Rp.w);
+                float ro0, ro1;
+                float2 mo0, mo1;
+                site_rho_m(q0, sp.x, ro0, mo0);
+                site_rho_m(q1, sp.y, ro1, mo1);
+                float muo0[3], muo1[3];
+#pragma unroll
+                for (int n = 0; n < NMSD; ++n) {
+                    const int a = axis_of[n];
+                    const float* uc = reinterpret_cast<const float*>(sc + SL.mu[n]);
+                    const float2 u_u = *reinterpret_cast<const float2*>(uc + o - W);
+                    const float2 u_d = *reinterpret_cast<const float2*>(uc + o + W);
+                    const float2 u_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv + SL.mu[n]) + o);
+                    const float4 dm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.dm[n]) + os);
+                    const float nb0[6] = {uc[o - 1], muc[n].y, u_u.x, u_d.x, bmu[n].x, u_a.x};
+                    const float nb1[6] = {muc[n].x, uc[o + 2], u_u.y, u_d.y, bmu[n].y, u_a.y};
+                    muo0[n] = site_mu(q0.win, q0.r, nb0, sp.x, muc[n].x, a);
+                    muo1[n] = site_mu(q1.win, q1.r, nb1, sp.y, muc[n].y, a);
+                    float wo0[6], wo1[6];
+                    wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
+                    wo1[2 * a] = dm.z; wo1[2 * a + 1] = dm.w;
+                    if (site0) part[3 + a] += site_dmsd(wo0, muc[n].x, q0.rc, a);
+                    if (site1) part[3 + a] += site_dmsd(wo1, muc[n].y, q1.rc, a);
+                }
+                // both slots are read: release them before the stores
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[center]);
+                if (lane == 0) {
+                    mbar_arrive(&empty1[center]);
+                    mbar_arrive(&empty2[sslot]);
+                }
+                if (inner) {
+                    const long long p = col + (long long)z * zplane;
+                    *reinterpret_cast<float2*>(v.rho_out + p) = make_float2(ro0, ro1);
+                    *reinterpret_cast<float4*>(v.m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
+#pragma unroll
+                    for (int n = 0; n < NMSD; ++n)
+                        *reinterpret_cast<float2*>(v.mu_out[axis_of[n]] + p) = make_float2(muo0[n], muo1[n]);
+                } else {
+                    const long long zoff = (long long)z * zplane;
+                    if (site0) {
+                        store_images(v.rho_out, v, x, y, zoff, ro0);
+                        store_images(v.m_out, v, x, y, zoff, mo0);
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo0[n]);
+                    }
+                    if (site1) {
+                        store_images(v.rho_out, v, x + 1, y, zoff, ro1);
+                        store_images(v.m_out, v, x + 1, y, zoff, mo1);
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x + 1, y, zoff, muo1[n]);
+                    }
+                }
+                if (site0) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
+                if (site1) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
+                // this plane is the next one's "below"
+                br = r_c;
+                bm = m_c;
+#pragma unroll
+                for (int n = 0; n < NMSD; ++n) bmu[n] = muc[n];
                 center = above;
             }
-            if (ok) {
-                // release the last plane of the item (loaded as the final "above")
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[center]);
-            }
+            if (!ok) break;
+            // release the last plane of the item (loaded as the final "above")
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty1[center]);
         }
         if (!ok) *abort_flag = 1;
         // per-warp FP64 sums (one butterfly per quantity for the whole launch)
@@ -301,10 +396,12 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     if (*abort_flag) {
         if (tid == 0) {
             atomicExch(g.err, (unsigned int)LPC_ERR_TIMEOUT);
-            // wait (bounded) until the copies of the last S issued loads landed
-            const unsigned int n_issued = *issued;
-            for (unsigned int l = n_issued > (unsigned)S ? n_issued - S : 0; l < n_issued; ++l)
-                mbar_wait_bounded(&full[l % S], (l / S) & 1u);
+            // wait (bounded) until the copies of the last issued loads of both rings landed
+            const unsigned int m1 = *issued1, m2 = *issued2;
+            for (unsigned int l = m1 > (unsigned)S1 ? m1 - S1 : 0; l < m1; ++l)
+                mbar_wait_bounded(&full1[l % S1], (l / S1) & 1u);
+            for (unsigned int l = m2 > (unsigned)S2 ? m2 - S2 : 0; l < m2; ++l)
+                mbar_wait_bounded(&full2[l % S2], (l / S2) & 1u);
         }
         __syncthreads();
         return;
@@ -312,129 +409,177 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     block_finish_smem<NC + 1>(v, 1, red);
 }
 
-template <typename WT, int MSD, int NC, int RPW>
-void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, RPW>); }
+template <typename WT, int MSD, int NC>
+void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC>); }
 
-template <int NC, int RPW>
+template <int NC>
 void* t1_kernel_shape(int wdtype, int msd) {
     static void* tab[2][8] = {
-        {t1_fn<float, 0, NC, RPW>(), t1_fn<float, 1, NC, RPW>(), t1_fn<float, 2, NC, RPW>(),
-         t1_fn<float, 3, NC, RPW>(), t1_fn<float, 4, NC, RPW>(), t1_fn<float, 5, NC, RPW>(),
-         t1_fn<float, 6, NC, RPW>(), t1_fn<float, 7, NC, RPW>()},
-        {t1_fn<__nv_bfloat16, 0, NC, RPW>(), t1_fn<__nv_bfloat16, 1, NC, RPW>(),
-         t1_fn<__nv_bfloat16, 2, NC, RPW>(), t1_fn<__nv_bfloat16, 3, NC, RPW>(),
-         t1_fn<__nv_bfloat16, 4, NC, RPW>(), t1_fn<__nv_bfloat16, 5, NC, RPW>(),
-         t1_fn<__nv_bfloat16, 6, NC, RPW>(), t1_fn<__nv_bfloat16, 7, NC, RPW>()}};
+        {t1_fn<float, 0, NC>(), t1_fn<float, 1, NC>(), t1_fn<float, 2, NC>(), t1_fn<float, 3, NC>(),
+         t1_fn<float, 4, NC>(), t1_fn<float, 5, NC>(), t1_fn<float, 6, NC>(), t1_fn<float, 7, NC>()},
+        {t1_fn<__nv_bfloat16, 0, NC>(), t1_fn<__nv_bfloat16, 1, NC>(), t1_fn<__nv_bfloat16, 2, NC>(),
+         t1_fn<__nv_bfloat16, 3, NC>(), t1_fn<__nv_bfloat16, 4, NC>(), t1_fn<__nv_bfloat16, 5, NC>(),
+         t1_fn<__nv_bfloat16, 6, NC>(), t1_fn<__nv_bfloat16, 7, NC>()}};
     return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
 }
 
-// Tile shapes (consumer warps x rows per warp): 16 x 2 (32 x 32 core) or
-// 16 x 1 (32 x 16 core) with one CTA per SM, and 8 x 1 (32 x 8 core) with two
-// CTAs per SM.  The largest shape whose ring holds at least kMinSlots planes
-// is used.
-constexpr int kMinSlots = 6;
+// Tile heights (= consumer warps) tried in order; the first whose rings keep
+// at least LPC_T1_MIN_DEPTH planes in flight is used (the last one always).
+constexpr int kShapes[3] = {16, 12, 8};
 
 struct T1Choice {
-    int shape;                 // 0: 16 x 2, 1: 16 x 1, 2: 8 x 1
-    int W, H, S, slot_bytes, smem;
+    int TY, W, S1, S2, depth;
+    T1Slots L;
+    int smem;
 };
 
-}  // namespace
+// Box width of the state: the 64 core columns plus G on each side, rounded
+// up to 16 bytes.
+int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 
-// Box width of the depth-1 kernel: the 32 core columns plus G on each side,
-// rounded up to 16 bytes of the narrowest element (4 FP32, 8 BF16 weights).
-int t1_box_width(int G, int wdtype) {
-    const int a = wdtype == LPC_WEIGHTS_BF16 ? 8 : 4;
-    return (32 + 2 * G + a - 1) / a * a;
-}
-
-static T1Choice t1_choose(const LatticeView& v, int wdtype) {
-    const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+T1Choice t1_choose(const LatticeView& v, int wdtype) {
     const int nmsd = popc(v.msd_axes);
-    T1Choice c;
-    c.W = t1_box_width(v.G, wdtype);
-    const int fixed = 128 + 2048 + 16;
-    const int rows[3] = {32, 16, 8};
-    const int per_sm[3] = {1, 1, 2};
-    for (int shape = 0; shape < 3; ++shape) {
-        const int H = rows[shape] + 2;
-        const int sb = t1_slot(c.W, H, nmsd, wb).bytes;
-        int S = (device_props().max_smem_optin / per_sm[shape] - fixed) / (sb + 16);
-        if (S > 8) S = 8;
-        const bool last = shape == 2;
-        if ((S >= kMinSlots && v.ny > rows[shape] / 2) || last) {
-            if (S < 4) S = 4;
-            c.shape = shape;
-            c.H = H;
-            c.S = S;
-            c.slot_bytes = sb;
-            c.smem = fixed + S * (sb + 16);
+    const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    T1Choice c{};
+    c.W = t1_box_width(v.G);
+    for (int i = 0; i < 3; ++i) {
+        const int TY = kShapes[i];
+        const T1Slots L = t1_slots(c.W, TY, nmsd, wb);
+        const int fixed = 128 + (TY + 1) * kNumSums * 8 + 64;
+        const int budget = device_props().max_smem_optin - 1024 - fixed;
+        // depth d: S1 = d + 2 state slots (centre and above held), S2 = d + 1
+        // static slots (centre held); per slot one full and one empty barrier,
+        // and a header per state slot
+        const int per1 = L.bytes1 + 16 + 16, per2 = L.bytes2 + 16;
+        int d = (budget - 2 * per1 - per2) / (per1 + per2);
+        if (d > 8) d = 8;
+        if ((d >= LPC_T1_MIN_DEPTH && v.ny > TY / 2) || i == 2) {
+            c.TY = TY;
+            c.depth = d;
+            c.S1 = d + 2;
+            c.S2 = d + 1;
+            c.L = L;
+            c.smem = fixed + c.S1 * per1 + c.S2 * per2;
             return c;
         }
     }
     return c;
 }
 
-int t1_box_rows(const LatticeView& v, int wdtype) { return t1_choose(v, wdtype).H; }
-
-static void* t1_kernel(const T1Choice& c, int wdtype, int msd) {
-    if (c.shape == 0) return t1_kernel_shape<16, 2>(wdtype, msd);
-    if (c.shape == 1) return t1_kernel_shape<16, 1>(wdtype, msd);
-    return t1_kernel_shape<8, 1>(wdtype, msd);
+void* t1_kernel(int TY, int wdtype, int msd) {
+    if (TY == 16) return t1_kernel_shape<16>(wdtype, msd);
+    if (TY == 12) return t1_kernel_shape<12>(wdtype, msd);
+    return t1_kernel_shape<8>(wdtype, msd);
 }
+
+}  // namespace
 
 cudaError_t t1_prepare(int wdtype, int msd) {
     static bool done[2][8] = {};
     bool& d = done[wdtype == LPC_WEIGHTS_BF16][msd & 7];
     if (d) return cudaSuccess;
-    void* fns[3] = {t1_kernel_shape<16, 2>(wdtype, msd), t1_kernel_shape<16, 1>(wdtype, msd),
-                    t1_kernel_shape<8, 1>(wdtype, msd)};
-    const int limit[3] = {device_props().max_smem_optin, device_props().max_smem_optin,
-                          device_props().max_smem_optin / 2};
     for (int i = 0; i < 3; ++i) {
+        void* fn = t1_kernel(kShapes[i], wdtype, msd);
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, fns[i]);
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 limit[i] - (int)fa.sharedSizeBytes);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 device_props().max_smem_optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
     }
     d = true;
     return cudaSuccess;
 }
 
+bool t1_supported(const LatticeView& v, int wdtype) {
+    const T1Choice c = t1_choose(v, wdtype);
+    return v.G >= 2 && v.G % 2 == 0 && encode_fn() != nullptr && c.depth >= 1;
+}
+
+bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
+    if (!v.gwin) return false;
+    const T1Choice c = t1_choose(v, wdtype);
+    const cuuint64_t Xp = (cuuint64_t)v.Xp, Yp = (cuuint64_t)v.Yp, nz = (cuuint64_t)v.nz;
+    const cuuint32_t W = (cuuint32_t)c.W, TY = (cuuint32_t)c.TY;
+    bool ok = true;
+    {
+        const cuuint64_t dims[3] = {Xp, Yp, nz};
+        const cuuint64_t str[2] = {Xp * 4, Xp * Yp * 4};
+        const cuuint32_t box[3] = {W, TY + 2, 1};
+        ok = ok && tma_encode(&maps->rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.rho_in, dims, str, box);
+        for (int a = 0, n = 0; a < 3; ++a)
+            if (v.msd_axes >> a & 1)
+                ok = ok && tma_encode(&maps->mu[n++], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.mu_in[a], dims, str, box);
+    }
+    {
+        const cuuint64_t dims[3] = {2 * Xp, Yp, nz};
+        const cuuint64_t str[2] = {Xp * 8, Xp * Yp * 8};
+        const cuuint32_t box[3] = {2 * W, TY + 2, 1};
+        ok = ok && tma_encode(&maps->m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.m_in, dims, str, box);
+    }
+    {
+        const cuuint64_t Xs = (cuuint64_t)v.Xs, ny = (cuuint64_t)v.ny;
+        const cuuint64_t e = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+        const CUtensorMapDataType dt =
+            wdtype == LPC_WEIGHTS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        const cuuint64_t dw[4] = {Xs, ny, nz, 6};
+        const cuuint64_t sw[3] = {Xs * e, Xs * ny * e, Xs * ny * nz * e};
+        const cuuint32_t bw[4] = {(cuuint32_t)kTX, TY, 1, 6};
+        ok = ok && tma_encode(&maps->gwin, dt, 4, v.gwin, dw, sw, bw);
+        const cuuint64_t ds[3] = {Xs, ny, nz};
+        const cuuint64_t ss[2] = {Xs * 4, Xs * ny * 4};
+        const cuuint32_t bs[3] = {(cuuint32_t)kTX, TY, 1};
+        ok = ok && tma_encode(&maps->gs, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gs, ds, ss, bs);
+        const cuuint64_t dr[3] = {2 * Xs, ny, nz};
+        const cuuint64_t sr[2] = {Xs * 8, Xs * ny * 8};
+        const cuuint32_t br[3] = {(cuuint32_t)(2 * kTX), TY, 1};
+        ok = ok && tma_encode(&maps->gR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gR, dr, sr, br);
+        if (v.msd_axes) {
+            const cuuint64_t dd[4] = {2 * Xs, ny, nz, 3};
+            const cuuint64_t sd[3] = {Xs * 8, Xs * ny * 8, Xs * ny * nz * 8};
+            const cuuint32_t bd[4] = {(cuuint32_t)(2 * kTX), TY, 1, 1};
+            ok = ok && tma_encode(&maps->gdm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.gdm, dd, sd, bd);
+        }
+    }
+    return ok;
+}
+
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st) {
+    if (!v.gwin) return cudaErrorInvalidValue;
     const T1Choice c = t1_choose(v, wdtype);
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
-    const int NC = c.shape == 2 ? 8 : 16;
-    const int TY = c.shape == 0 ? 32 : (c.shape == 1 ? 16 : 8);
     T1Geom g;
     g.W = c.W;
-    g.S = c.S;
-    g.slot_bytes = c.slot_bytes;
-    g.tx_bytes = c.H * c.W * (4 + 8 + 4 * nmsd + 6 * wb + 8);   // the boxes (padding not written)
-    g.tiles_x = (v.nx + 31) / 32;
-    g.tiles_y = (v.ny + TY - 1) / TY;
-    const long long xy = (long long)g.tiles_x * g.tiles_y;
-    const int ctas = device_props().sm_count * (c.shape == 2 ? 2 : 1);
-    const long long nchunks = (4LL * ctas + xy - 1) / xy;     // ~4 items per CTA
-    int cz = (int)((v.nz + nchunks - 1) / nchunks);
+    g.TY = c.TY;
+    g.S1 = c.S1;
+    g.S2 = c.S2;
+    g.slot1 = c.L.bytes1;
+    g.slot2 = c.L.bytes2;
+    g.tx1 = (c.TY + 2) * c.W * (12 + 4 * nmsd);
+    g.tx2 = c.TY * kTX * (6 * wb + 4 + 8 + 8 * nmsd);
+    g.tiles_x = (v.nx + kTX - 1) / kTX;
+    g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
+    const int sms = device_props().sm_count;
+    long long cz = (long long)g.tiles * v.nz / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
     if (cz < 16) cz = 16;
     if (cz > v.nz) cz = v.nz;
-    g.cz = cz;
-    g.n_items = (int)(xy * ((v.nz + cz - 1) / cz));
+    g.cz = (int)cz;
+    g.n_items = g.tiles * ((v.nz + g.cz - 1) / g.cz);
     g.err = err;
+    g.work = err + 7;
     cudaError_t e = t1_prepare(wdtype, v.msd_axes);
     if (e != cudaSuccess) return e;
-    int grid = ctas;
+    e = cudaMemsetAsync(g.work, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int grid = sms;
     if (grid > g.n_items) grid = g.n_items;
     LatticeView vv = v;
     TBMaps mm = maps;
     void* args[] = {&mm, &vv, &g};
-    return cudaLaunchKernel(t1_kernel(c, wdtype, v.msd_axes), dim3(grid), dim3((NC + 1) * 32), args,
-                            (size_t)c.smem, st);
+    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes), dim3((unsigned)grid), dim3((c.TY + 1) * 32),
+                            args, (size_t)c.smem, st);
 }
 
 }  // namespace lpc

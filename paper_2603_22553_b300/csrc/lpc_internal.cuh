@@ -43,6 +43,14 @@ struct LatticeView {
     float* mu_out[3];
     const void* w;                   // [6][Np] float or bf16
     const float2* R;                 // [Np]
+    // gather form of the static data (one-step TMA kernel), unpadded rows of
+    // pitch Xs (a multiple of 64), Ns = Xs * ny * nz; null until first used
+    const void* gwin;                // [6][Ns] in-weights win_k(x) = w_k(x - e_k), float or bf16
+    const float* gs;                 // [Ns] stay weight 1 - sum_k w_k(x)
+    const float2* gR;                // [Ns] rotation
+    const float2* gdm;               // [3][Ns] (w_+a(x), w_-a(x)) for the MSD axes
+    int Xs;
+    long long Ns;
     // reductions: per-block partials, completion counter, history
     double* partials;                // [levels][grid][kNumSums]
     unsigned int* counter;
@@ -262,11 +270,16 @@ bool tb_supported(const LatticeView& v, int wdtype, int K);
 cudaError_t tb_prepare(int wdtype, int K, int msd);
 bool tb_encode_maps(const LatticeView& v, int wdtype, int W, int H, TBMaps* maps);
 bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H);
+// err points into the lattice's counter block: err[0] is the error word,
+// err[7] the one-step TMA kernel's work-queue counter (reset per launch).
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st);
 cudaError_t t1_prepare(int wdtype, int msd);
-int t1_box_width(int G, int wdtype);
-int t1_box_rows(const LatticeView& v, int wdtype);
+bool t1_supported(const LatticeView& v, int wdtype);
+bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
+int gather_pitch(int nx);
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, float2* dm,
+                               cudaStream_t st);
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st);
 int tb_grid(const LatticeView& v, int wdtype, int K);

@@ -77,6 +77,13 @@ struct lpc_lattice {
     int kdepth = 1;
     TBMaps* maps[2] = {nullptr, nullptr};   // TMA tensor maps per input parity
     int maps_K = 0;
+    // gather form of the static data (one-step TMA kernel), made on first use
+    void* gwin = nullptr;
+    float* gs = nullptr;
+    float2* gR = nullptr;
+    float2* gdm = nullptr;
+    int Xs = 0;
+    long long Ns = 0;
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -137,6 +144,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     v.rho_out = h->rho[in ^ 1]; v.m_out = h->m[in ^ 1];
     for (int a = 0; a < 3; ++a) { v.mu_in[a] = h->mu[in][a]; v.mu_out[a] = h->mu[in ^ 1][a]; }
     v.w = h->w; v.R = h->R;
+    v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.Xs = h->Xs; v.Ns = h->Ns;
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
     return v;
@@ -177,15 +185,50 @@ lpc_status ensure_history(lpc_lattice* h, long long needed) {
     return LPC_OK;
 }
 
+// win (6 planes), s, R and, with any MSD axis, one (w+a, w-a) plane per axis
+size_t gather_bytes(long long Ns, int wdtype, int msd) {
+    return (size_t)Ns * (6 * (wdtype == LPC_WEIGHTS_BF16 ? 2 : 4) + 4 + 8 + (msd ? 3 * 8 : 0));
+}
+
+// The gather-form static arrays: allocated and filled once (outside any
+// stream capture), from the padded weight planes.
+lpc_status ensure_gather(lpc_lattice* h) {
+    if (h->gwin) return LPC_OK;
+    const int Xs = gather_pitch(h->p.nx);
+    const long long Ns = (long long)Xs * h->p.ny * h->p.nz;
+    char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, h->p.msd_axes));
+    if (!blk) { set_error("gather-form allocation failed"); return LPC_ERR_OOM; }
+    h->Xs = Xs;
+    h->Ns = Ns;
+    h->gwin = blk;
+    blk += (size_t)Ns * 6 * wbytes(h);
+    h->gs = (float*)blk;
+    blk += (size_t)Ns * 4;
+    h->gR = (float2*)blk;
+    blk += (size_t)Ns * 8;
+    h->gdm = h->p.msd_axes ? (float2*)blk : nullptr;     // [3][Ns], indexed by axis
+    LatticeView v = make_view(h, h->cur);
+    cudaError_t e = launch_gather_pack(v, h->p.weight_dtype, h->gwin, h->gs, h->gR, h->gdm, h->wstream);
+    if (e != cudaSuccess) return cuda_fail(e, "gather pack");
+    return LPC_OK;
+}
+
 lpc_status ensure_maps(lpc_lattice* h) {
+    if (h->kdepth == 1) {
+        lpc_status g = ensure_gather(h);
+        if (g != LPC_OK) return g;
+    }
     if (h->maps[0] && h->maps_K == h->kdepth) return LPC_OK;
     for (int par = 0; par < 2; ++par) {
         if (!h->maps[par]) h->maps[par] = tb_maps_new();
         if (!h->maps[par]) { set_error("tensor map allocation failed"); return LPC_ERR_OOM; }
         LatticeView v = make_view(h, par);
         int W = 0, H = 0;
-        if (!tb_box_dims(v, h->p.weight_dtype, h->kdepth, &W, &H) ||
-            !tb_encode_maps(v, h->p.weight_dtype, W, H, h->maps[par])) {
+        const bool ok = h->kdepth == 1
+                            ? t1_encode_maps(v, h->p.weight_dtype, h->maps[par])
+                            : tb_box_dims(v, h->p.weight_dtype, h->kdepth, &W, &H) &&
+                                  tb_encode_maps(v, h->p.weight_dtype, W, H, h->maps[par]);
+        if (!ok) {
             set_error("TMA tensor map encoding failed");
             return LPC_ERR_CUDA;
         }
@@ -196,14 +239,14 @@ lpc_status ensure_maps(lpc_lattice* h) {
 
 // One launch: a TB block of kdepth steps (tb = true) or one step.
 lpc_status launch_one(lpc_lattice* h, cudaStream_t st, bool tb = false) {
-    LatticeView v = make_view(h, h->cur);
     cudaError_t e;
     if (tb) {
         lpc_status s = ensure_maps(h);
         if (s != LPC_OK) return s;
+        const LatticeView v = make_view(h, h->cur);
         e = launch_tb(v, h->p.weight_dtype, h->kdepth, *h->maps[h->cur], h->counter + 1, st);
     } else {
-        e = launch_step1(v, h->p.weight_dtype, st);
+        e = launch_step1(make_view(h, h->cur), h->p.weight_dtype, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     h->cur ^= 1;
@@ -227,13 +270,17 @@ constexpr int kGraphLen = 32;   // steps per captured graph (even: keeps buffer 
 
 lpc_status build_graph(lpc_lattice* h, int parity) {
     cudaGraph_t g = nullptr;
+    const bool tb = h->kernel == LPC_KERNEL_TB;
+    if (tb) {
+        // maps and gather-form arrays are made before the capture
+        lpc_status s0 = ensure_maps(h);
+        if (s0 != LPC_OK) return s0;
+    }
     cudaError_t e = cudaStreamBeginCapture(h->wstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
     const int save = h->cur;
     h->cur = parity;
     lpc_status st = LPC_OK;
-    const bool tb = h->kernel == LPC_KERNEL_TB;
-    if (tb) st = ensure_maps(h);
     for (int i = 0; i < kGraphLen && st == LPC_OK; ++i) st = launch_one(h, h->wstream, tb);
     h->cur = save;
     e = cudaStreamEndCapture(h->wstream, &g);
@@ -249,7 +296,7 @@ lpc_status build_graph(lpc_lattice* h, int parity) {
 // Default schedule: the TMA-fed one-step kernel for lattices large enough to
 // fill its tiles, else the register-pipelined one-step kernel.
 void auto_schedule(lpc_lattice* h) {
-    const bool big = h->p.nx >= 32 && h->p.ny >= 16 && h->N >= (1LL << 18);
+    const bool big = h->p.nx >= 64 && h->p.ny >= 16 && h->N >= (1LL << 18);
     if (big && tb_supported(make_view(h, 0), h->p.weight_dtype, 1) &&
         tb_prepare(h->p.weight_dtype, 1, h->p.msd_axes) == cudaSuccess) {
         h->kernel = LPC_KERNEL_TB;
@@ -278,6 +325,7 @@ void release_all(lpc_lattice* h) {
     }
     dfree(h, h->w, Np * 6 * wbytes(h));
     dfree(h, h->R, Np * 8);
+    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, h->p.msd_axes));
     dfree(h, h->solid, (size_t)h->N);
     if (h->histM) dfree(h, h->histM, history_bytes(h->cap));
     dfree(h, h->partials, h->partials_doubles * 8);
@@ -327,7 +375,7 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     int G = p->ghost;
     if (G == 0) G = 2;
     h->G = G;
-    h->Xp = ((p->nx + 2 * G) + 7) / 8 * 8;
+    h->Xp = ((p->nx + 2 * G) + 31) / 32 * 32;     // rows start on 128-byte lines
     h->Yp = p->ny + 2 * G;
     h->Np = (long long)h->Xp * h->Yp * p->nz;
     if (h->Np > 2147483647LL) {
@@ -415,7 +463,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     const long long N = (long long)p->nx * p->ny * p->nz;
     int G = p->ghost;
     if (G == 0) G = 2;
-    const long long Xp = ((p->nx + 2 * G) + 7) / 8 * 8, Yp = p->ny + 2 * G;
+    const long long Xp = ((p->nx + 2 * G) + 31) / 32 * 32, Yp = p->ny + 2 * G;
     const long long Np = Xp * Yp * p->nz;
     int na = 0;
     for (int a = 0; a < 3; ++a) na += p->msd_axes >> a & 1;
@@ -425,6 +473,8 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     b += (long long)device_props().sm_count * 32 * kMaxTB * kNumSums * 8 + 256 + 8 * 1024;
     b += (long long)history_bytes(cap);
     b += 16 * N;    // transient copies of F and omega during create
+    if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 18))     // the automatic schedule's gather form
+        b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, p->msd_axes);
     *bytes = b;
     return LPC_OK;
 }
