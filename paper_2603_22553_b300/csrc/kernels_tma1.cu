@@ -131,9 +131,11 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     uint64_t* empty1 = full1 + S1;
     uint64_t* full2 = empty1 + S1;
     uint64_t* empty2 = full2 + S2;
-    SlotHdr* hdr = reinterpret_cast<SlotHdr*>(empty2 + S2);        // [S1]
-    double* red = reinterpret_cast<double*>(hdr + S1);             // [NC+1][kNumSums]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(red + (NC + 1) * kNumSums);
+    uint64_t* ifree = empty2 + S2;                                  // [2] item sums combined
+    unsigned int* icount = reinterpret_cast<unsigned int*>(ifree + 2);   // [2] warps done
+    SlotHdr* hdr = reinterpret_cast<SlotHdr*>(ifree + 3);          // [S1]
+    double* ired = reinterpret_cast<double*>(hdr + S1);            // [2][NC][8] per-warp item sums
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(ired + 2 * NC * 8);
     volatile unsigned int* issued1 = reinterpret_cast<volatile unsigned int*>(abort_flag + 1);
     volatile unsigned int* issued2 = issued1 + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -149,12 +151,15 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             mbar_init(&full2[s], 1);
             mbar_init(&empty2[s], NC);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ifree[b], 1);
+            icount[b] = 0u;
+        }
         *abort_flag = 0;
         *issued1 = 0;
         *issued2 = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < (NC + 1) * kNumSums; i += (NC + 1) * 32) red[i] = 0.0;
     __syncthreads();
 
     int axis_of[3] = {0, 0, 0};
@@ -234,6 +239,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool ok = true;
         Cursor w1{0, 0u}, w2{0, 0u};
+        unsigned int kitem = 0;                          // items this warp has finished
         const int o = (warp + 1) * W + G + 2 * lane;     // site 0 in the state arrays
         const int os = warp * kTX + 2 * lane;            // site 0 in the static arrays
         const int C = TY * kTX;
@@ -382,15 +388,44 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             // release the last plane of the item (loaded as the final "above")
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty1[center]);
+            // item sums: a butterfly per warp; the last warp to finish the
+            // item adds the warps in order and stores the item's FP64
+            // partials (two buffers; a buffer is reused once its previous
+            // item was combined, a bounded mbarrier wait)
+            const int b = kitem & 1;
+            const unsigned int use = kitem >> 1;
+            if (use > 0) ok = mbar_wait_bounded(&ifree[b], (use - 1) & 1u);
+            if (!ok) break;
+#pragma unroll
+            for (int qq = 0; qq < kNumSums; ++qq) {
+                const float t = warp_sum_f32(part[qq]);
+                if (lane == 0) ired[(b * NC + warp) * 8 + qq] = (double)t;
+                part[qq] = 0.f;
+            }
+            __syncwarp();
+            unsigned int last = 0u;
+            if (lane == 0) {
+                __threadfence_block();
+                last = atomicAdd(&icount[b], 1u) == (unsigned)NC - 1u;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                if (lane < kNumSums) {
+                    double sum = 0.0;
+                    for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * 8 + lane];
+                    const int item = (h.za / g.cz) * g.tiles + h.tile;
+                    v.partials[(long long)item * kNumSums + lane] = sum;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    icount[b] = 0u;
+                    mbar_arrive(&ifree[b]);
+                }
+            }
+            ++kitem;
         }
         if (!ok) *abort_flag = 1;
-        // per-warp FP64 sums (one butterfly per quantity for the whole launch)
-#pragma unroll
-        for (int qq = 0; qq < kNumSums; ++qq) {
-            if (qq >= 3 && !(MSD >> (qq - 3) & 1)) continue;
-            const float t = warp_sum_f32(part[qq]);
-            if (lane == 0) red[warp * kNumSums + qq] = (double)t;
-        }
     }
     __syncthreads();
     if (*abort_flag) {
@@ -406,7 +441,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         __syncthreads();
         return;
     }
-    block_finish_smem<NC + 1>(v, 1, red);
+    // the rings are idle now: their memory is the final reduction's scratch
+    items_finish<NC + 1>(v, g.n_items, reinterpret_cast<double*>(ring1));
 }
 
 template <typename WT, int MSD, int NC>
@@ -445,7 +481,7 @@ T1Choice t1_choose(const LatticeView& v, int wdtype) {
     for (int i = 0; i < 3; ++i) {
         const int TY = kShapes[i];
         const T1Slots L = t1_slots(c.W, TY, nmsd, wb);
-        const int fixed = 128 + (TY + 1) * kNumSums * 8 + 64;
+        const int fixed = 128 + 3 * 8 + 2 * TY * 8 * 8 + 64;     // slack, item barriers/counts/sums, flags
         const int budget = device_props().max_smem_optin - 1024 - fixed;
         // depth d: S1 = d + 2 state slots (centre and above held), S2 = d + 1
         // static slots (centre held); per slot one full and one empty barrier,
@@ -491,9 +527,14 @@ cudaError_t t1_prepare(int wdtype, int msd) {
     return cudaSuccess;
 }
 
+// Item partials fit the lattice's partials buffer (sm_count * 32 * kMaxTB
+// entries of kNumSums doubles).
+static int t1_max_items() { return device_props().sm_count * 32 * kMaxTB; }
+
 bool t1_supported(const LatticeView& v, int wdtype) {
     const T1Choice c = t1_choose(v, wdtype);
-    return v.G >= 2 && v.G % 2 == 0 && encode_fn() != nullptr && c.depth >= 1;
+    const long long tiles = (long long)((v.nx + kTX - 1) / kTX) * ((v.ny + c.TY - 1) / c.TY);
+    return v.G >= 2 && v.G % 2 == 0 && encode_fn() != nullptr && c.depth >= 1 && tiles <= t1_max_items();
 }
 
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
@@ -565,8 +606,11 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     long long cz = (long long)g.tiles * v.nz / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
     if (cz < 16) cz = 16;
     if (cz > v.nz) cz = v.nz;
+    while ((long long)g.tiles * ((v.nz + cz - 1) / cz) > t1_max_items() && cz < v.nz) cz *= 2;
+    if (cz > v.nz) cz = v.nz;
     g.cz = (int)cz;
     g.n_items = g.tiles * ((v.nz + g.cz - 1) / g.cz);
+    if (g.n_items > t1_max_items()) return cudaErrorInvalidConfiguration;
     g.err = err;
     g.work = err + 7;
     cudaError_t e = t1_prepare(wdtype, v.msd_axes);

@@ -208,6 +208,55 @@ __device__ void block_finish_smem(const LatticeView& v, int levels, double* smem
     }
 }
 
+// Final reduction of per-item FP64 sums v.partials[item * kNumSums + q]
+// written by the blocks of a work-queue kernel: the last block to finish sums
+// the items in a fixed order (thread t adds items t, t + T, ... in order into
+// scratch[q][t], then warp q adds the T values lane-strided and by an FP64
+// butterfly), so the result does not depend on which block took which item,
+// and writes the history entries of one step at *v.step.  `scratch` is
+// shared memory for kNumSums * blockDim doubles (free at this point).
+template <int NW>
+__device__ void items_finish(const LatticeView& v, int n_items, double* scratch) {
+    const int T = NW * 32;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    __shared__ unsigned int is_last;
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(v.counter, 1u) == (unsigned)nblk - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int b = tid; b < n_items; b += T) {
+        const double* p = v.partials + (long long)b * kNumSums;
+#pragma unroll
+        for (int q = 0; q < kNumSums; ++q) acc[q] += __ldcg(p + q);
+    }
+#pragma unroll
+    for (int q = 0; q < kNumSums; ++q) scratch[q * T + tid] = acc[q];
+    __syncthreads();
+    const long long n = *v.step;
+    for (int q = warp; q < kNumSums; q += NW) {
+        double s = 0.0;
+        for (int t = lane; t < T; t += 32) s += scratch[q * T + t];
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            if (q == 0) v.histM[n + 1].x = s;
+            else if (q == 1) v.histM[n + 1].y = s;
+            else if (q == 2) v.histP[n + 1] = s;
+            else if (n >= 0 && (v.msd_axes >> (q - 3) & 1)) v.histD[(long long)(q - 3) * v.cap + n] = s;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *v.step = n + 1;
+        *v.counter = 0u;
+    }
+}
+
 // Same, starting from per-warp sums in registers (lane 0 of every warp).
 template <int NW>
 __device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int levels,
