@@ -331,62 +331,146 @@ cudaError_t launch_step1(const LatticeView& v, int wdtype, cudaStream_t st) {
 
 namespace {
 
+// One work item of a batched step: the tile's update, its sums combined in
+// the block in a fixed order and stored at the item's index, and, in the
+// block that completes the lattice's last item, the lattice's sums in item
+// order.  V is the lattice's view for this step (input and output buffers).
 template <typename WT, int MSD>
-__global__ void __launch_bounds__(BX * BY, 2)
-k_step_batch(const __grid_constant__ BatchParams bp) {
+__device__ __forceinline__ void batch_item(const LatticeView& V, const BatchEntry& E, int li) {
     __shared__ double wsum[NWARP][kNumSums];
     __shared__ unsigned int last;
     const int lane = threadIdx.x;
     const int warp = threadIdx.y;
     const int tid = threadIdx.y * BX + threadIdx.x;
-    for (int gi = blockIdx.x; gi < bp.total_items; gi += gridDim.x) {
-        int lo_ = 0, hi_ = bp.count - 1;          // lattice of this item
-        while (lo_ < hi_) {
-            const int mid = (lo_ + hi_ + 1) >> 1;
-            if (bp.e[mid].item0 <= gi) lo_ = mid;
-            else hi_ = mid - 1;
-        }
-        const BatchEntry& E = bp.e[lo_];
-        const int li = gi - E.item0;
-        float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        step1_item<WT, MSD>(E.v, E.cz, E.tiles_x, E.tiles_y, li, part);
+    float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    step1_item<WT, MSD>(V, E.cz, E.tiles_x, E.tiles_y, li, part);
 #pragma unroll
-        for (int qq = 0; qq < kNumSums; ++qq) {
-            const float t = warp_sum_f32(part[qq]);
-            if (lane == 0) wsum[warp][qq] = (double)t;
+    for (int qq = 0; qq < kNumSums; ++qq) {
+        const float t = warp_sum_f32(part[qq]);
+        if (lane == 0) wsum[warp][qq] = (double)t;
+    }
+    __syncthreads();
+    if (tid < kNumSums) {
+        double sacc = 0.0;
+        for (int w = 0; w < NWARP; ++w) sacc += wsum[w][tid];
+        V.partials[(long long)li * kNumSums + tid] = sacc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(V.counter, 1u) == (unsigned)E.n_items - 1u;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        const long long n = *V.step;
+        if (warp < kNumSums) {
+            const int q = warp;
+            double sacc = 0.0;
+            for (int b = lane; b < E.n_items; b += 32) sacc += __ldcg(&V.partials[(long long)b * kNumSums + q]);
+            sacc = warp_sum_f64(sacc);
+            if (lane == 0) {
+                if (q == 0) V.histM[n + 1].x = sacc;
+                else if (q == 1) V.histM[n + 1].y = sacc;
+                else if (q == 2) V.histP[n + 1] = sacc;
+                else if (MSD >> (q - 3) & 1) V.histD[(long long)(q - 3) * V.cap + n] = sacc;
+            }
         }
         __syncthreads();
-        if (tid < kNumSums) {
-            double sacc = 0.0;
-            for (int w = 0; w < NWARP; ++w) sacc += wsum[w][tid];
-            E.v.partials[(long long)li * kNumSums + tid] = sacc;
+        if (tid == 0) {
+            *V.step = n + 1;
+            *V.counter = 0u;
+        }
+    }
+    __syncthreads();
+}
+
+// Entry of a global item among the first `count` entries (items listed
+// lattice after lattice).
+__device__ __forceinline__ int batch_entry_of(const BatchParams& bp, int count, int gi) {
+    int lo_ = 0, hi_ = count - 1;
+    while (lo_ < hi_) {
+        const int mid = (lo_ + hi_ + 1) >> 1;
+        if (bp.e[mid].item0 <= gi) lo_ = mid;
+        else hi_ = mid - 1;
+    }
+    return lo_;
+}
+
+template <typename WT, int MSD>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_step_batch(const __grid_constant__ BatchParams bp) {
+    for (int gi = blockIdx.x; gi < bp.total_items; gi += gridDim.x) {
+        const BatchEntry& E = bp.e[batch_entry_of(bp, bp.count, gi)];
+        batch_item<WT, MSD>(E.v, E, gi - E.item0);
+    }
+}
+
+// The next step reads what this one wrote.
+__device__ __forceinline__ void swap_io(LatticeView& v) {
+    float* r = v.rho_out;
+    v.rho_out = const_cast<float*>(v.rho_in);
+    v.rho_in = r;
+    float2* m = v.m_out;
+    v.m_out = const_cast<float2*>(v.m_in);
+    v.m_in = m;
+    for (int a = 0; a < 3; ++a) {
+        float* u = v.mu_out[a];
+        v.mu_out[a] = const_cast<float*>(v.mu_in[a]);
+        v.mu_in[a] = u;
+    }
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr long long kGridWaitCycles = 2000000000LL;    // ~1 s at 2 GHz
+
+// Grid-wide barrier of a cooperative launch: arrive on a counter, wait
+// (bounded, with a short sleep) until all blocks of this phase arrived.
+// Returns false when the wait ran out.
+__device__ bool grid_sync_bounded(unsigned int* bar, unsigned int target) {
+    __shared__ int bad;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        bad = 0;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const long long t0 = clock64();
+        while (ld_acquire(bar) < target) {
+            if (clock64() - t0 > kGridWaitCycles) { bad = 1; break; }
+            __nanosleep(64);
         }
         __threadfence();
-        __syncthreads();
-        if (tid == 0) last = atomicAdd(E.v.counter, 1u) == (unsigned)E.n_items - 1u;
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            const long long n = *E.v.step;
-            if (warp < kNumSums) {
-                const int q = warp;
-                double sacc = 0.0;
-                for (int b = lane; b < E.n_items; b += 32) sacc += __ldcg(&E.v.partials[(long long)b * kNumSums + q]);
-                sacc = warp_sum_f64(sacc);
-                if (lane == 0) {
-                    if (q == 0) E.v.histM[n + 1].x = sacc;
-                    else if (q == 1) E.v.histM[n + 1].y = sacc;
-                    else if (q == 2) E.v.histP[n + 1] = sacc;
-                    else if (MSD >> (q - 3) & 1) E.v.histD[(long long)(q - 3) * E.v.cap + n] = sacc;
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                *E.v.step = n + 1;
-                *E.v.counter = 0u;
-            }
+    }
+    __syncthreads();
+    return bad == 0;
+}
+
+// Persistent batched launch: every lattice advances its own number of steps
+// (entries sorted by step count, descending, so the lattices still running at
+// step t are a prefix), with a grid-wide barrier between steps.  Must be a
+// cooperative launch.  A barrier that runs out records LPC_ERR_TIMEOUT in
+// every lattice's error word and ends the launch.
+template <typename WT, int MSD>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_step_batch_multi(const __grid_constant__ BatchParams bp, int nsteps, unsigned int* bar) {
+    for (int t = 0; t < nsteps; ++t) {
+        int A = bp.count;
+        while (A > 0 && bp.e[A - 1].steps <= t) --A;
+        const int total = A == bp.count ? bp.total_items : bp.e[A].item0;
+        for (int gi = blockIdx.x; gi < total; gi += gridDim.x) {
+            const BatchEntry& E = bp.e[batch_entry_of(bp, A, gi)];
+            LatticeView V = E.v;
+            if (t & 1) swap_io(V);
+            batch_item<WT, MSD>(V, E, gi - E.item0);
         }
-        __syncthreads();
+        if (t + 1 < nsteps && !grid_sync_bounded(bar, (unsigned)(t + 1) * gridDim.x)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+                for (int i = 0; i < bp.count; ++i) atomicExch(bp.e[i].v.counter + 1, (unsigned int)LPC_ERR_TIMEOUT);
+            return;
+        }
     }
 }
 
@@ -403,7 +487,23 @@ void* batch_kernel(int wdtype, int msd) {
     return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
 }
 
+
+template <typename WT, int MSD>
+void* batch_multi_fn() { return reinterpret_cast<void*>(&k_step_batch_multi<WT, MSD>); }
+
+void* batch_multi_kernel(int wdtype, int msd) {
+    static void* tab[2][8] = {
+        {batch_multi_fn<float, 0>(), batch_multi_fn<float, 1>(), batch_multi_fn<float, 2>(),
+         batch_multi_fn<float, 3>(), batch_multi_fn<float, 4>(), batch_multi_fn<float, 5>(),
+         batch_multi_fn<float, 6>(), batch_multi_fn<float, 7>()},
+        {batch_multi_fn<__nv_bfloat16, 0>(), batch_multi_fn<__nv_bfloat16, 1>(), batch_multi_fn<__nv_bfloat16, 2>(),
+         batch_multi_fn<__nv_bfloat16, 3>(), batch_multi_fn<__nv_bfloat16, 4>(), batch_multi_fn<__nv_bfloat16, 5>(),
+         batch_multi_fn<__nv_bfloat16, 6>(), batch_multi_fn<__nv_bfloat16, 7>()}};
+    return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
+}
+
 }  // namespace
+
 
 int batch_items(const LatticeView& v, int* tiles_x, int* tiles_y, int* cz) {
     *tiles_x = (v.nx + TX - 1) / TX;
@@ -425,6 +525,31 @@ cudaError_t launch_batch(const BatchParams& bp, int wdtype, int msd, cudaStream_
     if (grid < 1) return cudaSuccess;
     void* args[] = {const_cast<BatchParams*>(&bp)};
     return cudaLaunchKernel(fn, dim3(grid), dim3(BX, BY), args, 0, st);
+}
+
+}  // namespace lpc
+
+namespace lpc {
+
+cudaError_t launch_batch_multi(const BatchParams& bp, int wdtype, int msd, int nsteps, unsigned int* bar,
+                               cudaStream_t st) {
+    void* fn = batch_multi_kernel(wdtype, msd);
+    static int occ_cache[2][8] = {{0}};
+    int& occ = occ_cache[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
+    if (occ == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BX * BY, 0);
+        if (occ < 1) occ = 1;
+    }
+    // every block must be resident (grid barrier): at most occupancy x SMs
+    int grid = device_props().sm_count * occ;
+    if (grid > bp.total_items) grid = bp.total_items;
+    if (grid < 1 || nsteps < 1) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int ns = nsteps;
+    unsigned int* b = bar;
+    void* args[] = {const_cast<BatchParams*>(&bp), &ns, &b};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BX, BY), args, 0, st);
 }
 
 }  // namespace lpc

@@ -304,6 +304,7 @@ struct BatchEntry {
     LatticeView v;
     int item0;                       // first global item of this lattice
     int n_items, tiles_x, tiles_y, cz;
+    int steps;                       // steps of this lattice in a multi-step launch
 };
 struct BatchParams {
     int count;
@@ -312,6 +313,10 @@ struct BatchParams {
 };
 int batch_items(const LatticeView& v, int* tiles_x, int* tiles_y, int* cz);
 cudaError_t launch_batch(const BatchParams& bp, int wdtype, int msd, cudaStream_t st);
+// Persistent cooperative launch of `nsteps` steps (entries sorted by steps,
+// descending); bar: a device word, zeroed by the launcher.
+cudaError_t launch_batch_multi(const BatchParams& bp, int wdtype, int msd, int nsteps, unsigned int* bar,
+                               cudaStream_t st);
 
 // Temporally blocked kernel (K steps per launch, TMA-staged planes).
 struct TBMaps;

@@ -1,6 +1,7 @@
 // C ABI of the lattice-propagation library: handle lifetime, validation,
 // device memory through the caller's allocator, the step schedule (direct
 // launches or replay of captured CUDA graphs), history buffers and queries.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -583,36 +584,58 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
     }
     static thread_local BatchParams bp;
     lpc_status status = LPC_OK;
-    for (long long s = 0; s < max_n && status == LPC_OK; ++s) {
-        // one launch per (weight type, MSD mask) group and per kMaxBatch lattices
-        for (int wd = 0; wd < 2 && status == LPC_OK; ++wd)
-            for (int msd = 0; msd < 8 && status == LPC_OK; ++msd) {
+    // per (weight type, MSD mask) group, chunks of kMaxBatch lattices sorted
+    // by step count: one persistent launch runs every step of a chunk; where
+    // a cooperative launch is not possible, one launch per step
+    for (int wd = 0; wd < 2 && status == LPC_OK; ++wd)
+        for (int msd = 0; msd < 8 && status == LPC_OK; ++msd) {
+            std::vector<int> group;
+            for (int i : batched)
+                if (n[i] > 0 && hs[i]->p.weight_dtype == wd && hs[i]->p.msd_axes == msd) group.push_back(i);
+            std::stable_sort(group.begin(), group.end(), [&](int a, int b) { return n[a] > n[b]; });
+            for (size_t c0 = 0; c0 < group.size() && status == LPC_OK; c0 += kMaxBatch) {
+                const size_t c1 = std::min(group.size(), c0 + (size_t)kMaxBatch);
                 bp.count = 0;
                 bp.total_items = 0;
-                auto flush = [&]() -> lpc_status {
-                    if (bp.count == 0) return LPC_OK;
-                    cudaError_t e = launch_batch(bp, wd, msd, bs);
-                    bp.count = 0;
-                    bp.total_items = 0;
-                    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "batched step launch");
-                };
-                for (int i : batched) {
-                    lpc_lattice* h = hs[i];
-                    if (n[i] <= s || h->p.weight_dtype != wd || h->p.msd_axes != msd) continue;
-                    BatchEntry& E = bp.e[bp.count];
+                for (size_t j = c0; j < c1; ++j) {
+                    lpc_lattice* h = hs[group[j]];
+                    BatchEntry& E = bp.e[bp.count++];
                     E.v = make_view(h, h->cur);
                     E.n_items = batch_items(E.v, &E.tiles_x, &E.tiles_y, &E.cz);
                     E.item0 = bp.total_items;
+                    E.steps = (int)std::min<int64_t>(n[group[j]], INT32_MAX);
                     bp.total_items += E.n_items;
-                    h->cur ^= 1;
-                    if (++bp.count == kMaxBatch) status = flush();
-                    if (status != LPC_OK) break;
                 }
-                if (status == LPC_OK) status = flush();
+                const long long steps_c = n[group[c0]];
+                cudaError_t e = steps_c <= INT32_MAX
+                                    ? launch_batch_multi(bp, wd, msd, (int)steps_c, h0->counter + 9, bs)
+                                    : cudaErrorInvalidValue;
+                if (e == cudaSuccess) {
+                    for (size_t j = c0; j < c1; ++j) hs[group[j]]->cur ^= (int)(n[group[j]] & 1);
+                    continue;
+                }
+                cudaGetLastError();
+                for (long long s = 0; s < steps_c && status == LPC_OK; ++s) {
+                    bp.count = 0;
+                    bp.total_items = 0;
+                    for (size_t j = c0; j < c1; ++j) {
+                        lpc_lattice* h = hs[group[j]];
+                        if (n[group[j]] <= s) continue;
+                        BatchEntry& E = bp.e[bp.count++];
+                        E.v = make_view(h, h->cur);
+                        E.n_items = batch_items(E.v, &E.tiles_x, &E.tiles_y, &E.cz);
+                        E.item0 = bp.total_items;
+                        E.steps = 1;
+                        bp.total_items += E.n_items;
+                        h->cur ^= 1;
+                    }
+                    const cudaError_t e1 = launch_batch(bp, wd, msd, bs);
+                    if (e1 != cudaSuccess) status = cuda_fail(e1, "batched step launch");
+                }
             }
-        for (int i : alone)
-            if (status == LPC_OK && n[i] > s) status = launch_one(hs[i], bs, false);
-    }
+        }
+    for (int i : alone)
+        for (long long s = 0; s < n[i] && status == LPC_OK; ++s) status = launch_one(hs[i], bs, false);
     for (int i = 0; i < count; ++i) hs[i]->steps += n[i];
     // every lattice's private stream continues after the batch (queries and
     // later calls synchronise on it); callers' streams are left free so that
