@@ -293,6 +293,36 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
 
 }  // namespace
 
+namespace {
+
+// Restart of the propagation phase from the current populations: both
+// buffers get rho = the current rho (ghost images included), m = rho, mu = 0.
+__global__ void k_restart(LatticeView v, const float* __restrict__ rho_cur, float* rho_other, float2* m0,
+                          float2* m1, float* mu00, float* mu01, float* mu02, float* mu10, float* mu11,
+                          float* mu12) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.Np) return;
+    const float r = rho_cur[p];
+    rho_other[p] = r;
+    m0[p] = make_float2(r, 0.0f);
+    m1[p] = make_float2(r, 0.0f);
+    float* mu[6] = {mu00, mu01, mu02, mu10, mu11, mu12};
+    for (int i = 0; i < 6; ++i)
+        if (mu[i]) mu[i][p] = 0.0f;
+}
+
+}  // namespace
+
+cudaError_t launch_restart(const LatticeView& v, cudaStream_t st) {
+    const int B = 256;
+    const long long g = (v.Np + B - 1) / B;
+    // v: input = the current state, output = the other buffer
+    k_restart<<<(unsigned)g, B, 0, st>>>(v, v.rho_in, v.rho_out, const_cast<float2*>(v.m_in), v.m_out,
+                                          const_cast<float*>(v.mu_in[0]), const_cast<float*>(v.mu_in[1]),
+                                          const_cast<float*>(v.mu_in[2]), v.mu_out[0], v.mu_out[1], v.mu_out[2]);
+    return cudaGetLastError();
+}
+
 // Pitch of the gather-form arrays: rows start on 256-byte boundaries.
 int gather_pitch(int nx) { return (nx + 63) / 64 * 64; }
 

@@ -87,12 +87,12 @@ struct T1Slots {
     int s, R, dm[3], bytes2;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
-__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb) {
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only) {
     T1Slots L;
     const int H = TY + 2;
     int off = up128(H * W * 4);
     L.m = off;
-    off += up128(H * W * 8);
+    if (!rho_only) off += up128(H * W * 8);
     for (int n = 0; n < 3; ++n) {
         L.mu[n] = off;
         if (n < nmsd) off += up128(H * W * 4);
@@ -103,7 +103,7 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb) {
     L.s = off;
     off += up128(C * 4);
     L.R = off;
-    off += up128(C * 8);
+    if (!rho_only) off += up128(C * 8);
     for (int n = 0; n < 3; ++n) {
         L.dm[n] = off;
         if (n < nmsd) off += up128(C * 8);
@@ -116,15 +116,16 @@ struct SlotHdr {
     int tile, za, n, pad;
 };
 
-template <typename WT, int MSD, int NC>
+template <typename WT, int MSD, int NC, bool RHO>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
 k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
+    static_assert(!RHO || MSD == 0, "the rho-only step carries no moments");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc(MSD);
     constexpr int TY = NC;                    // one core row per consumer warp
     const int W = g.W, S1 = g.S1, S2 = g.S2;
-    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT));
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
@@ -188,7 +189,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 } else {
                     mbar_expect_tx(fb, (uint32_t)g.tx1);
                     tma3(st, &maps.rho, fb, bx, by, z);
-                    tma3(st + SL.m, &maps.m, fb, 2 * bx, by, z);
+                    if (!RHO) tma3(st + SL.m, &maps.m, fb, 2 * bx, by, z);
 #pragma unroll
                     for (int n = 0; n < NMSD; ++n) tma3(st + SL.mu[n], &maps.mu[n], fb, bx, by, z);
                 }
@@ -220,7 +221,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         mbar_expect_tx(fb, (uint32_t)g.tx2);
                         tma4(st, &maps.gwin, fb, sx, sy, z, 0);
                         tma3(st + SL.s, &maps.gs, fb, sx, sy, z);
-                        tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
+                        if (!RHO) tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
 #pragma unroll
                         for (int m = 0; m < NMSD; ++m) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
                         *issued2 = ++n2;
@@ -263,7 +264,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             {
                 const unsigned char* s0 = ring1 + (size_t)w1.slot * g.slot1;
                 br = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(s0) + o);
-                bm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(s0 + SL.m) + o);
+                if (!RHO) bm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(s0 + SL.m) + o);
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n)
                     bmu[n] = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(s0 + SL.mu[n]) + o);
@@ -288,20 +289,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 const unsigned char* sv = ring1 + (size_t)above * g.slot1;
                 const unsigned char* ss = ring2 + (size_t)sslot * g.slot2;
                 const float* rc = reinterpret_cast<const float*>(sc);
-                const float2* mc = reinterpret_cast<const float2*>(sc + SL.m);
                 const float2 r_c = *reinterpret_cast<const float2*>(rc + o);
-                const float4 m_c = *reinterpret_cast<const float4*>(mc + o);
                 const float r_l = rc[o - 1], r_r = rc[o + 2];
                 const float2 r_u = *reinterpret_cast<const float2*>(rc + o - W);
                 const float2 r_d = *reinterpret_cast<const float2*>(rc + o + W);
                 const float2 r_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv) + o);
-                const float2 m_l = mc[o - 1], m_r = mc[o + 2];
-                const float4 m_u = *reinterpret_cast<const float4*>(mc + o - W);
-                const float4 m_d = *reinterpret_cast<const float4*>(mc + o + W);
-                const float4 m_a = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(sv + SL.m) + o);
                 const WT* win = reinterpret_cast<const WT*>(ss);
                 const float2 sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
-                const float4 Rp = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.R) + os);
                 float2 muc[3];
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n)
@@ -316,18 +310,33 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 }
                 q0.r[0] = r_l;   q0.r[1] = r_c.y; q0.r[2] = r_u.x; q0.r[3] = r_d.x; q0.r[4] = br.x; q0.r[5] = r_a.x;
                 q1.r[0] = r_c.x; q1.r[1] = r_r;   q1.r[2] = r_u.y; q1.r[3] = r_d.y; q1.r[4] = br.y; q1.r[5] = r_a.y;
-                q0.m[0] = m_l;                         q1.m[0] = make_float2(m_c.x, m_c.y);
-                q0.m[1] = make_float2(m_c.z, m_c.w);   q1.m[1] = m_r;
-                q0.m[2] = make_float2(m_u.x, m_u.y);   q1.m[2] = make_float2(m_u.z, m_u.w);
-                q0.m[3] = make_float2(m_d.x, m_d.y);   q1.m[3] = make_float2(m_d.z, m_d.w);
-                q0.m[4] = make_float2(bm.x, bm.y);     q1.m[4] = make_float2(bm.z, bm.w);
-                q0.m[5] = make_float2(m_a.x, m_a.y);   q1.m[5] = make_float2(m_a.z, m_a.w);
-                q0.rc = r_c.x; q0.mc = make_float2(m_c.x, m_c.y); q0.R = make_float2(Rp.x, Rp.y);
-                q1.rc = r_c.y; q1.mc = make_float2(m_c.z, m_c.w); q1.R = make_float2(Rp.z, Rp.w);
+                q0.rc = r_c.x;
+                q1.rc = r_c.y;
                 float ro0, ro1;
-                float2 mo0, mo1;
-                site_rho_m(q0, sp.x, ro0, mo0);
-                site_rho_m(q1, sp.y, ro1, mo1);
+                float2 mo0 = make_float2(0.f, 0.f), mo1 = make_float2(0.f, 0.f);
+                float4 m_c = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (RHO) {
+                    ro0 = site_rho(q0.win, q0.r, q0.rc, sp.x);
+                    ro1 = site_rho(q1.win, q1.r, q1.rc, sp.y);
+                } else {
+                    const float2* mc = reinterpret_cast<const float2*>(sc + SL.m);
+                    m_c = *reinterpret_cast<const float4*>(mc + o);
+                    const float2 m_l = mc[o - 1], m_r = mc[o + 2];
+                    const float4 m_u = *reinterpret_cast<const float4*>(mc + o - W);
+                    const float4 m_d = *reinterpret_cast<const float4*>(mc + o + W);
+                    const float4 m_a = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(sv + SL.m) + o);
+                    const float4 Rp = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.R) + os);
+                    q0.m[0] = m_l;                         q1.m[0] = make_float2(m_c.x, m_c.y);
+                    q0.m[1] = make_float2(m_c.z, m_c.w);   q1.m[1] = m_r;
+                    q0.m[2] = make_float2(m_u.x, m_u.y);   q1.m[2] = make_float2(m_u.z, m_u.w);
+                    q0.m[3] = make_float2(m_d.x, m_d.y);   q1.m[3] = make_float2(m_d.z, m_d.w);
+                    q0.m[4] = make_float2(bm.x, bm.y);     q1.m[4] = make_float2(bm.z, bm.w);
+                    q0.m[5] = make_float2(m_a.x, m_a.y);   q1.m[5] = make_float2(m_a.z, m_a.w);
+                    q0.mc = make_float2(m_c.x, m_c.y); q0.R = make_float2(Rp.x, Rp.y);
+                    q1.mc = make_float2(m_c.z, m_c.w); q1.R = make_float2(Rp.z, Rp.w);
+                    site_rho_m(q0, sp.x, ro0, mo0);
+                    site_rho_m(q1, sp.y, ro1, mo1);
+                }
                 float muo0[3], muo1[3];
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n) {
@@ -356,7 +365,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 if (inner) {
                     const long long p = col + (long long)z * zplane;
                     *reinterpret_cast<float2*>(v.rho_out + p) = make_float2(ro0, ro1);
-                    *reinterpret_cast<float4*>(v.m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
+                    if (!RHO) *reinterpret_cast<float4*>(v.m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
 #pragma unroll
                     for (int n = 0; n < NMSD; ++n)
                         *reinterpret_cast<float2*>(v.mu_out[axis_of[n]] + p) = make_float2(muo0[n], muo1[n]);
@@ -364,13 +373,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const long long zoff = (long long)z * zplane;
                     if (site0) {
                         store_images(v.rho_out, v, x, y, zoff, ro0);
-                        store_images(v.m_out, v, x, y, zoff, mo0);
+                        if (!RHO) store_images(v.m_out, v, x, y, zoff, mo0);
 #pragma unroll
                         for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo0[n]);
                     }
                     if (site1) {
                         store_images(v.rho_out, v, x + 1, y, zoff, ro1);
-                        store_images(v.m_out, v, x + 1, y, zoff, mo1);
+                        if (!RHO) store_images(v.m_out, v, x + 1, y, zoff, mo1);
 #pragma unroll
                         for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x + 1, y, zoff, muo1[n]);
                     }
@@ -446,7 +455,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
 }
 
 template <typename WT, int MSD, int NC>
-void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC>); }
+void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false>); }
+
+template <int NC>
+void* t1_rho_kernel(int wdtype) {
+    return wdtype == LPC_WEIGHTS_BF16 ? reinterpret_cast<void*>(&k_step_tma1<__nv_bfloat16, 0, NC, true>)
+                                      : reinterpret_cast<void*>(&k_step_tma1<float, 0, NC, true>);
+}
 
 template <int NC>
 void* t1_kernel_shape(int wdtype, int msd) {
@@ -473,36 +488,45 @@ struct T1Choice {
 // up to 16 bytes.
 int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 
-T1Choice t1_choose(const LatticeView& v, int wdtype) {
+// Ring depth d and shared memory of a tile height: S1 = d + 2 state slots
+// (centre and above held), S2 = d + 1 static slots (centre held); per slot one
+// full and one empty barrier, and a header per state slot.
+void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only) {
+    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only);
+    const int fixed = 128 + 3 * 8 + 2 * TY * 8 * 8 + 64;     // slack, item barriers/counts/sums, flags
+    const int budget = device_props().max_smem_optin - 1024 - fixed;
+    const int per1 = L.bytes1 + 16 + 16, per2 = L.bytes2 + 16;
+    int d = (budget - 2 * per1 - per2) / (per1 + per2);
+    if (d > 8) d = 8;
+    c.TY = TY;
+    c.depth = d;
+    c.S1 = d + 2;
+    c.S2 = d + 1;
+    c.L = L;
+    c.smem = fixed + c.S1 * per1 + c.S2 * per2;
+}
+
+// The tile height comes from the full step (so that one set of tensor maps
+// serves both modes); the rho-only step re-sizes its rings for it.
+T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false) {
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     T1Choice c{};
     c.W = t1_box_width(v.G);
     for (int i = 0; i < 3; ++i) {
-        const int TY = kShapes[i];
-        const T1Slots L = t1_slots(c.W, TY, nmsd, wb);
-        const int fixed = 128 + 3 * 8 + 2 * TY * 8 * 8 + 64;     // slack, item barriers/counts/sums, flags
-        const int budget = device_props().max_smem_optin - 1024 - fixed;
-        // depth d: S1 = d + 2 state slots (centre and above held), S2 = d + 1
-        // static slots (centre held); per slot one full and one empty barrier,
-        // and a header per state slot
-        const int per1 = L.bytes1 + 16 + 16, per2 = L.bytes2 + 16;
-        int d = (budget - 2 * per1 - per2) / (per1 + per2);
-        if (d > 8) d = 8;
-        if ((d >= LPC_T1_MIN_DEPTH && v.ny > TY / 2) || i == 2) {
-            c.TY = TY;
-            c.depth = d;
-            c.S1 = d + 2;
-            c.S2 = d + 1;
-            c.L = L;
-            c.smem = fixed + c.S1 * per1 + c.S2 * per2;
-            return c;
-        }
+        t1_rings(c, kShapes[i], nmsd, wb, false);
+        if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
+    if (rho_only) t1_rings(c, c.TY, 0, wb, true);
     return c;
 }
 
-void* t1_kernel(int TY, int wdtype, int msd) {
+void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false) {
+    if (rho_only) {
+        if (TY == 16) return t1_rho_kernel<16>(wdtype);
+        if (TY == 12) return t1_rho_kernel<12>(wdtype);
+        return t1_rho_kernel<8>(wdtype);
+    }
     if (TY == 16) return t1_kernel_shape<16>(wdtype, msd);
     if (TY == 12) return t1_kernel_shape<12>(wdtype, msd);
     return t1_kernel_shape<8>(wdtype, msd);
@@ -514,8 +538,8 @@ cudaError_t t1_prepare(int wdtype, int msd) {
     static bool done[2][8] = {};
     bool& d = done[wdtype == LPC_WEIGHTS_BF16][msd & 7];
     if (d) return cudaSuccess;
-    for (int i = 0; i < 3; ++i) {
-        void* fn = t1_kernel(kShapes[i], wdtype, msd);
+    for (int i = 0; i < 6; ++i) {
+        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, i >= 3);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, fn);
         if (e != cudaSuccess) return e;
@@ -586,10 +610,10 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
 }
 
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool rho_only) {
     if (!v.gwin) return cudaErrorInvalidValue;
-    const T1Choice c = t1_choose(v, wdtype);
-    const int nmsd = popc(v.msd_axes);
+    const T1Choice c = t1_choose(v, wdtype, rho_only);
+    const int nmsd = rho_only ? 0 : popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     T1Geom g;
     g.W = c.W;
@@ -598,8 +622,8 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.S2 = c.S2;
     g.slot1 = c.L.bytes1;
     g.slot2 = c.L.bytes2;
-    g.tx1 = (c.TY + 2) * c.W * (12 + 4 * nmsd);
-    g.tx2 = c.TY * kTX * (6 * wb + 4 + 8 + 8 * nmsd);
+    g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
+    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 8 * nmsd));
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
@@ -622,8 +646,8 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     LatticeView vv = v;
     TBMaps mm = maps;
     void* args[] = {&mm, &vv, &g};
-    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes), dim3((unsigned)grid), dim3((c.TY + 1) * 32),
-                            args, (size_t)c.smem, st);
+    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes, rho_only), dim3((unsigned)grid),
+                            dim3((c.TY + 1) * 32), args, (size_t)c.smem, st);
 }
 
 }  // namespace lpc

@@ -124,6 +124,15 @@ __device__ __forceinline__ void site_rho_m(const SiteIn& q, float s, float& r_ou
     m_out.y = __fmaf_rn(q.R.x, ai, __fmul_rn(q.R.y, ar));
 }
 
+// The population part of site_rho_m alone (same operations in the same
+// order, so the same bits): the equilibration phase propagates rho only.
+__device__ __forceinline__ float site_rho(const float* win, const float* r, float rc, float s) {
+    float v = __fmul_rn(s, rc);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v = __fmaf_rn(win[k], r[k], v);
+    return v;
+}
+
 // First moment along axis a: mu'(y) = s mu(y) + sum_k win_k [mu_k + d_ka r_k].
 __device__ __forceinline__ float site_mu(const float* win, const float* r, const float* mu_nb,
                                          float s, float mu_c, int a) {
@@ -326,8 +335,10 @@ bool tb_encode_maps(const LatticeView& v, int wdtype, int W, int H, TBMaps* maps
 bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H);
 // err points into the lattice's counter block: err[0] is the error word,
 // err[7] the one-step TMA kernel's work-queue counter (reset per launch).
+// rho_only: propagate rho alone (m and mu untouched, M sums zero), the
+// equilibration phase.
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
-                        cudaStream_t st);
+                        cudaStream_t st, bool rho_only = false);
 cudaError_t t1_prepare(int wdtype, int msd);
 bool t1_supported(const LatticeView& v, int wdtype);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);

@@ -42,6 +42,12 @@ const DeviceProps& device_props() {
 
 }  // namespace lpc
 
+namespace lpc {
+// Both state buffers from the current rho: rho copied, m = rho, mu = 0
+// (v: input = the current buffer); in kernels_pack.cu.
+cudaError_t launch_restart(const LatticeView& v, cudaStream_t st);
+}  // namespace lpc
+
 using namespace lpc;
 
 struct lpc_lattice {
@@ -990,12 +996,28 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
     long long done = 0;
     double diff = INFINITY;
     cudaError_t e = cudaSuccess;
+    // with the one-step TMA schedule, rho alone is propagated (m and mu are
+    // rebuilt from rho below); otherwise full steps of the one-step kernel
+    const bool rho_only = h->kernel == LPC_KERNEL_TB && h->kdepth == 1;
+    if (rho_only) {
+        st = ensure_maps(h);
+        if (st != LPC_OK) return st;
+    }
     while (done < max_iter) {
         const long long chunk = (max_iter - done) < check_every ? (max_iter - done) : check_every;
         const long long zero = 0;
         e = cudaMemcpyAsync(h->dstep, &zero, 8, cudaMemcpyHostToDevice, h->wstream);
         if (e != cudaSuccess) break;
-        for (long long i = 0; i < chunk && st == LPC_OK; ++i) st = launch_one(h, h->wstream);
+        for (long long i = 0; i < chunk && st == LPC_OK && e == cudaSuccess; ++i) {
+            if (rho_only) {
+                e = launch_tma1(make_view(h, h->cur), h->p.weight_dtype, *h->maps[h->cur], h->counter + 1,
+                                h->wstream, true);
+                h->cur ^= 1;
+            } else {
+                st = launch_one(h, h->wstream);
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "equilibration step launch");
         if (st != LPC_OK) return st;
         done += chunk;
         e = launch_maxdiff(h->rho[h->cur], h->rho[h->cur ^ 1], make_view(h, h->cur), h->scratch, h->wstream);
@@ -1009,31 +1031,18 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
         if (diff < threshold) break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
-    // restart the propagation phase from the equilibrated populations
-    LatticeView v = make_view(h, h->cur ^ 1);   // out buffers = current
+    // restart the propagation phase from the equilibrated populations:
+    // m = rho, mu = 0 in both buffers, step counter -1, then the n = 0 sums
     const long long minus_one = -1;
     e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
-    if (e == cudaSuccess) {
-        // m = rho, mu = 0: reuse the init kernel with rho0 taken from the state
-        float* tmp = (float*)dalloc(h, (size_t)h->N * 4);
-        double* tmpd = (double*)dalloc(h, (size_t)h->N * 8);
-        if (!tmp || !tmpd) { dfree(h, tmp, (size_t)h->N * 4); dfree(h, tmpd, (size_t)h->N * 8); set_error("lattice_equilibrate: temporary allocation failed"); return LPC_ERR_OOM; }
-        e = launch_unpad(h->rho[h->cur], 4, make_view(h, h->cur), tmp, h->wstream);
-        std::vector<float> hf;
-        if (e == cudaSuccess) {
-            hf.resize((size_t)h->N);
-            e = cudaMemcpyAsync(hf.data(), tmp, (size_t)h->N * 4, cudaMemcpyDeviceToHost, h->wstream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
-        }
-        std::vector<double> hd(hf.begin(), hf.end());
-        if (e == cudaSuccess) e = cudaMemcpyAsync(tmpd, hd.data(), (size_t)h->N * 8, cudaMemcpyHostToDevice, h->wstream);
-        if (e == cudaSuccess) e = launch_init_state(v, tmpd, LPC_INIT_UNIFORM, nullptr, h->solid, h->p.kT, h->scratch, h->wstream);
-        if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
-        dfree(h, tmp, (size_t)h->N * 4);
-        dfree(h, tmpd, (size_t)h->N * 8);
-    }
+    if (e == cudaSuccess) e = launch_restart(make_view(h, h->cur), h->wstream);
+    if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
+    {
+        const lpc_status ds = check_device_error(h);
+        if (ds != LPC_OK) return ds;
+    }
     if (iters) *iters = done;
     if (max_diff) *max_diff = diff;
     return LPC_OK;

@@ -198,6 +198,28 @@ def test_raw_cuda_allocator_path():
     b["lattice"].close()
 
 
+def test_equilibration_rho_only_tma_step_matches_full_step():
+    """With the one-step TMA schedule the equilibration phase propagates rho
+    alone; its populations are bit-identical to full steps of the
+    register-pipelined kernel, and it stops after the same number of steps."""
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case((40, 70, 130), 13, solid_frac=0.2, alpha=0.5, msd_axes=2)
+    out = []
+    for sched in ((B.LPC_KERNEL_TB, 1), (B.LPC_KERNEL_STEP1, 1)):
+        lat = Lattice.from_input(inp)
+        lat.set_schedule(*sched)
+        it, diff = lat.equilibrate(1e-5, 3000, check_every=150)
+        out.append((it, diff, lat.density(), lat.magnetization(), lat.fid(), lat.population()))
+        lat.step(5)
+        out[-1] += (lat.density(),)
+        lat.close()
+    a, b = out
+    assert a[0] == b[0] and a[1] == b[1]
+    for x, y in zip(a[2:], b[2:]):
+        assert np.array_equal(x, y)
+
+
 def test_equilibration_phase():
     inp = lpc_inputs.random_case((8, 12, 40), 12, solid_frac=0.2, alpha=0.5, msd_axes=1)
     from paper_2603_22553_b300.lattice import Lattice
