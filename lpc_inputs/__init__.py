@@ -89,6 +89,7 @@ class LatticeInput:
     weight_dtype: int = 0      # 0 = FP32 weights, 1 = BF16 weights
     msd_axes: int = 0          # bitmask x=1, y=2, z=4
     regions: dict | None = None
+    alpha_links: np.ndarray | None = None   # [3][nz][ny][nx]: alpha of the link to the +x/+y/+z neighbour
 
     @property
     def n_sites(self):
@@ -257,3 +258,19 @@ CONFIGS = {
     "monolith_512": lambda: monolith(),
     "monolith_512_sub64": lambda: monolith(sub=64),
 }
+
+
+def symmetric_links(shape, seed, lo=0.2, hi=1.0):
+    """Per-link jump factors alpha_ij = lo + (hi - lo) (u_i + u_j) / 2 from a
+    seeded per-site field u ~ U(0, 1): symmetric in i and j by construction.
+
+    Returns (u, links) with links[a][z, y, x] the factor of the link between
+    the site and its +a neighbour (periodic wrap; links across a wall are never
+    used)."""
+    rng = _rng(seed)
+    u = rng.random(tuple(shape))
+    links = np.empty((3,) + tuple(shape))
+    for a in range(3):
+        nb = np.roll(u, -1, axis=2 - a)          # axis a of (x, y, z) is array axis 2 - a
+        links[a] = lo + (hi - lo) * 0.5 * (u + nb)
+    return u, links

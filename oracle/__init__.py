@@ -68,6 +68,10 @@ def _bind(path):
                                                      ctypes.c_double, ctypes.c_int, dp, dp, u8p,
                                                      dp, dp, dp]
         lib.or_pack.restype = ctypes.c_int
+        lib.or_pack_links.argtypes = [ctypes.c_int] * 3 + [ip, ctypes.c_double, dp, ctypes.c_double,
+                                                           ctypes.c_double, ctypes.c_int, dp, dp, u8p,
+                                                           dp, dp, dp]
+        lib.or_pack_links.restype = ctypes.c_int
         lib.or_run.argtypes = [ctypes.c_int] * 3 + [ip, dp, dp, dp, ctypes.c_int, ctypes.c_int64,
                                                     ctypes.c_int, dp, dp, dp, dp, dp, dp]
         lib.or_run.restype = ctypes.c_int
@@ -103,7 +107,9 @@ class Packed:
         self.R = R
 
 
-def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT):
+def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT, alpha_links=None):
+    """Hop weights of Eq. 1 times alpha/6 (alpha_links: optional [3][nz][ny][nx]
+    per-link factors, link between a site and its +x, +y, +z neighbour)."""
     lib = _load()
     N = nx * ny * nz
     F = _c64(F, (N,))
@@ -113,9 +119,10 @@ def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT):
     s = np.empty(N)
     R = np.empty((N, 2))
     per = (ctypes.c_int * 3)(*[int(p) for p in periodic])
-    rc = lib.or_pack(nx, ny, nz, per, float(alpha), float(dt), float(kT), int(mode), _dp(F),
-                     _dp(omega), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-                     _dp(w), _dp(s), _dp(R))
+    links = None if alpha_links is None else _c64(alpha_links, (3 * N,))
+    rc = lib.or_pack_links(nx, ny, nz, per, float(alpha), None if links is None else _dp(links),
+                           float(dt), float(kT), int(mode), _dp(F), _dp(omega),
+                           solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(w), _dp(s), _dp(R))
     if rc != 0:
         raise ValueError("oracle pack rejected its inputs")
     return Packed((nz, ny, nx), tuple(int(p) for p in periodic), w, s, R[:, 0] + 1j * R[:, 1])
@@ -124,7 +131,7 @@ def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT):
 def pack_input(inp, mode=MODE_EXACT):
     """``pack`` on an ``lpc_inputs.LatticeInput``."""
     return pack(inp.nx, inp.ny, inp.nz, inp.periodic, inp.alpha, inp.dt, inp.kT, inp.F,
-                inp.omega, inp.solid, mode)
+                inp.omega, inp.solid, mode, getattr(inp, "alpha_links", None))
 
 
 class Result:

@@ -14,6 +14,11 @@
  *    domain across a non-periodic face, is rejected (weight 0); the particle
  *    stays.  w_k(x) = (alpha/6) * P(x -> x+e_k) and the stay weight is
  *    s(x) = 1 - sum_k w_k(x).
+ *    Position-dependent diffusivity (Sec. 2.1, after Eq. 7): alpha may be
+ *    given per link, alpha_ij = alpha_ji, the same factor for both
+ *    directions of a link so that detailed balance holds; it is stored once
+ *    per link as alpha_links[a][i] for the link between site i and its +a
+ *    neighbour (a = x, y, z).
  *
  *  One step (master equation of the average densities, Sec. 2.1 / Eq. 2, and
  *  the moment-propagation recursion of Sec. 2.2-2.3, Eq. 13 in 3D with the
@@ -93,14 +98,17 @@ static int64_t neighbour(int x, int y, int z, int k, int nx, int ny, int nz, con
  * mode 0: exact FP64.  mode 1: weights and R rounded to binary32.
  * mode 2: weights rounded to bfloat16, R rounded to binary32.
  * In the rounded modes s = 1 - sum of the rounded weights (in FP64).
+ * alpha_links: NULL (alpha on every link) or [3][N] per-link factors in [0, 1].
  */
-int or_pack(int nx, int ny, int nz, const int* periodic, double alpha, double dt, double kT,
-            int mode, const double* F, const double* omega, const uint8_t* solid,
-            double* w, double* s, double* R)
+int or_pack_links(int nx, int ny, int nz, const int* periodic, double alpha, const double* alpha_links,
+                  double dt, double kT, int mode, const double* F, const double* omega,
+                  const uint8_t* solid, double* w, double* s, double* R)
 {
     if (nx < 1 || ny < 1 || nz < 1 || !(alpha > 0.0 && alpha <= 1.0) || !(kT > 0.0)) return OR_INVALID;
     const int64_t N = (int64_t)nx * ny * nz;
-    const double attempt = alpha / 6.0;
+    if (alpha_links)
+        for (int64_t i = 0; i < 3 * N; ++i)
+            if (!(alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0)) return OR_INVALID;
     #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -113,7 +121,10 @@ int or_pack(int nx, int ny, int nz, const int* periodic, double alpha, double dt
                     if (j >= 0 && !solid[i] && !solid[j]) {
                         double dE = (F[j] - F[i]) / kT;
                         double p = (dE > 0.0) ? exp(-dE) : 1.0;   /* Eq. 1 */
-                        wk = attempt * p;
+                        /* the link of a +a hop starts at i, that of a -a hop at j */
+                        double a_link = alpha;
+                        if (alpha_links) a_link = alpha_links[(int64_t)(k >> 1) * N + ((k & 1) ? j : i)];
+                        wk = a_link / 6.0 * p;
                     }
                     if (mode == 1) wk = or_round_f32(wk);
                     else if (mode == 2) wk = or_round_bf16(wk);
@@ -127,8 +138,14 @@ int or_pack(int nx, int ny, int nz, const int* periodic, double alpha, double dt
                 R[2 * i] = c;
                 R[2 * i + 1] = sn;
             }
-    (void)N;
     return OR_OK;
+}
+
+int or_pack(int nx, int ny, int nz, const int* periodic, double alpha, double dt, double kT,
+            int mode, const double* F, const double* omega, const uint8_t* solid,
+            double* w, double* s, double* R)
+{
+    return or_pack_links(nx, ny, nz, periodic, alpha, NULL, dt, kT, mode, F, omega, solid, w, s, R);
 }
 
 /* Boltzmann densities of Eq. 2 over pore sites:

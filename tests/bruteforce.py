@@ -28,8 +28,11 @@ def _target(x, y, z, off, shape, periodic):
     return (c[2] * ny + c[1]) * nx + c[0]
 
 
-def moves(F, solid, periodic, alpha, kT=1.0):
-    """List of (source, target, probability, offset) for every accepted move."""
+def moves(F, solid, periodic, alpha, kT=1.0, link_alpha=None):
+    """List of (source, target, probability, offset) for every accepted move.
+
+    link_alpha: optional symmetric function (i, j) -> alpha of the link between
+    sites i and j (position-dependent diffusivity); alpha otherwise."""
     nz, ny, nx = F.shape
     Ff = F.reshape(-1)
     sf = solid.reshape(-1)
@@ -46,15 +49,16 @@ def moves(F, solid, periodic, alpha, kT=1.0):
                         continue
                     dE = (Ff[j] - Ff[i]) / kT
                     acc = math.exp(-dE) if dE > 0 else 1.0
-                    out.append((i, j, alpha / 6.0 * acc, off))
+                    a_ij = alpha if link_alpha is None else link_alpha(i, j)
+                    out.append((i, j, a_ij / 6.0 * acc, off))
     return out
 
 
-def transition_matrix(F, solid, periodic, alpha, kT=1.0):
+def transition_matrix(F, solid, periodic, alpha, kT=1.0, link_alpha=None):
     """Column-stochastic T with T[j, i] = P(i -> j) for one step (stay on the diagonal)."""
     N = F.size
     T = np.zeros((N, N))
-    for i, j, p, _ in moves(F, solid, periodic, alpha, kT):
+    for i, j, p, _ in moves(F, solid, periodic, alpha, kT, link_alpha):
         T[j, i] += p
         T[i, i] -= p
     T[np.diag_indices(N)] += 1.0

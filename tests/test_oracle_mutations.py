@@ -21,7 +21,8 @@ MUTATIONS = {
     "gather from the wrong side": ("neighbour(x, y, z, k ^ 1, nx, ny, nz, periodic)",
                                    "neighbour(x, y, z, k, nx, ny, nz, periodic)"),
     "conjugated rotation": ("m2[2 * i + 1] = c * mi + sn * mr;", "m2[2 * i + 1] = c * mi - sn * mr;"),
-    "attempt factor 1/3": ("alpha / 6.0", "alpha / 3.0"),
+    "attempt factor 1/3": ("a_link / 6.0", "a_link / 3.0"),
+    "link of a -a hop read at the source": ("((k & 1) ? j : i)", "i"),
     "displacement sign": ("double d = (k & 1) ? -1.0 : 1.0;", "double d = (k & 1) ? 1.0 : -1.0;"),
     "dMSD drift term sign": ("2.0 * (wp - wm)", "2.0 * (wp + wm)"),
     "walls treated as periodic": ("if (!periodic[a]) return -1;", "if (0) return -1;"),
@@ -52,6 +53,10 @@ def _pin_calls():
         ("3d brute force", lambda: [pins.test_msd_3d_bruteforce(p) for p in [(1, 1, 1), (0, 1, 0)]]),
         ("one-step MSD", pins.test_one_step_msd_eq5),
         ("Kohn", lambda: [pins.test_kohn_identity_eq4(a) for a in (0, 2)]),
+        ("links reduce to scalar", pins.test_links_uniform_reduce_to_scalar_alpha),
+        ("links detailed balance", lambda: [pins.test_links_detailed_balance_and_boltzmann(p)
+                                            for p in [(1, 1, 1), (0, 1, 1)]]),
+        ("links brute force", lambda: [pins.test_links_dense_matrix_power(p) for p in [(1, 1, 1), (1, 0, 1)]]),
     ]
     return calls
 

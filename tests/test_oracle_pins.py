@@ -328,3 +328,68 @@ def test_kohn_identity_eq4(axis):
     msd_kohn = np.array([k * c0 + 2.0 * sum((k - m) * c[m] for m in range(1, k))
                          for k in range(n + 1)])
     assert np.allclose(r.msd(axis), msd_kohn, rtol=1e-11, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Position-dependent diffusivity: per-link alpha_ij = alpha_ji (Sec. 2.1, after Eq. 7)
+# --------------------------------------------------------------------------
+
+def _links_case(shape, seed, periodic):
+    inp = lpc_inputs.random_case(shape, seed, periodic=periodic, solid_frac=0.2, F_sd=1.2,
+                                 shift_sd=30.0, alpha=1.0)
+    u, links = lpc_inputs.symmetric_links(shape, seed + 1000)
+    uf = u.reshape(-1)
+
+    def link_alpha(i, j):
+        return 0.2 + 0.8 * 0.5 * (uf[i] + uf[j])
+    return inp, links, link_alpha
+
+
+def test_links_uniform_reduce_to_scalar_alpha():
+    inp = lpc_inputs.random_case((4, 5, 6), 61, periodic=(1, 0, 1), alpha=0.37)
+    a = oracle.pack_input(inp)
+    b = oracle.pack(inp.nx, inp.ny, inp.nz, inp.periodic, inp.alpha, inp.dt, inp.kT, inp.F, inp.omega,
+                    inp.solid, alpha_links=np.full((3,) + inp.F.shape, inp.alpha))
+    assert np.array_equal(a.w, b.w) and np.array_equal(a.s, b.s)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 1), (1, 0, 0)])
+def test_links_detailed_balance_and_boltzmann(periodic):
+    inp, links, link_alpha = _links_case((5, 6, 7), 62, periodic)
+    pk = oracle.pack(inp.nx, inp.ny, inp.nz, periodic, inp.alpha, inp.dt, inp.kT, inp.F, inp.omega,
+                     inp.solid, alpha_links=links)
+    nz, ny, nx = inp.F.shape
+    pi = np.exp(-inp.F.reshape(-1))
+    solid = inp.solid.reshape(-1)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = (z * ny + y) * nx + x
+                for k, off in enumerate(bf.OFFSETS):
+                    j = bf._target(x, y, z, off, inp.F.shape, periodic)
+                    if j is None or solid[i] or solid[j]:
+                        assert pk.w[i, k] == 0.0
+                        continue
+                    assert pi[i] * pk.w[i, k] == pytest.approx(pi[j] * pk.w[j, k ^ 1], rel=1e-14)
+                    assert 0.0 < pk.w[i, k] <= link_alpha(i, j) / 6.0 * (1 + 1e-15)
+    rho_eq = oracle.boltzmann(inp.F, inp.solid)
+    r = oracle.run(pk, rho_eq, 1, msd_axes=0)
+    assert np.max(np.abs(r.rho - rho_eq)) <= 1e-14 * rho_eq.max()
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (1, 0, 1)])
+def test_links_dense_matrix_power(periodic):
+    """Brute force with alpha_ij evaluated from the two sites (no storage convention)."""
+    inp, links, link_alpha = _links_case((4, 3, 5), 63, periodic)
+    pk = oracle.pack(inp.nx, inp.ny, inp.nz, periodic, inp.alpha, inp.dt, inp.kT, inp.F, inp.omega,
+                     inp.solid, alpha_links=links)
+    T = bf.transition_matrix(inp.F, inp.solid, periodic, inp.alpha, link_alpha=link_alpha)
+    N = inp.F.size
+    R = np.exp(1j * inp.omega.reshape(-1) * inp.dt)
+    A = R[:, None] * T
+    rng = np.random.default_rng(64)
+    rho0 = rng.random(N) * (inp.solid.reshape(-1) == 0)
+    r = oracle.run(pk, rho0.reshape(inp.F.shape), 120, msd_axes=0)
+    assert np.max(np.abs(r.rho.reshape(-1) - np.linalg.matrix_power(T, 120) @ rho0)) <= 1e-12 * rho0.max()
+    for n in (1, 9, 120):
+        assert abs(r.M[n] - np.ones(N) @ (np.linalg.matrix_power(A, n) @ rho0)) <= 1e-12 * rho0.sum()
