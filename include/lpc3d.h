@@ -139,6 +139,25 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
                           void* stream, lpc_lattice** out);
 
 /*
+ * lattice_create with a jump factor per link (position-dependent
+ * diffusivity, Sec. 2.1 after Eq. 7: alpha_ij = alpha_ji, the same factor for
+ * both directions of a link, so that detailed balance and the Boltzmann
+ * equilibrium of Eq. 2 are kept).
+ *   alpha_links  [3][N] double, host, C order per axis: alpha_links[a*N + i]
+ *                is the factor of the link between site i and its +a
+ *                neighbour (a = 0: x, 1: y, 2: z; the neighbour wraps on a
+ *                periodic axis, the value is unused across a wall); each in
+ *                [0, 1] (0 closes the link).  NULL: params.alpha on every link.
+ * The hop weight is w_k(x) = alpha_link / 6 * min(1, exp(-dF/kT)).  Other
+ * arguments, ownership and errors as lattice_create; LPC_ERR_INVALID for a
+ * factor outside [0, 1].  The copy of alpha_links (24 bytes per site) is
+ * transient, like those of F and omega.
+ */
+lpc_status lattice_create_links(const lpc_params* p, const double* F, const double* omega,
+                                const uint8_t* solid, const double* rho0, const double* alpha_links,
+                                const lpc_allocator* a, void* stream, lpc_lattice** out);
+
+/*
  * Device bytes lattice_create would hold for these parameters, plus the
  * history of `steps` steps and the transient input copies of create (used to
  * admit requests by HBM footprint).  No device work.  LPC_ERR_INVALID on bad

@@ -57,6 +57,9 @@ SIGNATURES = {
     "lattice_create": (ctypes.c_int, [ctypes.POINTER(lpc_params), _DP, _DP, _U8P, _DP,
                                       ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
                                       ctypes.POINTER(_H)]),
+    "lattice_create_links": (ctypes.c_int, [ctypes.POINTER(lpc_params), _DP, _DP, _U8P, _DP, _DP,
+                                            ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
+                                            ctypes.POINTER(_H)]),
     "lattice_destroy": (ctypes.c_int, [_H]),
     "lattice_footprint": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.c_int64, _I64P]),
     "lattice_step_n": (ctypes.c_int, [_H, ctypes.c_int64]),

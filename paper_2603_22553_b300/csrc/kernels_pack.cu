@@ -38,10 +38,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 round_weight<__nv_bfloat16>
 
 // Hop weights of Eq. 1 (Metropolis) times alpha/6 (six equally likely
 // attempts, jump factor of Eq. 7); zero towards solids and across walls.
+// With per-link factors (position-dependent diffusivity, Sec. 2.1 after
+// Eq. 7) the factor of the link between a site and its +a neighbour is
+// links[a][site], the same for both directions of the link.
 // Rotation R = exp(i omega dt) in FP64, rounded to FP32.
 template <typename WT>
 __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double* __restrict__ omega,
-                       const uint8_t* __restrict__ solid, double alpha, double dt, double kT) {
+                       const uint8_t* __restrict__ solid, double alpha, const double* __restrict__ links,
+                       double dt, double kT) {
     const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (pidx >= v.Np) return;
     WT* W = static_cast<WT*>(const_cast<void*>(v.w));
@@ -57,12 +61,13 @@ __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double
     if (x >= 0 && y >= 0) {
         const long long i = ((long long)z * v.ny + y) * v.nx + x;
         if (!solid[i]) {
-            const double attempt = alpha / 6.0;
+            const long long N = (long long)v.nx * v.ny * v.nz;
             for (int k = 0; k < 6; ++k) {
                 const long long j = nb_site(x, y, z, k, v.nx, v.ny, v.nz, v.per_x, v.per_y, v.per_z);
                 if (j < 0 || solid[j]) continue;
                 const double dE = (F[j] - F[i]) / kT;
-                w[k] = attempt * (dE > 0.0 ? exp(-dE) : 1.0);
+                const double a_link = links ? links[(long long)(k >> 1) * N + ((k & 1) ? j : i)] : alpha;
+                w[k] = a_link / 6.0 * (dE > 0.0 ? exp(-dE) : 1.0);
             }
         }
         double s, c;
@@ -238,13 +243,14 @@ int grid_for(long long n, int block) {
 }  // namespace
 
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
-                        const uint8_t* solid, double alpha, double dt, double kT, cudaStream_t st) {
+                        const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
+                        cudaStream_t st) {
     const int B = 256;
     const long long g = (v.Np + B - 1) / B;
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, dt, kT);
+        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT);
     else
-        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, dt, kT);
+        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT);
     return cudaGetLastError();
 }
 

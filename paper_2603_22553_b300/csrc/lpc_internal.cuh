@@ -290,8 +290,10 @@ struct DeviceProps {
 const DeviceProps& device_props();
 
 // Launchers (return cudaSuccess or the launch error).
+// alpha_links: null (alpha on every link) or device [3][N] per-link factors.
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
-                        const uint8_t* solid, double alpha, double dt, double kT, cudaStream_t st);
+                        const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
+                        cudaStream_t st);
 cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
                               const double* F, const uint8_t* solid, double kT, double* scratch,
                               cudaStream_t st);

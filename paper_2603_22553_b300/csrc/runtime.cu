@@ -356,6 +356,12 @@ const char* lpc_version(void) { return LPC_VERSION; }
 lpc_status lattice_create(const lpc_params* p, const double* F, const double* omega,
                           const uint8_t* solid, const double* rho0, const lpc_allocator* a,
                           void* stream, lpc_lattice** out) {
+    return lattice_create_links(p, F, omega, solid, rho0, nullptr, a, stream, out);
+}
+
+lpc_status lattice_create_links(const lpc_params* p, const double* F, const double* omega,
+                                const uint8_t* solid, const double* rho0, const double* alpha_links,
+                                const lpc_allocator* a, void* stream, lpc_lattice** out) {
     if (out) *out = nullptr;
     if (!p || !F || !omega || !solid || !out) { set_error("lattice_create: NULL argument"); return LPC_ERR_INVALID; }
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { set_error("lattice_create: edges must be >= 1"); return LPC_ERR_INVALID; }
@@ -373,6 +379,9 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     if (!finite_all(F, solid, N, true)) { set_error("lattice_create: non-finite F on a pore site"); return LPC_ERR_INVALID; }
     if (!finite_all(omega, solid, N, false)) { set_error("lattice_create: non-finite omega"); return LPC_ERR_INVALID; }
     if (rho0 && !finite_all(rho0, solid, N, true)) { set_error("lattice_create: non-finite rho0 on a pore site"); return LPC_ERR_INVALID; }
+    if (alpha_links)
+        for (long long i = 0; i < 3 * N; ++i)
+            if (!(alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0)) { set_error("lattice_create_links: link factors must be in [0, 1]"); return LPC_ERR_INVALID; }
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
@@ -415,13 +424,15 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
     ok = ok && (h->counter = (unsigned int*)dalloc(h, 256));
     ok = ok && (h->scratch = (double*)dalloc(h, 8 * 1024));
     // temporaries for the inputs
-    double* dF = nullptr; double* dO = nullptr; double* dR0 = nullptr;
+    double* dF = nullptr; double* dO = nullptr; double* dR0 = nullptr; double* dA = nullptr;
     ok = ok && (dF = (double*)dalloc(h, (size_t)N * 8));
     ok = ok && (dO = (double*)dalloc(h, (size_t)N * 8));
     if (ok && rho0) ok = (dR0 = (double*)dalloc(h, (size_t)N * 8)) != nullptr;
+    if (ok && alpha_links) ok = (dA = (double*)dalloc(h, (size_t)N * 24)) != nullptr;
     if (!ok) {
         set_error("lattice_create: device allocation failed");
         dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
+        dfree(h, dA, (size_t)N * 24);
         release_all(h); delete h;
         return LPC_ERR_OOM;
     }
@@ -436,11 +447,12 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
         if (e == cudaSuccess) e = cudaMemcpyAsync(dO, omega, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid, solid, (size_t)N, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess && rho0) e = cudaMemcpyAsync(dR0, rho0, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess && alpha_links) e = cudaMemcpyAsync(dA, alpha_links, (size_t)N * 24, cudaMemcpyHostToDevice, h->wstream);
         // the byte mask is stored as given; solid means nonzero
         if (e == cudaSuccess) st = ensure_history(h, 1024);
         if (e == cudaSuccess && st == LPC_OK) {
             LatticeView v = make_view(h, 1);   // writes go to buffer 0
-            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, p->dt, p->kT, h->wstream);
+            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, dA, p->dt, p->kT, h->wstream);
             if (e == cudaSuccess)
                 e = launch_init_state(v, dR0, p->init, dF, h->solid, p->kT, h->scratch, h->wstream);
             h->cur = 0;
@@ -449,6 +461,7 @@ lpc_status lattice_create(const lpc_params* p, const double* F, const double* om
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     }
     dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
+    dfree(h, dA, (size_t)N * 24);
     if (e != cudaSuccess || st != LPC_OK) {
         if (st == LPC_OK) st = cuda_fail(e, "lattice_create");
         release_all(h); delete h;

@@ -57,7 +57,7 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, F, omega, solid, *, periodic=(1, 1, 1), alpha=0.005,
                  dt=5e-6, kT=1.0, rho0=None, weight_dtype=0, msd_axes=0, init=0, ghost=0,
-                 stream=None, allocator="torch"):
+                 stream=None, allocator="torch", alpha_links=None):
         self.lib = B.load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -77,6 +77,11 @@ class Lattice:
             r0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
             if r0.size != self.N:
                 raise ValueError("rho0 size does not match the lattice")
+        links = None
+        if alpha_links is not None:
+            links = np.ascontiguousarray(alpha_links, dtype=np.float64).reshape(-1)
+            if links.size != 3 * self.N:
+                raise ValueError("alpha_links must hold 3 values per site")
         self._alloc = None
         aptr = None
         if allocator == "torch":
@@ -87,10 +92,16 @@ class Lattice:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = ctypes.c_void_p()
-        st = self.lib.lattice_create(ctypes.byref(p), _dp(F), _dp(om),
-                                     sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-                                     _dp(r0) if r0 is not None else None, aptr,
-                                     ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if links is None:
+            st = self.lib.lattice_create(ctypes.byref(p), _dp(F), _dp(om),
+                                         sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                         _dp(r0) if r0 is not None else None, aptr,
+                                         ctypes.c_void_p(self.stream), ctypes.byref(h))
+        else:
+            st = self.lib.lattice_create_links(ctypes.byref(p), _dp(F), _dp(om),
+                                               sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                               _dp(r0) if r0 is not None else None, _dp(links), aptr,
+                                               ctypes.c_void_p(self.stream), ctypes.byref(h))
         B.check(st, self.lib)
         self.h = h
 
@@ -98,7 +109,8 @@ class Lattice:
     def from_input(cls, inp, **kw):
         """Create from an ``lpc_inputs.LatticeInput``."""
         args = dict(periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
-                    rho0=inp.rho0, weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes)
+                    rho0=inp.rho0, weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes,
+                    alpha_links=getattr(inp, "alpha_links", None))
         args.update(kw)
         return cls(inp.nx, inp.ny, inp.nz, inp.F, inp.omega, inp.solid, **args)
 

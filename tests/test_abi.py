@@ -109,3 +109,18 @@ def test_null_handle_calls(lib):
     out = np.zeros(2)
     assert lib.lattice_fid(None, 0, 1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == B.LPC_ERR_INVALID
     assert lib.lattice_step_many(None, None, -1) == B.LPC_ERR_INVALID
+
+
+@pytest.mark.parametrize("bad", [1.5, -0.1, float("nan")])
+def test_link_factors_outside_unit_interval_rejected(lib, bad):
+    p = _params()
+    z = np.zeros(64)
+    links = np.full(3 * 64, 0.5)
+    links[70] = bad
+    h = ctypes.c_void_p()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.lattice_create_links(ctypes.byref(p), dp(z), dp(z),
+                                  np.zeros(64, np.uint8).ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                  None, dp(links), None, None, ctypes.byref(h))
+    assert st == B.LPC_ERR_INVALID and not h.value
+    assert b"link" in lib.lpc_last_error()

@@ -234,3 +234,34 @@ def test_equilibration_phase():
     lat.step(10)
     assert lat.msd(0)[-1] > 0
     lat.close()
+
+
+@pytest.mark.parametrize("sched", ["auto", "step1", "tb1", "batch"])
+def test_per_link_alpha_parity(sched):
+    """Position-dependent diffusivity (per-link alpha_ij = alpha_ji): GPU
+    weights equal the oracle's rounded weights; every schedule matches the
+    FP64 oracle and the Boltzmann state stays stationary."""
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice, step_many
+    shape = (20, 36, 130)
+    inp = lpc_inputs.random_case(shape, 71, periodic=(1, 0, 1), alpha=1.0, msd_axes=5)
+    _, inp.alpha_links = lpc_inputs.symmetric_links(shape, 72, lo=0.05, hi=0.9)
+    lat = Lattice.from_input(inp)
+    if sched == "step1":
+        lat.set_schedule(B.LPC_KERNEL_STEP1, 1)
+    elif sched == "tb1":
+        lat.set_schedule(B.LPC_KERNEL_TB, 1)
+    steps = 60
+    if sched == "batch":
+        step_many([lat], [steps])
+    else:
+        lat.step(steps)
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    w = lat.weights().reshape(6, -1).T.astype(np.float64)      # (N, 6) like the oracle
+    assert np.array_equal(w, pk.w)
+    g = dict(M=lat.fid(), P=lat.population(), rho=lat.density().astype(np.float64), m=lat.magnetization())
+    for a in (0, 2):
+        g["msd%d" % a] = lat.msd(a)
+    o = oracle.run(pk, inp.uniform_rho0(), steps, msd_axes=5)
+    H.compare(g, o, 5, tol=1e-5)
+    lat.close()
