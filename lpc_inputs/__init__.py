@@ -90,6 +90,9 @@ class LatticeInput:
     msd_axes: int = 0          # bitmask x=1, y=2, z=4
     regions: dict | None = None
     alpha_links: np.ndarray | None = None   # [3][nz][ny][nx]: alpha of the link to the +x/+y/+z neighbour
+    # reservoir faces: 6 entries (face f = 2 a + side; side 0 below coordinate 0,
+    # side 1 above n_a - 1), each None (wall) or (F_res, rho_res, m_res complex)
+    reservoirs: tuple | None = None
 
     @property
     def n_sites(self):
@@ -274,3 +277,29 @@ def symmetric_links(shape, seed, lo=0.2, hi=1.0):
         nb = np.roll(u, -1, axis=2 - a)          # axis a of (x, y, z) is array axis 2 - a
         links[a] = lo + (hi - lo) * 0.5 * (u + nb)
     return u, links
+
+
+def region_labels(inp):
+    """Per-site region labels (uint8, shape (nz, ny, nx)) and their names from
+    the workload's ``regions`` description: a boolean mask (label 1 where set,
+    0 elsewhere, names ("outside", name)) or x ranges [x0, x1) (labels in the
+    order given)."""
+    shp = (inp.nz, inp.ny, inp.nx)
+    lab = np.zeros(shp, np.uint8)
+    if not inp.regions:
+        return lab, ("all",)
+    items = list(inp.regions.items())
+    if len(items) == 1 and isinstance(items[0][1], np.ndarray):
+        name, mask = items[0]
+        lab[np.asarray(mask, dtype=bool)] = 1
+        return lab, ("outside", name)
+    names = []
+    for r, (name, (x0, x1)) in enumerate(items):
+        lab[:, :, x0:x1] = r
+        names.append(name)
+    return lab, tuple(names)
+
+
+def random_regions(shape, seed, n_regions):
+    """Random per-site labels in [0, n_regions) for tests."""
+    return _rng(seed).integers(0, n_regions, tuple(shape)).astype(np.uint8)

@@ -17,6 +17,9 @@ module marshals numpy arrays into it and adds the plain downstream formulas:
   per axis (Eq. 6-7).
 * ``spectrum``: the plain DFT of M (Eq. 9), numpy's e^{-2 pi i k n / N}.
 * ``boltzmann``: the equilibrium densities of Eq. 2 over pore sites.
+* reservoir faces (Sec. 3.2 item 1: fixed field values in the ghost layer of a
+  non-periodic face) and region-resolved sums M_r, P_r, dMSD_a,r (the
+  spectra and diffusion of separate parts of the system, Sec. 4).
 
 Parity pins are in ``tests/test_oracle_pins.py``.  The physics outputs of the
 paper's Sec. 4 (D/D_bulk in Table 1, spectral peaks of Fig. 9) need the
@@ -75,6 +78,14 @@ def _bind(path):
         lib.or_run.argtypes = [ctypes.c_int] * 3 + [ip, dp, dp, dp, ctypes.c_int, ctypes.c_int64,
                                                     ctypes.c_int, dp, dp, dp, dp, dp, dp]
         lib.or_run.restype = ctypes.c_int
+        lib.or_pack_ex.argtypes = [ctypes.c_int] * 3 + [ip, ctypes.c_double, dp, ctypes.c_double,
+                                                        ctypes.c_double, ctypes.c_int, dp, dp, u8p,
+                                                        dp, dp, dp, dp, dp]
+        lib.or_pack_ex.restype = ctypes.c_int
+        lib.or_run_ex.argtypes = [ctypes.c_int] * 3 + [ip, dp, dp, dp, dp, dp, u8p, ctypes.c_int,
+                                                       ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                                       dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.or_run_ex.restype = ctypes.c_int
         lib.or_boltzmann.argtypes = [ctypes.c_int64, dp, u8p, ctypes.c_double, ctypes.c_double, dp]
         lib.or_boltzmann.restype = ctypes.c_int
         lib.or_round_f32.argtypes = [ctypes.c_double]
@@ -97,19 +108,40 @@ def _c64(a, shape=None):
 
 
 class Packed:
-    """Weights w[N, 6] (k = +x, -x, +y, -y, +z, -z), stay s[N], rotation R[N] (complex)."""
+    """Weights w[N, 6] (k = +x, -x, +y, -y, +z, -z), stay s[N], rotation R[N]
+    (complex); with reservoir faces also res[6, 5] and the reservoir
+    in-weights wres[N, 6]."""
 
-    def __init__(self, shape, periodic, w, s, R):
+    def __init__(self, shape, periodic, w, s, R, res=None, wres=None):
         self.shape = shape
         self.periodic = periodic
         self.w = w
         self.s = s
         self.R = R
+        self.res = res
+        self.wres = wres
 
 
-def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT, alpha_links=None):
+def reservoir_table(reservoirs):
+    """[6, 5] table {enabled, F_res, rho_res, m_res re, m_res im} per face
+    f = 2 a + side (side 0 below coordinate 0, side 1 above n_a - 1) from a
+    sequence of 6 entries, each None or (F_res, rho_res, m_res)."""
+    if reservoirs is None:
+        return None
+    t = np.zeros((6, 5))
+    for f, e in enumerate(reservoirs):
+        if e is None:
+            continue
+        F_res, rho_res, m_res = e
+        t[f] = (1.0, F_res, rho_res, complex(m_res).real, complex(m_res).imag)
+    return t
+
+
+def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT, alpha_links=None,
+         reservoirs=None):
     """Hop weights of Eq. 1 times alpha/6 (alpha_links: optional [3][nz][ny][nx]
-    per-link factors, link between a site and its +x, +y, +z neighbour)."""
+    per-link factors, link between a site and its +x, +y, +z neighbour;
+    reservoirs: optional 6 faces, see ``reservoir_table``)."""
     lib = _load()
     N = nx * ny * nz
     F = _c64(F, (N,))
@@ -120,24 +152,29 @@ def pack(nx, ny, nz, periodic, alpha, dt, kT, F, omega, solid, mode=MODE_EXACT, 
     R = np.empty((N, 2))
     per = (ctypes.c_int * 3)(*[int(p) for p in periodic])
     links = None if alpha_links is None else _c64(alpha_links, (3 * N,))
-    rc = lib.or_pack_links(nx, ny, nz, per, float(alpha), None if links is None else _dp(links),
-                           float(dt), float(kT), int(mode), _dp(F), _dp(omega),
-                           solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(w), _dp(s), _dp(R))
+    res = reservoir_table(reservoirs)
+    wres = None if res is None else np.empty((N, 6))
+    rc = lib.or_pack_ex(nx, ny, nz, per, float(alpha), None if links is None else _dp(links),
+                        float(dt), float(kT), int(mode), _dp(F), _dp(omega),
+                        solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                        None if res is None else _dp(res), _dp(w), _dp(s), _dp(R),
+                        None if wres is None else _dp(wres))
     if rc != 0:
         raise ValueError("oracle pack rejected its inputs")
-    return Packed((nz, ny, nx), tuple(int(p) for p in periodic), w, s, R[:, 0] + 1j * R[:, 1])
+    return Packed((nz, ny, nx), tuple(int(p) for p in periodic), w, s, R[:, 0] + 1j * R[:, 1], res, wres)
 
 
 def pack_input(inp, mode=MODE_EXACT):
     """``pack`` on an ``lpc_inputs.LatticeInput``."""
     return pack(inp.nx, inp.ny, inp.nz, inp.periodic, inp.alpha, inp.dt, inp.kT, inp.F,
-                inp.omega, inp.solid, mode, getattr(inp, "alpha_links", None))
+                inp.omega, inp.solid, mode, getattr(inp, "alpha_links", None),
+                getattr(inp, "reservoirs", None))
 
 
 class Result:
     """Final state and per-step histories of an oracle run."""
 
-    def __init__(self, rho, m, mu, M, P, dmsd, msd_axes):
+    def __init__(self, rho, m, mu, M, P, dmsd, msd_axes, Mr=None, Pr=None, Dr=None):
         self.rho = rho          # (nz, ny, nx) float64
         self.m = m              # (nz, ny, nx) complex128
         self.mu = mu            # (3, nz, ny, nx) float64
@@ -145,14 +182,18 @@ class Result:
         self.P = P              # (steps+1,) float64
         self.dmsd = dmsd        # (3, steps) float64
         self.msd_axes = msd_axes
+        self.Mr = Mr            # (n_regions, steps+1) complex128, or None
+        self.Pr = Pr            # (n_regions, steps+1) float64
+        self.Dr = Dr            # (n_regions, 3, steps) float64
 
     def msd(self, axis):
         """MSD_a(n), n = 0..steps."""
         return msd(self.dmsd[axis], self.P[0])
 
 
-def run(packed, rho0, steps, m0=None, mu0=None, msd_axes=7, nthreads=0):
-    """Run ``steps`` steps from rho0 (m0 = rho0 and mu0 = 0 unless given)."""
+def run(packed, rho0, steps, m0=None, mu0=None, msd_axes=7, nthreads=0, region=None, n_regions=0):
+    """Run ``steps`` steps from rho0 (m0 = rho0 and mu0 = 0 unless given).
+    region: optional [nz][ny][nx] labels < n_regions for region-resolved sums."""
     lib = _load()
     nz, ny, nx = packed.shape
     N = nx * ny * nz
@@ -171,13 +212,29 @@ def run(packed, rho0, steps, m0=None, mu0=None, msd_axes=7, nthreads=0):
     P = np.zeros(steps + 1)
     dmsd = np.zeros((3, max(steps, 1)))
     per = (ctypes.c_int * 3)(*packed.periodic)
-    rc = lib.or_run(nx, ny, nz, per, _dp(w), _dp(s), _dp(R), int(msd_axes), int(steps),
-                    int(nthreads), _dp(rho), _dp(m), _dp(mu), _dp(M), _dp(P), _dp(dmsd))
+    res = packed.res
+    wres = None if packed.wres is None else np.ascontiguousarray(packed.wres, dtype=np.float64)
+    reg = None
+    nr = 0
+    if region is not None:
+        reg = np.ascontiguousarray(region, dtype=np.uint8).reshape(N)
+        nr = int(n_regions)
+    Mr = np.zeros((max(nr, 1), steps + 1, 2))
+    Pr = np.zeros((max(nr, 1), steps + 1))
+    Dr = np.zeros((max(nr, 1), 3, max(steps, 1)))
+    rc = lib.or_run_ex(nx, ny, nz, per, _dp(w), _dp(s), _dp(R),
+                       None if wres is None else _dp(wres), None if res is None else _dp(res),
+                       None if reg is None else reg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                       nr, int(msd_axes), int(steps), int(nthreads), _dp(rho), _dp(m), _dp(mu),
+                       _dp(M), _dp(P), _dp(dmsd), _dp(Mr), _dp(Pr), _dp(Dr))
     if rc != 0:
         raise ValueError("oracle run rejected its inputs")
+    extra = {}
+    if nr:
+        extra = dict(Mr=Mr[..., 0] + 1j * Mr[..., 1], Pr=Pr, Dr=Dr[:, :, :steps])
     return Result(rho.reshape(nz, ny, nx), (m[:, 0] + 1j * m[:, 1]).reshape(nz, ny, nx),
                   mu.reshape(3, nz, ny, nx), M[:, 0] + 1j * M[:, 1], P, dmsd[:, :steps],
-                  msd_axes)
+                  msd_axes, **extra)
 
 
 def boltzmann(F, solid, kT=1.0, mean_rho=1.0):

@@ -147,3 +147,67 @@ def bits_round(v, drop):
     b += ((np.int64(1) << (drop - 1)) - 1) + lsb
     b &= ~((np.int64(1) << drop) - 1)
     return b.view(np.float64)
+
+
+def reservoir_operators(F, solid, periodic, alpha, reservoirs, kT=1.0):
+    """One-step affine operator of a lattice with reservoir faces.
+
+    A reservoir is a layer of fixed virtual sites just outside a face (face
+    f = 2 a + side; side 0 lies below coordinate 0, side 1 above n_a - 1),
+    given as (F_res, rho_res, m_res).  Every move that leaves the domain
+    through a reservoir face is accepted by the Metropolis rule against F_res;
+    every move from the reservoir into a boundary pore site against the
+    site's F.  Returns dict with
+      T      [N, N]  T[j, i] = P(i -> j) inside the domain, stay on the diagonal
+                     (moves into a reservoir leave the domain);
+      Win    [N, 6]  Win[i, f] = P(reservoir site of f -> i) per unit reservoir population;
+      dface  [6, 3]  displacement of a move from face f into the domain;
+      u, q   [3, N]  sum over all moves from i (reservoirs included) of p d_a and p d_a^2;
+      Dax    [3][N, N] displacement operators of the moves inside the domain.
+    """
+    nz, ny, nx = F.shape
+    N = F.size
+    Ff = F.reshape(-1)
+    sf = solid.reshape(-1)
+    n = (nx, ny, nz)
+    T = np.zeros((N, N))
+    Win = np.zeros((N, 6))
+    u = np.zeros((3, N))
+    q = np.zeros((3, N))
+    Dax = [np.zeros((N, N)) for _ in range(3)]
+    dface = np.zeros((6, 3))
+    for f in range(6):
+        dface[f, f // 2] = 1.0 if f % 2 == 0 else -1.0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = (z * ny + y) * nx + x
+                if sf[i]:
+                    continue
+                c = (x, y, z)
+                for off in OFFSETS:
+                    a = next(k for k in range(3) if off[k] != 0)
+                    t = c[a] + off[a]
+                    if 0 <= t < n[a] or periodic[a]:
+                        j = _target(x, y, z, off, F.shape, periodic)
+                        if sf[j]:
+                            continue
+                        dE = (Ff[j] - Ff[i]) / kT
+                        p = alpha / 6.0 * (math.exp(-dE) if dE > 0 else 1.0)
+                        T[j, i] += p
+                        T[i, i] -= p
+                        Dax[a][j, i] += p * off[a]
+                    else:
+                        f = 2 * a + (1 if off[a] > 0 else 0)
+                        if reservoirs[f] is None:
+                            continue
+                        F_res = reservoirs[f][0]
+                        dE = (F_res - Ff[i]) / kT
+                        p = alpha / 6.0 * (math.exp(-dE) if dE > 0 else 1.0)
+                        T[i, i] -= p
+                        dE_in = (Ff[i] - F_res) / kT
+                        Win[i, f] += alpha / 6.0 * (math.exp(-dE_in) if dE_in > 0 else 1.0)
+                    u[a, i] += p * off[a]
+                    q[a, i] += p * off[a] ** 2
+    T[np.diag_indices(N)] += 1.0
+    return dict(T=T, Win=Win, dface=dface, u=u, q=q, Dax=Dax)

@@ -27,11 +27,20 @@ MUTATIONS = {
     "dMSD drift term sign": ("2.0 * (wp - wm)", "2.0 * (wp + wm)"),
     "walls treated as periodic": ("if (!periodic[a]) return -1;", "if (0) return -1;"),
     "transposed site index": ("return ((int64_t)z * ny + y) * nx + x;", "return ((int64_t)z * nx + x) * ny + y;"),
-    "FID sums rho": ("sr += m[2 * i];", "sr += rho[i];"),
+    "FID sums rho": ("double v[6] = {m[2 * i], ", "double v[6] = {rho[i], "),
     "solid target accepted": ("if (j >= 0 && !solid[i] && !solid[j])", "if (j >= 0 && !solid[i])"),
     "temperature dropped": ("double dE = (F[j] - F[i]) / kT;", "double dE = (F[j] - F[i]);"),
-    "moment hop without rho": ("ua[a] += wk * (mu[a * N + j] + (a == axis ? d * rho[j] : 0.0));",
-                               "ua[a] += wk * mu[a * N + j];"),
+    "moment hop without rho": ("ua[a] += wk * (muj[a] + (a == axis ? d * rj : 0.0));",
+                               "ua[a] += wk * muj[a];"),
+    "reservoir in-weight with the out-hop's energy difference": ("double dE = (F[i] - rf[1]) / kT;",
+                                                                 "double dE = (rf[1] - F[i]) / kT;"),
+    "reservoir faces swapped": ("res + 5 * (2 * (k >> 1) + (k & 1))", "res + 5 * (2 * (k >> 1) + 1 - (k & 1))"),
+    "no out-flow into a reservoir": ("} else if (j < 0 && !solid[i] && res) {", "} else if (0) {"),
+    "reservoir magnetisation taken as its population": ("mjr = rf[3];", "mjr = rf[2];"),
+    "region sums only for the first region": ("pl[6 * (1 + region[i]) + q] += v[q];",
+                                              "if (region[i] == 0) pl[6 + q] += v[q];"),
+    "region FID from the population": ("Mr[((int64_t)r * (nsteps + 1) + n) * 2] = t[0];",
+                                       "Mr[((int64_t)r * (nsteps + 1) + n) * 2] = t[2];"),
 }
 
 
@@ -57,6 +66,13 @@ def _pin_calls():
         ("links detailed balance", lambda: [pins.test_links_detailed_balance_and_boltzmann(p)
                                             for p in [(1, 1, 1), (0, 1, 1)]]),
         ("links brute force", lambda: [pins.test_links_dense_matrix_power(p) for p in [(1, 1, 1), (1, 0, 1)]]),
+        ("reservoir Boltzmann", lambda: [pins.test_reservoir_boltzmann_is_stationary(p, f) for p, f in
+                                         [((0, 1, 1), (0, 1)), ((0, 0, 0), (1, 2, 4))]]),
+        ("reservoir chain", lambda: pins.test_reservoir_chain_linear_profile(1.0)),
+        ("reservoir brute force", lambda: [pins.test_reservoir_dense_affine(p, s) for p, s in
+                                           [((0, 1, 1), 81), ((0, 0, 1), 82)]]),
+        ("regions", pins.test_regions_partition_the_totals_and_match_bruteforce),
+        ("single region", pins.test_single_region_equals_the_totals_bitwise),
     ]
     return calls
 

@@ -393,3 +393,161 @@ def test_links_dense_matrix_power(periodic):
     assert np.max(np.abs(r.rho.reshape(-1) - np.linalg.matrix_power(T, 120) @ rho0)) <= 1e-12 * rho0.max()
     for n in (1, 9, 120):
         assert abs(r.M[n] - np.ones(N) @ (np.linalg.matrix_power(A, n) @ rho0)) <= 1e-12 * rho0.sum()
+
+
+# --------------------------------------------------------------------------
+# Reservoir faces (Sec. 3.2 item 1: field values fixed in the ghost layer of
+# a non-periodic face)
+# --------------------------------------------------------------------------
+
+def _with_reservoirs(inp, reservoirs):
+    inp.reservoirs = tuple(reservoirs)
+    return inp
+
+
+@pytest.mark.parametrize("periodic,faces", [((0, 1, 1), (0, 1)), ((0, 0, 1), (0, 3)),
+                                            ((0, 0, 0), (1, 2, 4))])
+def test_reservoir_boltzmann_is_stationary(periodic, faces):
+    """Every reservoir at the same (F_res, rho_res): the grand-canonical state
+    rho = rho_res exp(-(F - F_res)/kT) on pore sites is a fixed point (detailed
+    balance holds on the reservoir links too); with omega = 0 and
+    m_res = rho_res the magnetisation stays equal to rho."""
+    kT, F_res, rho_res = 0.8, -0.7, 1.3
+    inp = lpc_inputs.random_case((5, 6, 7), 71, periodic=periodic, F_sd=1.2, alpha=0.9)
+    inp.kT = kT
+    inp.omega[:] = 0.0
+    res = [None] * 6
+    for f in faces:
+        res[f] = (F_res, rho_res, rho_res)
+    _with_reservoirs(inp, res)
+    pk = oracle.pack_input(inp)
+    rho_eq = rho_res * np.exp(-(inp.F - F_res) / kT) * (inp.solid == 0)
+    r = oracle.run(pk, rho_eq, 3, msd_axes=0)
+    assert np.max(np.abs(r.rho - rho_eq)) <= 1e-14 * rho_eq.max()
+    assert np.max(np.abs(r.m - rho_eq)) <= 1e-14 * rho_eq.max()
+    # the canonical Boltzmann state of Eq. 2 with another mean is not stationary
+    other = oracle.boltzmann(inp.F, inp.solid, kT=kT, mean_rho=0.5)
+    r2 = oracle.run(pk, other, 1, msd_axes=0)
+    assert np.max(np.abs(r2.rho - other)) > 1e-6 * other.max()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.4])
+def test_reservoir_chain_linear_profile(alpha):
+    """A uniform chain between two reservoirs (F = F_res = 0): the stationary
+    profile of the discrete diffusion equation is linear, with the reservoir
+    values at the virtual sites x = -1 and x = n; from an empty chain the
+    iteration converges to it."""
+    nx, rho_lo, rho_hi = 9, 2.0, 0.5
+    shape = (1, 1, nx)
+    F = np.zeros(shape)
+    om = np.zeros(shape)
+    solid = np.zeros(shape, np.uint8)
+    res = [(0.0, rho_lo, 0.0), (0.0, rho_hi, 0.0), None, None, None, None]
+    pk = oracle.pack(nx, 1, 1, (0, 0, 0), alpha, lpc_inputs.DT, 1.0, F, om, solid, reservoirs=res)
+    x = np.arange(nx)
+    lin = (rho_lo + (rho_hi - rho_lo) * (x + 1) / (nx + 1)).reshape(shape)
+    r = oracle.run(pk, lin, 1, msd_axes=0)
+    assert np.max(np.abs(r.rho - lin)) <= 1e-15 * rho_lo
+    # steady flux: alpha/6 (rho_lo - rho_hi)/(n + 1) per step through every link
+    r = oracle.run(pk, np.zeros(shape), int(60 / alpha * (nx + 1) ** 2 / 10) * 10, msd_axes=0)
+    assert np.max(np.abs(r.rho - lin)) <= 1e-12
+
+
+@pytest.mark.parametrize("periodic,seed", [((0, 1, 1), 81), ((0, 0, 1), 82)])
+def test_reservoir_dense_affine(periodic, seed):
+    """Brute force: the augmented dense operator [[T, Win rho_res], [0, 1]]
+    (and its complex and first-moment forms) raised to n, against the
+    oracle's populations, FID and MSD increments."""
+    inp = lpc_inputs.random_case((4, 3, 4), seed, periodic=periodic, solid_frac=0.2, F_sd=1.2,
+                                 shift_sd=30.0, alpha=0.8)
+    rng = np.random.default_rng(seed)
+    res = [None] * 6
+    for f in range(4):
+        if periodic[f // 2] == 0:
+            res[f] = (float(rng.normal(0, 1)), float(rng.uniform(0.3, 2.0)),
+                      complex(rng.normal(0, 1), rng.normal(0, 1)))
+    _with_reservoirs(inp, res)
+    pk = oracle.pack_input(inp)
+    op = bf.reservoir_operators(inp.F, inp.solid, periodic, inp.alpha, res)
+    T, Win = op["T"], op["Win"]
+    N = inp.F.size
+    rho_res = np.array([0.0 if e is None else e[1] for e in res])
+    m_res = np.array([0.0 if e is None else e[2] for e in res], dtype=np.complex128)
+    R = np.exp(1j * inp.omega.reshape(-1) * inp.dt)
+    rho0 = rng.random(N) * (inp.solid.reshape(-1) == 0)
+    steps = 60
+    r = oracle.run(pk, rho0.reshape(inp.F.shape), steps, msd_axes=7)
+    # augmented matrices
+    Aug = np.zeros((N + 1, N + 1))
+    Aug[:N, :N] = T
+    Aug[:N, N] = Win @ rho_res
+    Aug[N, N] = 1.0
+    Am = np.zeros((N + 1, N + 1), dtype=np.complex128)
+    Am[:N, :N] = R[:, None] * T
+    Am[:N, N] = R * (Win @ m_res)
+    Am[N, N] = 1.0
+    x0 = np.append(rho0, 1.0)
+    for n in (1, 5, 60):
+        xn = np.linalg.matrix_power(Aug, n) @ x0
+        mn = np.linalg.matrix_power(Am, n) @ x0.astype(np.complex128)
+        assert abs(r.P[n] - xn[:N].sum()) <= 1e-12 * max(1.0, xn[:N].sum())
+        assert abs(r.M[n] - mn[:N].sum()) <= 1e-12 * max(1.0, np.abs(mn[:N]).sum())
+    assert np.max(np.abs(r.rho.reshape(-1) - (np.linalg.matrix_power(Aug, steps) @ x0)[:N])) <= 1e-12
+    # first moments: mu' = T mu + D rho + Win (d rho_res); dMSD = sum 2 u mu + q rho
+    for a in range(3):
+        rho = rho0.copy()
+        mu = np.zeros(N)
+        for n in range(steps):
+            d = 2.0 * op["u"][a] @ mu + op["q"][a] @ rho
+            assert d == pytest.approx(r.dmsd[a, n], rel=1e-11, abs=1e-13)
+            mu, rho = T @ mu + op["Dax"][a] @ rho + Win @ (op["dface"][:, a] * rho_res), \
+                T @ rho + Win @ rho_res
+        assert np.max(np.abs(r.mu[a].reshape(-1) - mu)) <= 1e-11
+
+
+# --------------------------------------------------------------------------
+# Region-resolved sums (spectra and diffusion of separate parts, Sec. 4)
+# --------------------------------------------------------------------------
+
+def test_regions_partition_the_totals_and_match_bruteforce():
+    inp = lpc_inputs.random_case((4, 4, 4), 91, periodic=(1, 0, 1), solid_frac=0.2, F_sd=1.0,
+                                 shift_sd=30.0, alpha=0.7)
+    pk = oracle.pack_input(inp)
+    lab = lpc_inputs.random_regions(inp.F.shape, 92, 3)
+    N = inp.F.size
+    rho0 = np.random.default_rng(93).random(N) * (inp.solid.reshape(-1) == 0)
+    steps = 40
+    r = oracle.run(pk, rho0.reshape(inp.F.shape), steps, msd_axes=5, region=lab, n_regions=3)
+    assert np.max(np.abs(r.Mr.sum(axis=0) - r.M)) <= 1e-13 * r.P[0]
+    assert np.max(np.abs(r.Pr.sum(axis=0) - r.P)) <= 1e-13 * r.P[0]
+    assert np.max(np.abs(r.Dr.sum(axis=0) - r.dmsd)) <= 1e-13
+    T = bf.transition_matrix(inp.F, inp.solid, inp.periodic, inp.alpha)
+    R = np.exp(1j * inp.omega.reshape(-1) * inp.dt)
+    A = R[:, None] * T
+    lf = lab.reshape(-1)
+    for n in (0, 1, 13, 40):
+        mn = np.linalg.matrix_power(A, n) @ rho0
+        pn = np.linalg.matrix_power(T, n) @ rho0
+        for g in range(3):
+            assert abs(r.Mr[g, n] - mn[lf == g].sum()) <= 1e-12 * rho0.sum()
+            assert abs(r.Pr[g, n] - pn[lf == g].sum()) <= 1e-12 * rho0.sum()
+    # region MSD increments against dense first moments
+    D = bf.displacement_operator(inp.F, inp.solid, inp.periodic, inp.alpha, 2)
+    u = D.sum(axis=0)
+    q = np.abs(D).sum(axis=0)
+    rho, mu = rho0.copy(), np.zeros(N)
+    for n in range(steps):
+        for g in range(3):
+            sel = lf == g
+            assert r.Dr[g, 2, n] == pytest.approx(2 * u[sel] @ mu[sel] + q[sel] @ rho[sel],
+                                                  rel=1e-11, abs=1e-13)
+        mu, rho = T @ mu + D @ rho, T @ rho
+
+
+def test_single_region_equals_the_totals_bitwise():
+    inp = lpc_inputs.random_case((5, 4, 6), 94, periodic=(0, 1, 1), alpha=0.6)
+    pk = oracle.pack_input(inp)
+    lab = np.zeros(inp.F.shape, np.uint8)
+    r = oracle.run(pk, inp.uniform_rho0(), 30, msd_axes=1, region=lab, n_regions=1)
+    assert np.array_equal(r.Mr[0], r.M) and np.array_equal(r.Pr[0], r.P)
+    assert np.array_equal(r.Dr[0, 0], r.dmsd[0])
