@@ -158,6 +158,64 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
                                 const lpc_allocator* a, void* stream, lpc_lattice** out);
 
 /*
+ * Reservoir face (Sec. 3.2 item 1: on a non-periodic boundary the field
+ * values in the ghost layer are held fixed).  A reservoir is the layer of
+ * ghost sites just outside one face of the domain, each holding the fixed
+ * population rho, magnetisation (m_re, m_im) and first moment 0 at every
+ * step, with free energy F.  A boundary pore site exchanges population with
+ * its reservoir site by the Metropolis rule of Eq. 1: out-weight
+ * alpha/6 * min(1, exp(-(F - F_site)/kT)), in-weight
+ * alpha/6 * min(1, exp(-(F_site - F)/kT)) times the reservoir's state
+ * (alpha is params.alpha on reservoir links).  With every reservoir at the
+ * same (F, rho) the state rho(x) = rho exp(-(F(x) - F)/kT) is stationary.
+ */
+typedef struct {
+    int32_t enabled;      /* 1 = reservoir on this face, 0 = wall */
+    int32_t reserved;     /* must be 0 */
+    double F;             /* free energy of the reservoir sites (finite) */
+    double rho;           /* fixed population of a reservoir site (finite) */
+    double m_re, m_im;    /* fixed magnetisation of a reservoir site (finite) */
+} lpc_reservoir;
+
+#define LPC_MAX_REGIONS 4
+
+/*
+ * Options of lattice_create_ex (zero-initialise the struct for none).
+ *   alpha_links  [3][N] per-link jump factors or NULL (as lattice_create_links).
+ *   reservoir[f] face f = 2 a + side of axis a (0 = x, 1 = y; side 0 is the
+ *                face below coordinate 0, side 1 the face above n_a - 1).
+ *                A reservoir needs periodic[a] = 0 and is available on the x
+ *                and y faces only (z has no ghost layer); reservoir[4] and
+ *                reservoir[5] must be disabled.
+ *   region       [N] uint8 site labels, each < n_regions, or NULL: region-
+ *                resolved FID, population and MSD sums (the spectra and
+ *                diffusion of separate parts of a system, e.g. bulk and
+ *                electrodes, Sec. 4).  Copied at create (1 byte per site is
+ *                kept on the device).
+ *   n_regions    1..LPC_MAX_REGIONS with region, 0 without.
+ */
+typedef struct {
+    const double* alpha_links;
+    lpc_reservoir reservoir[6];
+    const uint8_t* region;
+    int32_t n_regions;
+    int32_t reserved;     /* must be 0 */
+} lpc_options;
+
+/*
+ * lattice_create with options (o may be NULL: then it is lattice_create).
+ * Lattices with a reservoir face or with regions run the one-step kernels
+ * (lattice_set_schedule rejects TB with block_steps > 1 for them).  Other
+ * arguments, ownership and errors as lattice_create; LPC_ERR_INVALID also
+ * for a reservoir on a periodic axis or on a z face, non-finite reservoir
+ * values, region labels >= n_regions, or n_regions outside 1..4 with
+ * region (0 without).
+ */
+lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* o, const double* F,
+                             const double* omega, const uint8_t* solid, const double* rho0,
+                             const lpc_allocator* a, void* stream, lpc_lattice** out);
+
+/*
  * Device bytes lattice_create would hold for these parameters, plus the
  * history of `steps` steps and the transient input copies of create (used to
  * admit requests by HBM footprint).  No device work.  LPC_ERR_INVALID on bad
@@ -234,6 +292,23 @@ lpc_status lattice_fid(lpc_lattice* h, int64_t first, int64_t count, double* out
 lpc_status lattice_population(lpc_lattice* h, int64_t first, int64_t count, double* out);
 
 /*
+ * Region-resolved sums of a lattice created with region labels: the FID
+ * M_r(n) = sum of m(x, n) over the sites x labelled r (out: 2*count doubles,
+ * re/im), the population P_r(n), and MSD_r,a(n) = sum_{j<n} dMSD_r,a(j) / P(0)
+ * with dMSD_r,a(j) the MSD increment of Eq. 5 summed over the sites labelled r
+ * at step j (the part of MSD_a(n) accrued while the particles were in region
+ * r; the regions add up to lattice_msd).  Sums over r equal lattice_fid,
+ * lattice_population and lattice_msd up to FP64 rounding.  Range rules as
+ * lattice_fid; LPC_ERR_INVALID for a region >= n_regions or a lattice
+ * without regions.
+ */
+lpc_status lattice_fid_region(lpc_lattice* h, int32_t region, int64_t first, int64_t count, double* out);
+lpc_status lattice_population_region(lpc_lattice* h, int32_t region, int64_t first, int64_t count,
+                                     double* out);
+lpc_status lattice_msd_region(lpc_lattice* h, int32_t region, int32_t axis, int64_t first, int64_t count,
+                              double* out);
+
+/*
  * Mean-square displacement along `axis` (0 = x, 1 = y, 2 = z):
  * MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0) for n = first .. first+count-1,
  * from moment propagation (Sec. 2.2, Eq. 5); D = MSD / (2 n dt) per axis.
@@ -269,8 +344,8 @@ lpc_status lattice_solid(lpc_lattice* h, uint8_t* out);
 
 /*
  * Checkpoint / resume.  The state blob holds rho, m, mu (FP32, interior
- * sites), the step counter and the FP64 history; lattice_state_size gives
- * its size.  lattice_set_state requires a lattice created with the same
+ * sites), the step counter and the FP64 histories (totals and regions);
+ * lattice_state_size gives its size.  lattice_set_state requires a lattice created with the same
  * parameters.  Resuming and running m more steps gives the same results,
  * bit for bit, as running them without the checkpoint.
  */

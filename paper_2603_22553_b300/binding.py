@@ -37,6 +37,20 @@ class lpc_allocator(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
 
 
+class lpc_reservoir(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("reserved", ctypes.c_int32), ("F", ctypes.c_double),
+                ("rho", ctypes.c_double), ("m_re", ctypes.c_double), ("m_im", ctypes.c_double)]
+
+
+LPC_MAX_REGIONS = 4
+
+
+class lpc_options(ctypes.Structure):
+    _fields_ = [("alpha_links", ctypes.POINTER(ctypes.c_double)), ("reservoir", lpc_reservoir * 6),
+                ("region", ctypes.POINTER(ctypes.c_uint8)), ("n_regions", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class lpc_info(ctypes.Structure):
     _fields_ = [("n_sites", ctypes.c_int64), ("n_padded", ctypes.c_int64),
                 ("ghost", ctypes.c_int32), ("pitch_x", ctypes.c_int32),
@@ -60,6 +74,9 @@ SIGNATURES = {
     "lattice_create_links": (ctypes.c_int, [ctypes.POINTER(lpc_params), _DP, _DP, _U8P, _DP, _DP,
                                             ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
                                             ctypes.POINTER(_H)]),
+    "lattice_create_ex": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.POINTER(lpc_options), _DP, _DP,
+                                         _U8P, _DP, ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
+                                         ctypes.POINTER(_H)]),
     "lattice_destroy": (ctypes.c_int, [_H]),
     "lattice_footprint": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.c_int64, _I64P]),
     "lattice_step_n": (ctypes.c_int, [_H, ctypes.c_int64]),
@@ -73,6 +90,10 @@ SIGNATURES = {
     "lattice_fid": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_population": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_msd": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
+    "lattice_fid_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
+    "lattice_population_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
+    "lattice_msd_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                          _DP]),
     "lattice_density": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int32]),
     "lattice_magnetization": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int32]),
     "lattice_moment": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]),

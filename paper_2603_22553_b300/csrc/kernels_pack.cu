@@ -42,10 +42,35 @@ template <> __device__ __forceinline__ __nv_bfloat16 round_weight<__nv_bfloat16>
 // Eq. 7) the factor of the link between a site and its +a neighbour is
 // links[a][site], the same for both directions of the link.
 // Rotation R = exp(i omega dt) in FP64, rounded to FP32.
+// Reservoir faces (Sec. 3.2 item 1): a boundary pore site's move out of the
+// domain through a reservoir face is accepted against the reservoir's F; the
+// ghost site just outside the face carries the weight of the move from the
+// reservoir into its boundary neighbour (the only one of its weights any
+// kernel reads), so that the kernels' gather needs no special case.
+__device__ __forceinline__ double metropolis(double dE) { return dE > 0.0 ? exp(-dE) : 1.0; }
+
+// Reservoir ghost of a padded position: the face (0..3) when the position is
+// the ghost site just outside a reservoir face next to an interior row or
+// column, with the boundary site (bx, by) it feeds and the direction k of
+// that move; -1 otherwise.
+__device__ __forceinline__ int reservoir_ghost(const LatticeView& v, const ResFaces& rf, int px, int py,
+                                               int x, int y, int& bx, int& by, int& k) {
+    bx = x;
+    by = y;
+    if (x < 0 && y >= 0) {
+        if (px == v.G - 1 && rf.on[0]) { bx = 0; k = 0; return 0; }
+        if (px == v.G + v.nx && rf.on[1]) { bx = v.nx - 1; k = 1; return 1; }
+    } else if (y < 0 && x >= 0) {
+        if (py == v.G - 1 && rf.on[2]) { by = 0; k = 2; return 2; }
+        if (py == v.G + v.ny && rf.on[3]) { by = v.ny - 1; k = 3; return 3; }
+    }
+    return -1;
+}
+
 template <typename WT>
 __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double* __restrict__ omega,
                        const uint8_t* __restrict__ solid, double alpha, const double* __restrict__ links,
-                       double dt, double kT) {
+                       double dt, double kT, ResFaces rf) {
     const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (pidx >= v.Np) return;
     WT* W = static_cast<WT*>(const_cast<void*>(v.w));
@@ -64,15 +89,28 @@ __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double
             const long long N = (long long)v.nx * v.ny * v.nz;
             for (int k = 0; k < 6; ++k) {
                 const long long j = nb_site(x, y, z, k, v.nx, v.ny, v.nz, v.per_x, v.per_y, v.per_z);
-                if (j < 0 || solid[j]) continue;
+                if (j < 0) {
+                    // out through a face: +a hops leave by side 1, -a hops by side 0
+                    const int f = 2 * (k >> 1) + ((k & 1) ? 0 : 1);
+                    if (k < 4 && rf.on[f]) w[k] = alpha / 6.0 * metropolis((rf.F[f] - F[i]) / kT);
+                    continue;
+                }
+                if (solid[j]) continue;
                 const double dE = (F[j] - F[i]) / kT;
                 const double a_link = links ? links[(long long)(k >> 1) * N + ((k & 1) ? j : i)] : alpha;
-                w[k] = a_link / 6.0 * (dE > 0.0 ? exp(-dE) : 1.0);
+                w[k] = a_link / 6.0 * metropolis(dE);
             }
         }
         double s, c;
         sincos(omega[i] * dt, &s, &c);
         rot = make_float2(__double2float_rn(c), __double2float_rn(s));
+    } else {
+        int bx, by, k;
+        const int f = reservoir_ghost(v, rf, px, py, x, y, bx, by, k);
+        if (f >= 0) {
+            const long long i = ((long long)z * v.ny + by) * v.nx + bx;
+            if (!solid[i]) w[k] = alpha / 6.0 * metropolis((F[i] - rf.F[f]) / kT);
+        }
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) W[k * v.Np + pidx] = round_weight<WT>(w[k]);
@@ -137,6 +175,30 @@ __global__ void k_init(LatticeView v, const double* __restrict__ rho0, int mode,
     v.m_out[pidx] = make_float2(r, 0.0f);
     const_cast<float*>(v.rho_in)[pidx] = r;
     const_cast<float2*>(v.m_in)[pidx] = make_float2(r, 0.0f);
+    for (int a = 0; a < 3; ++a)
+        if (v.msd_axes >> a & 1) {
+            v.mu_out[a][pidx] = 0.0f;
+            const_cast<float*>(v.mu_in[a])[pidx] = 0.0f;
+        }
+}
+
+// Reservoir values into the reservoir ghost sites of both state buffers
+// (first moment 0).
+__global__ void k_reservoir_ghosts(LatticeView v, ResFaces rf) {
+    const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pidx >= v.Np) return;
+    const int px = (int)(pidx % v.Xp);
+    const long long t = pidx / v.Xp;
+    const int py = (int)(t % v.Yp);
+    const int x = unpad_coord(px, v.G, v.nx, v.per_x);
+    const int y = unpad_coord(py, v.G, v.ny, v.per_y);
+    int bx, by, k;
+    const int f = reservoir_ghost(v, rf, px, py, x, y, bx, by, k);
+    if (f < 0) return;
+    v.rho_out[pidx] = rf.rho[f];
+    v.m_out[pidx] = rf.m[f];
+    const_cast<float*>(v.rho_in)[pidx] = rf.rho[f];
+    const_cast<float2*>(v.m_in)[pidx] = rf.m[f];
     for (int a = 0; a < 3; ++a)
         if (v.msd_axes >> a & 1) {
             v.mu_out[a][pidx] = 0.0f;
@@ -244,13 +306,21 @@ int grid_for(long long n, int block) {
 
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
                         const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
-                        cudaStream_t st) {
+                        const ResFaces& rf, cudaStream_t st) {
     const int B = 256;
     const long long g = (v.Np + B - 1) / B;
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT);
+        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf);
     else
-        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT);
+        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reservoir_ghosts(const LatticeView& v, const ResFaces& rf, cudaStream_t st) {
+    if (!rf.any()) return cudaSuccess;
+    const int B = 256;
+    const long long g = (v.Np + B - 1) / B;
+    k_reservoir_ghosts<<<(unsigned)g, B, 0, st>>>(v, rf);
     return cudaGetLastError();
 }
 

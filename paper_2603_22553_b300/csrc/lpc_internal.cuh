@@ -55,10 +55,24 @@ struct LatticeView {
     double* partials;                // [levels][grid][kNumSums]
     unsigned int* counter;
     long long* step;                 // device step counter (index of the input state)
-    double2* histM;                  // [cap]
-    double* histP;                   // [cap]
-    double* histD;                   // [3][cap]
+    double2* histM;                  // [1 + nreg][cap]: the totals, then each region
+    double* histP;                   // [1 + nreg][cap]
+    double* histD;                   // [1 + nreg][3][cap]
     long long cap;
+    // region labels (null without regions): uint8 [nz][ny][Xr], Xr = roundup(nx, 64)
+    const uint8_t* region;
+    int nreg;
+    int Xr;
+};
+
+// Reservoir faces f = 2 a + side (a = x, y; side 0 below coordinate 0, side 1
+// above n_a - 1): the ghost sites just outside a face hold fixed values.
+struct ResFaces {
+    int on[4];
+    double F[4];
+    float rho[4];
+    float2 m[4];
+    __host__ __device__ bool any() const { return on[0] || on[1] || on[2] || on[3]; }
 };
 
 // Deterministic sum helpers --------------------------------------------------
@@ -291,9 +305,19 @@ const DeviceProps& device_props();
 
 // Launchers (return cudaSuccess or the launch error).
 // alpha_links: null (alpha on every link) or device [3][N] per-link factors.
+// rf: reservoir faces (their out- and in-weights are packed beside the others).
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
                         const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
-                        cudaStream_t st);
+                        const ResFaces& rf, cudaStream_t st);
+// Write the reservoir values into the ghost sites of the reservoir faces, in
+// both state buffers.
+cudaError_t launch_reservoir_ghosts(const LatticeView& v, const ResFaces& rf, cudaStream_t st);
+// Region-resolved sums of the current state (index *v.step): M_r, P_r and
+// dMSD_a,r into the region histories; part: [region_blocks(v)][6 * nreg]
+// doubles, done: a zeroed completion counter.
+cudaError_t launch_region_sums(const LatticeView& v, int wdtype, double* part, unsigned int* done,
+                               cudaStream_t st);
+int region_blocks();
 cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
                               const double* F, const uint8_t* solid, double kT, double* scratch,
                               cudaStream_t st);

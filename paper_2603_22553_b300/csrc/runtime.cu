@@ -95,6 +95,13 @@ struct lpc_lattice {
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_len = 0;
+
+    // reservoir faces and region labels (lattice_create_ex)
+    ResFaces rf{};
+    uint8_t* region = nullptr;          // [nz][ny][Xr]
+    int nreg = 0;
+    int Xr = 0;
+    double* rpart = nullptr;            // per-block partials of the region pass
 };
 
 namespace {
@@ -138,7 +145,16 @@ void dfree(lpc_lattice* h, void* p, size_t bytes) {
 
 size_t wbytes(const lpc_lattice* h) { return h->p.weight_dtype == LPC_WEIGHTS_BF16 ? 2 : 4; }
 
-size_t history_bytes(long long cap) { return (size_t)cap * (sizeof(double2) + sizeof(double) * 4); }
+// One history set is M (double2), P and dMSD x, y, z per step; a lattice
+// holds the totals and one set per region, laid out [set][cap] per quantity.
+size_t history_bytes(long long cap, int sets) {
+    return (size_t)cap * sets * (sizeof(double2) + sizeof(double) * 4);
+}
+
+// Steps of a TB launch that this lattice may use: reservoir ghosts must keep
+// their values and region sums are taken once per step, so lattices with
+// either run one step per launch.
+bool tb_depth_allowed(const lpc_lattice* h, int K) { return K == 1 || (!h->rf.any() && h->nreg == 0); }
 
 LatticeView make_view(lpc_lattice* h, int in) {
     LatticeView v;
@@ -154,6 +170,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.Xs = h->Xs; v.Ns = h->Ns;
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
+    v.region = h->region; v.nreg = h->nreg; v.Xr = h->Xr;
     return v;
 }
 
@@ -168,24 +185,28 @@ lpc_status ensure_history(lpc_lattice* h, long long needed) {
     long long ncap = h->cap * 2;
     if (ncap < needed) ncap = needed;
     if (ncap < 1024) ncap = 1024;
-    char* blk = (char*)dalloc(h, history_bytes(ncap));
+    const int sets = 1 + h->nreg;
+    char* blk = (char*)dalloc(h, history_bytes(ncap, sets));
     if (!blk) { set_error("history allocation failed"); return LPC_ERR_OOM; }
     double2* nM = (double2*)blk;
-    double* nP = (double*)(blk + sizeof(double2) * ncap);
-    double* nD = nP + ncap;
-    cudaError_t e = cudaMemsetAsync(blk, 0, history_bytes(ncap), h->wstream);
-    if (e == cudaSuccess && h->cap > 0) {
-        e = cudaMemcpyAsync(nM, h->histM, sizeof(double2) * h->cap, cudaMemcpyDeviceToDevice, h->wstream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(nP, h->histP, sizeof(double) * h->cap, cudaMemcpyDeviceToDevice, h->wstream);
-        for (int a = 0; a < 3 && e == cudaSuccess; ++a)
-            e = cudaMemcpyAsync(nD + a * ncap, h->histD + a * h->cap, sizeof(double) * h->cap,
+    double* nP = (double*)(blk + sizeof(double2) * ncap * sets);
+    double* nD = nP + ncap * sets;
+    cudaError_t e = cudaMemsetAsync(blk, 0, history_bytes(ncap, sets), h->wstream);
+    for (int st = 0; st < sets && e == cudaSuccess && h->cap > 0; ++st) {
+        e = cudaMemcpyAsync(nM + st * ncap, h->histM + st * h->cap, sizeof(double2) * h->cap,
+                            cudaMemcpyDeviceToDevice, h->wstream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(nP + st * ncap, h->histP + st * h->cap, sizeof(double) * h->cap,
                                 cudaMemcpyDeviceToDevice, h->wstream);
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(nD + (st * 3 + a) * ncap, h->histD + (st * 3 + a) * h->cap,
+                                sizeof(double) * h->cap, cudaMemcpyDeviceToDevice, h->wstream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "history copy");
     if (h->histM) {
         // the old block must not be reused before the copies above finish
         cudaStreamSynchronize(h->wstream);
-        dfree(h, h->histM, history_bytes(h->cap));
+        dfree(h, h->histM, history_bytes(h->cap, sets));
     }
     h->histM = nM; h->histP = nP; h->histD = nD; h->cap = ncap;
     drop_graphs(h);
@@ -257,6 +278,10 @@ lpc_status launch_one(lpc_lattice* h, cudaStream_t st, bool tb = false) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     h->cur ^= 1;
+    if (h->nreg > 0) {
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, st);
+        if (e != cudaSuccess) return cuda_fail(e, "region sums launch");
+    }
     return LPC_OK;
 }
 
@@ -334,7 +359,9 @@ void release_all(lpc_lattice* h) {
     dfree(h, h->R, Np * 8);
     if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, h->p.msd_axes));
     dfree(h, h->solid, (size_t)h->N);
-    if (h->histM) dfree(h, h->histM, history_bytes(h->cap));
+    if (h->region) dfree(h, h->region, (size_t)h->Xr * h->p.ny * h->p.nz);
+    if (h->rpart) dfree(h, h->rpart, (size_t)region_blocks() * LPC_MAX_REGIONS * 6 * 8);
+    if (h->histM) dfree(h, h->histM, history_bytes(h->cap, 1 + h->nreg));
     dfree(h, h->partials, h->partials_doubles * 8);
     dfree(h, h->counter, 256);
     dfree(h, h->scratch, 8 * 1024);
@@ -356,13 +383,26 @@ const char* lpc_version(void) { return LPC_VERSION; }
 lpc_status lattice_create(const lpc_params* p, const double* F, const double* omega,
                           const uint8_t* solid, const double* rho0, const lpc_allocator* a,
                           void* stream, lpc_lattice** out) {
-    return lattice_create_links(p, F, omega, solid, rho0, nullptr, a, stream, out);
+    return lattice_create_ex(p, nullptr, F, omega, solid, rho0, a, stream, out);
 }
 
 lpc_status lattice_create_links(const lpc_params* p, const double* F, const double* omega,
                                 const uint8_t* solid, const double* rho0, const double* alpha_links,
                                 const lpc_allocator* a, void* stream, lpc_lattice** out) {
+    lpc_options o;
+    memset(&o, 0, sizeof o);
+    o.alpha_links = alpha_links;
+    return lattice_create_ex(p, &o, F, omega, solid, rho0, a, stream, out);
+}
+
+lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const double* F,
+                             const double* omega, const uint8_t* solid, const double* rho0,
+                             const lpc_allocator* a, void* stream, lpc_lattice** out) {
     if (out) *out = nullptr;
+    lpc_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) o = *opt;
+    const double* alpha_links = o.alpha_links;
     if (!p || !F || !omega || !solid || !out) { set_error("lattice_create: NULL argument"); return LPC_ERR_INVALID; }
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { set_error("lattice_create: edges must be >= 1"); return LPC_ERR_INVALID; }
     const long long N = (long long)p->nx * p->ny * p->nz;
@@ -382,11 +422,38 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
     if (alpha_links)
         for (long long i = 0; i < 3 * N; ++i)
             if (!(alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0)) { set_error("lattice_create_links: link factors must be in [0, 1]"); return LPC_ERR_INVALID; }
+    if (o.reserved != 0) { set_error("lattice_create_ex: reserved option fields must be 0"); return LPC_ERR_INVALID; }
+    ResFaces rf{};
+    for (int f = 0; f < 6; ++f) {
+        const lpc_reservoir& r = o.reservoir[f];
+        if (!r.enabled) continue;
+        if (r.enabled != 1 || r.reserved != 0) { set_error("lattice_create_ex: reservoir.enabled must be 0 or 1 and reserved 0"); return LPC_ERR_INVALID; }
+        if (f >= 4) { set_error("lattice_create_ex: reservoirs are available on x and y faces only"); return LPC_ERR_INVALID; }
+        if (p->periodic[f >> 1]) { set_error("lattice_create_ex: a reservoir needs a non-periodic axis"); return LPC_ERR_INVALID; }
+        if (!std::isfinite(r.F) || !std::isfinite(r.rho) || !std::isfinite(r.m_re) || !std::isfinite(r.m_im)) {
+            set_error("lattice_create_ex: non-finite reservoir values");
+            return LPC_ERR_INVALID;
+        }
+        rf.on[f] = 1;
+        rf.F[f] = r.F;
+        rf.rho[f] = (float)r.rho;
+        rf.m[f] = make_float2((float)r.m_re, (float)r.m_im);
+    }
+    if ((o.region == nullptr) != (o.n_regions == 0) || o.n_regions < 0 || o.n_regions > LPC_MAX_REGIONS) {
+        set_error("lattice_create_ex: n_regions must be 1..4 with region labels and 0 without");
+        return LPC_ERR_INVALID;
+    }
+    if (o.region)
+        for (long long i = 0; i < N; ++i)
+            if (o.region[i] >= o.n_regions) { set_error("lattice_create_ex: a region label is >= n_regions"); return LPC_ERR_INVALID; }
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
     h->p = *p;
     h->N = N;
+    h->rf = rf;
+    h->nreg = o.n_regions;
+    h->Xr = gather_pitch(p->nx);
     cudaGetDevice(&h->device);
     int G = p->ghost;
     if (G == 0) G = 2;
@@ -423,6 +490,11 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
     ok = ok && (h->partials = (double*)dalloc(h, h->partials_doubles * 8));
     ok = ok && (h->counter = (unsigned int*)dalloc(h, 256));
     ok = ok && (h->scratch = (double*)dalloc(h, 8 * 1024));
+    const size_t region_bytes = (size_t)h->Xr * p->ny * p->nz;
+    if (o.region) {
+        ok = ok && (h->region = (uint8_t*)dalloc(h, region_bytes));
+        ok = ok && (h->rpart = (double*)dalloc(h, (size_t)region_blocks() * LPC_MAX_REGIONS * 6 * 8));
+    }
     // temporaries for the inputs
     double* dF = nullptr; double* dO = nullptr; double* dR0 = nullptr; double* dA = nullptr;
     ok = ok && (dF = (double*)dalloc(h, (size_t)N * 8));
@@ -448,15 +520,25 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid, solid, (size_t)N, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess && rho0) e = cudaMemcpyAsync(dR0, rho0, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess && alpha_links) e = cudaMemcpyAsync(dA, alpha_links, (size_t)N * 24, cudaMemcpyHostToDevice, h->wstream);
+        if (e == cudaSuccess && o.region) {
+            // labels into rows of pitch Xr (0 in the row padding)
+            e = cudaMemsetAsync(h->region, 0, region_bytes, h->wstream);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(h->region, (size_t)h->Xr, o.region, (size_t)p->nx, (size_t)p->nx,
+                                      (size_t)p->ny * p->nz, cudaMemcpyHostToDevice, h->wstream);
+        }
         // the byte mask is stored as given; solid means nonzero
         if (e == cudaSuccess) st = ensure_history(h, 1024);
         if (e == cudaSuccess && st == LPC_OK) {
             LatticeView v = make_view(h, 1);   // writes go to buffer 0
-            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, dA, p->dt, p->kT, h->wstream);
+            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, dA, p->dt, p->kT, rf, h->wstream);
             if (e == cudaSuccess)
                 e = launch_init_state(v, dR0, p->init, dF, h->solid, p->kT, h->scratch, h->wstream);
+            if (e == cudaSuccess) e = launch_reservoir_ghosts(v, rf, h->wstream);
             h->cur = 0;
             if (e == cudaSuccess) e = launch_sum_state(make_view(h, 0), h->wstream);
+            if (e == cudaSuccess)
+                e = launch_region_sums(make_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, h->wstream);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     }
@@ -491,7 +573,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     long long cap = steps + 1 < 1024 ? 1024 : steps + 1;
     long long b = Np * (2 * 4 + 2 * 8 + 2 * 4 * na + 6 * wb + 8) + N;
     b += (long long)device_props().sm_count * 32 * kMaxTB * kNumSums * 8 + 256 + 8 * 1024;
-    b += (long long)history_bytes(cap);
+    b += (long long)history_bytes(cap, 1);
     b += 16 * N;    // transient copies of F and omega during create
     if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 18))     // the automatic schedule's gather form
         b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, p->msd_axes);
@@ -524,6 +606,10 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
         if (!tb_supported(make_view(h, 0), h->p.weight_dtype, block_steps) ||
             !tb_box_dims(make_view(h, 0), h->p.weight_dtype, block_steps, &bw, &bh)) {
             set_error("lattice_set_schedule: TB needs 1 <= block_steps <= min(4, ghost)");
+            return LPC_ERR_INVALID;
+        }
+        if (!tb_depth_allowed(h, block_steps)) {
+            set_error("lattice_set_schedule: lattices with reservoirs or regions take one step per launch");
             return LPC_ERR_INVALID;
         }
         cudaError_t e = tb_prepare(h->p.weight_dtype, block_steps, h->p.msd_axes);
@@ -598,7 +684,7 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
     for (int i = 0; i < count; ++i) {
         int tx, ty, cz;
         const int items = batch_items(make_view(hs[i], hs[i]->cur), &tx, &ty, &cz);
-        if ((size_t)items * kNumSums > hs[i]->partials_doubles) alone.push_back(i);
+        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0) alone.push_back(i);
         else batched.push_back(i);
     }
     static thread_local BatchParams bp;
@@ -696,7 +782,7 @@ lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* ker
     for (int cand = 0; cand <= maxk && st == LPC_OK; ++cand) {
         const bool tb = cand > 0;
         const int K = tb ? cand : 1;
-        if (tb && !tb_supported(make_view(h, 0), h->p.weight_dtype, K)) continue;
+        if (tb && (!tb_supported(make_view(h, 0), h->p.weight_dtype, K) || !tb_depth_allowed(h, K))) continue;
         if (tb) {
             h->kernel = LPC_KERNEL_TB;
             h->kdepth = K;
@@ -826,6 +912,64 @@ lpc_status lattice_msd(lpc_lattice* h, int32_t axis, int64_t first, int64_t coun
     return LPC_OK;
 }
 
+static lpc_status region_check(lpc_lattice* h, int32_t region, const char* who) {
+    if (!h) { set_error(std::string(who) + ": NULL handle"); return LPC_ERR_INVALID; }
+    if (h->nreg == 0 || region < 0 || region >= h->nreg) {
+        set_error(std::string(who) + ": region outside 0..n_regions-1 (or no regions)");
+        return LPC_ERR_INVALID;
+    }
+    return LPC_OK;
+}
+
+lpc_status lattice_fid_region(lpc_lattice* h, int32_t region, int64_t first, int64_t count, double* out) {
+    lpc_status s = region_check(h, region, "lattice_fid_region");
+    if (s == LPC_OK) s = range_check(h, first, count, out, "lattice_fid_region");
+    if (s != LPC_OK || count == 0) return s;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) { lpc_status ds = check_device_error(h); if (ds != LPC_OK) return ds; }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, h->histM + (1 + region) * h->cap + first, sizeof(double2) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_fid_region");
+}
+
+lpc_status lattice_population_region(lpc_lattice* h, int32_t region, int64_t first, int64_t count,
+                                     double* out) {
+    lpc_status s = region_check(h, region, "lattice_population_region");
+    if (s == LPC_OK) s = range_check(h, first, count, out, "lattice_population_region");
+    if (s != LPC_OK || count == 0) return s;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, h->histP + (1 + region) * h->cap + first, sizeof(double) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_population_region");
+}
+
+lpc_status lattice_msd_region(lpc_lattice* h, int32_t region, int32_t axis, int64_t first, int64_t count,
+                              double* out) {
+    lpc_status s = region_check(h, region, "lattice_msd_region");
+    if (s == LPC_OK) s = range_check(h, first, count, out, "lattice_msd_region");
+    if (s != LPC_OK) return s;
+    if (axis < 0 || axis > 2 || !(h->p.msd_axes >> axis & 1)) { set_error("lattice_msd_region: axis not enabled"); return LPC_ERR_INVALID; }
+    if (count == 0) return LPC_OK;
+    cudaSetDevice(h->device);
+    const long long upto = first + count - 1;
+    std::vector<double> d((size_t)(upto > 0 ? upto : 1));
+    double P0 = 0.0;
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess && upto > 0)
+        e = cudaMemcpy(d.data(), h->histD + ((1 + region) * 3 + axis) * h->cap, sizeof(double) * upto,
+                       cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&P0, h->histP, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice_msd_region");
+    double acc = 0.0;
+    for (long long n = 0; n <= upto; ++n) {
+        if (n >= first) out[n - first] = acc / P0;
+        if (n < upto) acc += d[(size_t)n];
+    }
+    return LPC_OK;
+}
+
 static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* out, int32_t out_is_device, const char* who) {
     if (!h || !out) { set_error(std::string(who) + ": NULL argument"); return LPC_ERR_INVALID; }
     Entry en(h);
@@ -891,14 +1035,19 @@ struct StateHeader {
     char magic[8];
     int32_t nx, ny, nz, msd_axes;
     int64_t steps;
+    int32_t n_regions, reserved;
 };
 
+static const char kStateMagic[9] = "LPC3DST2";
+
+// header, state (rho, m, mu), then one history set (M, P, dMSD of the
+// enabled axes) for the totals and one per region
 static size_t state_bytes(const lpc_lattice* h) {
     int na = 0;
     for (int a = 0; a < 3; ++a) na += h->p.msd_axes >> a & 1;
     const size_t N = (size_t)h->N;
     const size_t S = (size_t)h->steps;
-    return sizeof(StateHeader) + N * (12 + 4 * na) + (S + 1) * 24 + S * 8 * na;
+    return sizeof(StateHeader) + N * (12 + 4 * na) + (1 + (size_t)h->nreg) * ((S + 1) * 24 + S * 8 * na);
 }
 
 lpc_status lattice_state_size(lpc_lattice* h, size_t* bytes) {
@@ -912,8 +1061,10 @@ lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
     if (bytes < state_bytes(h)) { set_error("lattice_get_state: buffer too small"); return LPC_ERR_INVALID; }
     char* p = (char*)buf;
     StateHeader hd;
-    memcpy(hd.magic, "LPC3DST1", 8);
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, kStateMagic, 8);
     hd.nx = h->p.nx; hd.ny = h->p.ny; hd.nz = h->p.nz; hd.msd_axes = h->p.msd_axes; hd.steps = h->steps;
+    hd.n_regions = h->nreg;
     memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     const size_t N = (size_t)h->N;
@@ -930,14 +1081,17 @@ lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
         p += N * 4;
     }
     const size_t S = (size_t)h->steps;
-    cudaError_t e = cudaMemcpy(p, h->histM, (S + 1) * 16, cudaMemcpyDeviceToHost);
-    p += (S + 1) * 16;
-    if (e == cudaSuccess) e = cudaMemcpy(p, h->histP, (S + 1) * 8, cudaMemcpyDeviceToHost);
-    p += (S + 1) * 8;
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-        if (!(h->p.msd_axes >> a & 1)) continue;
-        if (S > 0) e = cudaMemcpy(p, h->histD + a * h->cap, S * 8, cudaMemcpyDeviceToHost);
-        p += S * 8;
+    cudaError_t e = cudaSuccess;
+    for (int set = 0; set <= h->nreg && e == cudaSuccess; ++set) {
+        e = cudaMemcpy(p, h->histM + set * h->cap, (S + 1) * 16, cudaMemcpyDeviceToHost);
+        p += (S + 1) * 16;
+        if (e == cudaSuccess) e = cudaMemcpy(p, h->histP + set * h->cap, (S + 1) * 8, cudaMemcpyDeviceToHost);
+        p += (S + 1) * 8;
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+            if (!(h->p.msd_axes >> a & 1)) continue;
+            if (S > 0) e = cudaMemcpy(p, h->histD + (set * 3 + a) * h->cap, S * 8, cudaMemcpyDeviceToHost);
+            p += S * 8;
+        }
     }
     return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_get_state");
 }
@@ -947,8 +1101,8 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
     if (bytes < sizeof(StateHeader)) { set_error("lattice_set_state: buffer too small"); return LPC_ERR_INVALID; }
     StateHeader hd;
     memcpy(&hd, buf, sizeof hd);
-    if (memcmp(hd.magic, "LPC3DST1", 8) != 0 || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz ||
-        hd.msd_axes != h->p.msd_axes || hd.steps < 0) {
+    if (memcmp(hd.magic, kStateMagic, 8) != 0 || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz ||
+        hd.msd_axes != h->p.msd_axes || hd.steps < 0 || hd.n_regions != h->nreg) {
         set_error("lattice_set_state: blob does not match this lattice");
         return LPC_ERR_INVALID;
     }
@@ -980,14 +1134,18 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
         p += N * 4;
     }
     const size_t S = (size_t)hd.steps;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->histM, p, (S + 1) * 16, cudaMemcpyHostToDevice, h->wstream);
-    p += (S + 1) * 16;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->histP, p, (S + 1) * 8, cudaMemcpyHostToDevice, h->wstream);
-    p += (S + 1) * 8;
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-        if (!(h->p.msd_axes >> a & 1)) continue;
-        if (S > 0) e = cudaMemcpyAsync(h->histD + a * h->cap, p, S * 8, cudaMemcpyHostToDevice, h->wstream);
-        p += S * 8;
+    for (int set = 0; set <= h->nreg && e == cudaSuccess; ++set) {
+        e = cudaMemcpyAsync(h->histM + set * h->cap, p, (S + 1) * 16, cudaMemcpyHostToDevice, h->wstream);
+        p += (S + 1) * 16;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->histP + set * h->cap, p, (S + 1) * 8, cudaMemcpyHostToDevice, h->wstream);
+        p += (S + 1) * 8;
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+            if (!(h->p.msd_axes >> a & 1)) continue;
+            if (S > 0)
+                e = cudaMemcpyAsync(h->histD + (set * 3 + a) * h->cap, p, S * 8, cudaMemcpyHostToDevice, h->wstream);
+            p += S * 8;
+        }
     }
     const long long dstep = hd.steps;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &dstep, 8, cudaMemcpyHostToDevice, h->wstream);
@@ -1049,7 +1207,10 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
     const long long minus_one = -1;
     e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
     if (e == cudaSuccess) e = launch_restart(make_view(h, h->cur), h->wstream);
+    if (e == cudaSuccess) e = launch_reservoir_ghosts(make_view(h, h->cur), h->rf, h->wstream);
     if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
+    if (e == cudaSuccess)
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
     {

@@ -57,7 +57,11 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, F, omega, solid, *, periodic=(1, 1, 1), alpha=0.005,
                  dt=5e-6, kT=1.0, rho0=None, weight_dtype=0, msd_axes=0, init=0, ghost=0,
-                 stream=None, allocator="torch", alpha_links=None):
+                 stream=None, allocator="torch", alpha_links=None, reservoirs=None, region=None,
+                 n_regions=0):
+        """reservoirs: None or 6 faces (f = 2 a + side), each None (wall) or
+        (F_res, rho_res, m_res complex); region: None or per-site labels
+        < n_regions for region-resolved sums."""
         self.lib = B.load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -82,6 +86,26 @@ class Lattice:
             links = np.ascontiguousarray(alpha_links, dtype=np.float64).reshape(-1)
             if links.size != 3 * self.N:
                 raise ValueError("alpha_links must hold 3 values per site")
+        opts = None
+        self.n_regions = 0
+        if reservoirs is not None or region is not None:
+            opts = B.lpc_options()
+            if links is not None:
+                opts.alpha_links = links.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            for f, e in enumerate(reservoirs or ()):
+                if e is None:
+                    continue
+                F_res, rho_res, m_res = e
+                opts.reservoir[f] = B.lpc_reservoir(1, 0, float(F_res), float(rho_res),
+                                                    complex(m_res).real, complex(m_res).imag)
+            if region is not None:
+                reg = np.ascontiguousarray(region, dtype=np.uint8).reshape(-1)
+                if reg.size != self.N:
+                    raise ValueError("region labels must hold one value per site")
+                self._region = reg
+                opts.region = reg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                opts.n_regions = int(n_regions)
+                self.n_regions = int(n_regions)
         self._alloc = None
         aptr = None
         if allocator == "torch":
@@ -92,7 +116,12 @@ class Lattice:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = ctypes.c_void_p()
-        if links is None:
+        if opts is not None:
+            st = self.lib.lattice_create_ex(ctypes.byref(p), ctypes.byref(opts), _dp(F), _dp(om),
+                                            sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                            _dp(r0) if r0 is not None else None, aptr,
+                                            ctypes.c_void_p(self.stream), ctypes.byref(h))
+        elif links is None:
             st = self.lib.lattice_create(ctypes.byref(p), _dp(F), _dp(om),
                                          sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                          _dp(r0) if r0 is not None else None, aptr,
@@ -110,7 +139,8 @@ class Lattice:
         """Create from an ``lpc_inputs.LatticeInput``."""
         args = dict(periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
                     rho0=inp.rho0, weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes,
-                    alpha_links=getattr(inp, "alpha_links", None))
+                    alpha_links=getattr(inp, "alpha_links", None),
+                    reservoirs=getattr(inp, "reservoirs", None))
         args.update(kw)
         return cls(inp.nx, inp.ny, inp.nz, inp.F, inp.omega, inp.solid, **args)
 
@@ -192,6 +222,31 @@ class Lattice:
             count = self.steps_done + 1 - first
         out = np.empty(count)
         B.check(self.lib.lattice_msd(self.h, int(axis), int(first), int(count), _dp(out)), self.lib)
+        return out
+
+    def fid_region(self, region, first=0, count=None):
+        """M_r(n): the FID summed over the sites labelled ``region``."""
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(2 * count)
+        B.check(self.lib.lattice_fid_region(self.h, int(region), int(first), int(count), _dp(out)), self.lib)
+        return out[0::2] + 1j * out[1::2]
+
+    def population_region(self, region, first=0, count=None):
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(count)
+        B.check(self.lib.lattice_population_region(self.h, int(region), int(first), int(count), _dp(out)),
+                self.lib)
+        return out
+
+    def msd_region(self, region, axis, first=0, count=None):
+        """The part of MSD_axis(n) accrued while particles were in ``region``."""
+        if count is None:
+            count = self.steps_done + 1 - first
+        out = np.empty(count)
+        B.check(self.lib.lattice_msd_region(self.h, int(region), int(axis), int(first), int(count), _dp(out)),
+                self.lib)
         return out
 
     # -- fields ----------------------------------------------------------------

@@ -124,3 +124,49 @@ def test_link_factors_outside_unit_interval_rejected(lib, bad):
                                   None, dp(links), None, None, ctypes.byref(h))
     assert st == B.LPC_ERR_INVALID and not h.value
     assert b"link" in lib.lpc_last_error()
+
+
+def _create_ex(lib, p, opts):
+    N = p.nx * p.ny * p.nz
+    z = np.zeros(N)
+    h = ctypes.c_void_p()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.lattice_create_ex(ctypes.byref(p), ctypes.byref(opts), dp(z), dp(z),
+                               np.zeros(N, np.uint8).ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                               None, None, None, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("face,periodic,vals,msg", [
+    (0, (1, 1, 1), (0.0, 1.0, 1.0), "non-periodic"),       # reservoir on a periodic axis
+    (4, (0, 0, 0), (0.0, 1.0, 1.0), "x and y faces"),      # z faces have no ghost layer
+    (2, (1, 0, 1), (float("nan"), 1.0, 1.0), "non-finite"),
+    (3, (1, 0, 1), (0.0, float("inf"), 1.0), "non-finite"),
+])
+def test_invalid_reservoirs_rejected_on_host(lib, face, periodic, vals, msg):
+    opts = B.lpc_options()
+    opts.reservoir[face] = B.lpc_reservoir(1, 0, vals[0], vals[1], vals[2], 0.0)
+    st, h = _create_ex(lib, _params(periodic=periodic), opts)
+    assert st == B.LPC_ERR_INVALID and not h.value
+    assert msg in lib.lpc_last_error().decode()
+
+
+@pytest.mark.parametrize("labels_max,n_regions", [(3, 3), (0, 0), (0, 5), (1, -1)])
+def test_invalid_regions_rejected_on_host(lib, labels_max, n_regions):
+    p = _params()
+    opts = B.lpc_options()
+    lab = np.zeros(64, np.uint8)
+    lab[17] = labels_max
+    opts.region = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    opts.n_regions = n_regions
+    st, h = _create_ex(lib, p, opts)
+    assert st == B.LPC_ERR_INVALID and not h.value
+    assert b"region" in lib.lpc_last_error()
+
+
+def test_region_queries_reject_null_handle(lib):
+    out = np.zeros(4)
+    dp = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.lattice_fid_region(None, 0, 0, 1, dp) == B.LPC_ERR_INVALID
+    assert lib.lattice_population_region(None, 0, 0, 1, dp) == B.LPC_ERR_INVALID
+    assert lib.lattice_msd_region(None, 0, 0, 0, 1, dp) == B.LPC_ERR_INVALID

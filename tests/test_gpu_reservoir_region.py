@@ -1,0 +1,212 @@
+"""GPU parity of reservoir faces and region-resolved sums against the FP64 oracle.
+
+Reservoir faces (Sec. 3.2 item 1: field values fixed in the ghost layer of a
+non-periodic face) and region labels (the spectra and diffusion of separate
+parts of a system, Sec. 4) run through lattice_create_ex.  Tolerances as in
+test_gpu_parity: relative L2 <= 1e-5 against the matched-input oracle (its
+own FP32 roundings) and <= 1e-4 against the exact oracle; weights within one
+unit in the last place of the oracle's rounding, with the same zero pattern.
+Reservoir values are exactly representable in FP32, so the GPU's FP32 ghost
+values equal the oracle's FP64 ones.
+"""
+import numpy as np
+import pytest
+
+import lpc_inputs
+import oracle
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+RES = ((-0.75, 1.25, 0.5 - 0.25j), (0.5, 0.625, 1.0 + 0.0j), None, (-1.5, 2.0, 0.0j), None, None)
+
+
+def _lattice(inp, sched, **kw):
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+    lat = Lattice.from_input(inp, **kw)
+    if sched == "step1":
+        lat.set_schedule(B.LPC_KERNEL_STEP1, 1)
+    elif sched == "tb1":
+        lat.set_schedule(B.LPC_KERNEL_TB, 1)
+    return lat
+
+
+def _advance(lat, sched, steps):
+    from paper_2603_22553_b300.lattice import step_many
+    if sched == "batch":
+        step_many([lat], [steps])
+    else:
+        lat.step(steps)
+
+
+def _read(lat, axes):
+    g = dict(M=lat.fid(), P=lat.population(), rho=lat.density().astype(np.float64), m=lat.magnetization())
+    for a in range(3):
+        if axes >> a & 1:
+            g["msd%d" % a] = lat.msd(a)
+    return g
+
+
+def _ulp_diff(a, b, bits):
+    scale = np.where(b != 0, 2.0 ** (np.floor(np.log2(np.abs(np.where(b != 0, b, 1.0)))) - (bits - 1)), 1.0)
+    return np.abs(a - b) / scale
+
+
+def _compare_fid_pop(g, o, tol):
+    assert H.rel_l2(g["M"], o.M) <= tol
+    assert H.rel_l2(g["P"], o.P) <= tol
+    assert H.rel_l2(g["rho"], o.rho) <= tol
+    assert H.rel_l2(g["m"], o.m) <= tol
+
+
+@pytest.mark.parametrize("sched", ["auto", "step1", "tb1", "batch"])
+def test_reservoir_parity(sched):
+    shape = (20, 36, 130)
+    inp = lpc_inputs.random_case(shape, 301, periodic=(0, 0, 1), alpha=0.8, msd_axes=5)
+    inp.reservoirs = RES
+    lat = _lattice(inp, sched)
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    w = lat.weights().reshape(6, -1).T.astype(np.float64)
+    assert np.array_equal(w == 0, pk.w == 0), "link geometry differs"
+    assert _ulp_diff(w, pk.w, 24).max() <= 1.0
+    steps = 150
+    _advance(lat, sched, steps)
+    g = _read(lat, 5)
+    o = oracle.run(pk, inp.uniform_rho0(), steps, msd_axes=5)
+    _compare_fid_pop(g, o, 1e-5)
+    for a in (0, 2):
+        sl = slice(10, None)
+        assert np.max(np.abs(g["msd%d" % a][sl] - o.msd(a)[sl]) / np.abs(o.msd(a)[sl])) <= 1e-5
+    oe = oracle.run(oracle.pack_input(inp), inp.uniform_rho0(), steps, msd_axes=5)
+    _compare_fid_pop(g, oe, 1e-4)
+    # population flows through the reservoir faces: not conserved
+    assert abs(g["P"][-1] / g["P"][0] - 1.0) > 1e-3
+    lat.close()
+
+
+@pytest.mark.parametrize("sched", ["step1", "tb1"])
+def test_reservoir_grand_canonical_equilibrium(sched):
+    """Reservoirs at the same (F_res, rho_res) on both x faces: the
+    equilibration phase converges to rho_res exp(-(F - F_res)) on every pore
+    site (all connected: no solids); the propagation phase then restarts with
+    the reservoirs' own magnetisation m_res = 0 in the ghost layer (oracle run
+    from the equilibrated populations)."""
+    shape = (8, 16, 64)
+    inp = lpc_inputs.random_case(shape, 302, periodic=(0, 1, 1), solid_frac=0.0, F_sd=0.7, alpha=1.0,
+                                 msd_axes=0)
+    F_res, rho_res = -0.5, 1.5
+    inp.reservoirs = ((F_res, rho_res, 0.0), (F_res, rho_res, 0.0), None, None, None, None)
+    lat = _lattice(inp, sched)
+    # a fixed number of steps (threshold 0): the slowest mode decays by
+    # far more than e^-20 over them; FP32 rounding keeps max |drho| near 1 ulp
+    it, diff = lat.equilibrate(0.0, 30000, check_every=1000)
+    assert it == 30000 and diff < 1e-5
+    rho_eq = rho_res * np.exp(-(inp.F - F_res))
+    rho = lat.density().astype(np.float64)
+    assert H.rel_l2(rho, rho_eq) <= 1e-5
+    steps = 40
+    lat.step(steps)
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    o = oracle.run(pk, rho, steps, msd_axes=0)
+    assert H.rel_l2(lat.fid(), o.M) <= 1e-5
+    assert H.rel_l2(lat.population(), o.P) <= 1e-5
+    # the reservoirs bring in no magnetisation: |M| falls below P
+    assert abs(lat.fid()[-1]) < lat.population()[-1] * (1 - 1e-4)
+    lat.close()
+
+
+def test_reservoir_rejects_deep_temporal_blocks():
+    from paper_2603_22553_b300 import binding as B
+    inp = lpc_inputs.random_case((8, 16, 64), 303, periodic=(0, 1, 1), msd_axes=0)
+    inp.reservoirs = RES[:2] + (None,) * 4
+    lat = _lattice(inp, "auto", ghost=4)
+    with pytest.raises(B.LPCError):
+        lat.set_schedule(B.LPC_KERNEL_TB, 2)
+    lat.close()
+
+
+def _region_case(shape=(20, 36, 130), seed=311, n_regions=3, **kw):
+    inp = lpc_inputs.random_case(shape, seed, periodic=(1, 0, 1), alpha=0.9, msd_axes=5, **kw)
+    lab = lpc_inputs.random_regions(shape, seed + 1, n_regions)
+    return inp, lab
+
+
+@pytest.mark.parametrize("sched", ["auto", "step1", "tb1"])
+def test_region_sums_parity(sched):
+    inp, lab = _region_case()
+    lat = _lattice(inp, sched, region=lab, n_regions=3)
+    steps = 120
+    lat.step(steps)
+    o = oracle.run(oracle.pack_input(inp, oracle.MODE_F32), inp.uniform_rho0(), steps, msd_axes=5,
+                   region=lab, n_regions=3)
+    M, P = lat.fid(), lat.population()
+    Mr = np.array([lat.fid_region(r) for r in range(3)])
+    Pr = np.array([lat.population_region(r) for r in range(3)])
+    for r in range(3):
+        assert H.rel_l2(Mr[r], o.Mr[r]) <= 1e-5
+        assert H.rel_l2(Pr[r], o.Pr[r]) <= 1e-5
+        for a in (0, 2):
+            ms = lat.msd_region(r, a)
+            ref = np.concatenate([[0.0], np.cumsum(o.Dr[r, a])]) / o.P[0]
+            assert np.max(np.abs(ms[10:] - ref[10:])) <= 1e-5 * np.max(np.abs(ref[10:]))
+    # the regions partition the lattice
+    assert np.max(np.abs(Mr.sum(axis=0) - M)) <= 1e-6 * P[0]
+    assert np.max(np.abs(Pr.sum(axis=0) - P)) <= 1e-6 * P[0]
+    for a in (0, 2):
+        tot = sum(lat.msd_region(r, a) for r in range(3))
+        assert np.max(np.abs(tot - lat.msd(a))) <= 1e-6 * np.max(np.abs(lat.msd(a)))
+    lat.close()
+
+
+def test_region_lattice_in_step_many_and_checkpoint():
+    """A region lattice advanced by lattice_step_many beside a plain one gives
+    the region sums of lattice_step_n; a checkpoint carries the region
+    histories and resuming continues them bit for bit."""
+    from paper_2603_22553_b300.lattice import step_many
+    inp, lab = _region_case(shape=(12, 20, 70), seed=321, n_regions=2)
+    plain = lpc_inputs.random_case((10, 18, 40), 322, msd_axes=5)
+    a = _lattice(inp, "auto", region=lab, n_regions=2)
+    b = _lattice(plain, "auto")
+    step_many([a, b], [50, 30])
+    c = _lattice(inp, "auto", region=lab, n_regions=2)
+    c.step(50)
+    for r in range(2):
+        assert np.array_equal(a.fid_region(r), c.fid_region(r))
+        assert np.array_equal(a.msd_region(r, 0), c.msd_region(r, 0))
+    blob = c.get_state()
+    c.step(20)
+    d = _lattice(inp, "auto", region=lab, n_regions=2)
+    d.set_state(blob)
+    d.step(20)
+    for r in range(2):
+        assert np.array_equal(c.fid_region(r), d.fid_region(r))
+        assert np.array_equal(c.population_region(r), d.population_region(r))
+        assert np.array_equal(c.msd_region(r, 2), d.msd_region(r, 2))
+    for lat in (a, b, c, d):
+        lat.close()
+
+
+def test_supercapacitor_slab_regions_and_reservoirs():
+    """A scaled supercapacitor slab (electrode / bulk / electrode along x,
+    BF16 weights, MSD along x) with reservoirs on both x faces and the three
+    parts as regions: per-region FIDs, spectra (Parseval: the spectrum error
+    equals the FID error) and MSD against the matched-input oracle."""
+    from paper_2603_22553_b300 import downstream
+    inp = lpc_inputs.supercapacitor(nx=160, ny=32, nz=24, electrode=64, bulk=32, steps=300)
+    inp.alpha = 0.3
+    inp.reservoirs = ((0.0, 1.0, 1.0), (0.0, 1.0, 1.0), None, None, None, None)
+    lab, names = lpc_inputs.region_labels(inp)
+    assert names == ("electrode_minus", "bulk", "electrode_plus")
+    lat = _lattice(inp, "auto", region=lab, n_regions=3)
+    lat.step(inp.steps)
+    o = oracle.run(oracle.pack_input(inp, oracle.MODE_BF16), inp.uniform_rho0(), inp.steps, msd_axes=1,
+                   region=lab, n_regions=3)
+    for r in range(3):
+        Mr = lat.fid_region(r)
+        assert H.rel_l2(Mr, o.Mr[r]) <= 1e-5
+        _, _, S = downstream.spectrum(Mr, inp.dt)
+        _, So = oracle.spectrum(o.Mr[r], inp.dt)
+        assert H.rel_l2(S, So) <= 1e-5
+    assert H.rel_l2(lat.fid(), o.M) <= 1e-5
+    lat.close()
