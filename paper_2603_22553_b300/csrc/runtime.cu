@@ -1149,6 +1149,11 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
     }
     const long long dstep = hd.steps;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &dstep, 8, cudaMemcpyHostToDevice, h->wstream);
+    // the region pass takes dMSD_r of the current state ahead of its step (the
+    // blob holds steps entries): recompute entry `steps` (M_r and P_r come out
+    // the same bits)
+    if (e == cudaSuccess)
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     dfree(h, tmp, N * 8);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_set_state");
