@@ -24,7 +24,7 @@ constexpr int kFlush = 16;                      // segments summed in FP32
 
 template <typename WT>
 __global__ void __launch_bounds__(kWarps * 32) k_region_sums(LatticeView v, double* __restrict__ part,
-                                                          unsigned int* __restrict__ done) {
+                                                          unsigned int* __restrict__ done, int dmsd_only) {
     __shared__ double sm[kWarps][kRQ];
     __shared__ unsigned int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -99,10 +99,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_region_sums(LatticeView v, doub
         const long long n = *v.step;
         if (r < v.nreg && n >= 0) {
             const long long set = 1 + r;
-            if (q == 0) v.histM[set * v.cap + n].x = t;
-            else if (q == 1) v.histM[set * v.cap + n].y = t;
-            else if (q == 2) v.histP[set * v.cap + n] = t;
-            else if (v.msd_axes >> (q - 3) & 1) v.histD[(set * 3 + (q - 3)) * v.cap + n] = t;
+            if (q < 3 && dmsd_only) {
+            } else if (q == 0) {
+                v.histM[set * v.cap + n].x = t;
+            } else if (q == 1) {
+                v.histM[set * v.cap + n].y = t;
+            } else if (q == 2) {
+                v.histP[set * v.cap + n] = t;
+            } else if (v.msd_axes >> (q - 3) & 1) {
+                v.histD[(set * 3 + (q - 3)) * v.cap + n] = t;
+            }
         }
     }
     __syncthreads();
@@ -114,12 +120,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_region_sums(LatticeView v, doub
 int region_blocks() { return device_props().sm_count * 2; }
 
 cudaError_t launch_region_sums(const LatticeView& v, int wdtype, double* part, unsigned int* done,
-                               cudaStream_t st) {
+                               bool dmsd_only, cudaStream_t st) {
     if (v.nreg <= 0 || !v.region) return cudaSuccess;
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_region_sums<__nv_bfloat16><<<region_blocks(), kWarps * 32, 0, st>>>(v, part, done);
+        k_region_sums<__nv_bfloat16><<<region_blocks(), kWarps * 32, 0, st>>>(v, part, done, dmsd_only);
     else
-        k_region_sums<float><<<region_blocks(), kWarps * 32, 0, st>>>(v, part, done);
+        k_region_sums<float><<<region_blocks(), kWarps * 32, 0, st>>>(v, part, done, dmsd_only);
     return cudaGetLastError();
 }
 

@@ -81,13 +81,14 @@ namespace {
 
 // state slot:  rho [TY+2][W] f32 | m [TY+2][W] f32x2 | mu_n [TY+2][W] f32
 // static slot: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2 | dm_n [TY][64] f32x2
+//              | lab [TY][64] u8 (region labels, with regions only)
 // (each part on a 128-byte boundary, as TMA requires)
 struct T1Slots {
     int m, mu[3], bytes1;
-    int s, R, dm[3], bytes2;
+    int s, R, dm[3], lab, bytes2;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
-__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only) {
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg = false) {
     T1Slots L;
     const int H = TY + 2;
     int off = up128(H * W * 4);
@@ -108,24 +109,36 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
         L.dm[n] = off;
         if (n < nmsd) off += up128(C * 8);
     }
+    L.lab = off;
+    if (reg) off += up128(C);
     L.bytes2 = off;
     return L;
 }
+
+// Per-item sums: the totals, and with regions each region's (KS values,
+// stored with a stride of KSP doubles per warp in shared memory).
+template <bool REG> struct ItemSums {
+    static constexpr int KS = REG ? kNumSums * (1 + LPC_MAX_REGIONS) : kNumSums;
+    static constexpr int KSP = REG ? 32 : 8;
+};
 
 struct SlotHdr {
     int tile, za, n, pad;
 };
 
-template <typename WT, int MSD, int NC, bool RHO>
+template <typename WT, int MSD, int NC, bool RHO, bool REG>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
 k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     static_assert(!RHO || MSD == 0, "the rho-only step carries no moments");
+    static_assert(!RHO || !REG, "the rho-only step takes no sums");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc(MSD);
     constexpr int TY = NC;                    // one core row per consumer warp
+    constexpr int KS = ItemSums<REG>::KS, KSP = ItemSums<REG>::KSP;
+    static_assert(KS <= 32, "one lane per item sum");
     const int W = g.W, S1 = g.S1, S2 = g.S2;
-    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO);
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
@@ -135,8 +148,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     uint64_t* ifree = empty2 + S2;                                  // [2] item sums combined
     unsigned int* icount = reinterpret_cast<unsigned int*>(ifree + 2);   // [2] warps done
     SlotHdr* hdr = reinterpret_cast<SlotHdr*>(ifree + 3);          // [S1]
-    double* ired = reinterpret_cast<double*>(hdr + S1);            // [2][NC][8] per-warp item sums
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(ired + 2 * NC * 8);
+    double* ired = reinterpret_cast<double*>(hdr + S1);            // [2][NC][KSP] per-warp item sums
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(ired + 2 * NC * KSP);
     volatile unsigned int* issued1 = reinterpret_cast<volatile unsigned int*>(abort_flag + 1);
     volatile unsigned int* issued2 = issued1 + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -224,6 +237,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         if (!RHO) tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
 #pragma unroll
                         for (int m = 0; m < NMSD; ++m) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
+                        if (REG) tma3(st + SL.lab, &maps.glab, fb, sx, sy, z);
                         *issued2 = ++n2;
                         c2.next(S2);
                     }
@@ -238,6 +252,12 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     } else {
         // ---------------- consumer warps: core row `warp`, sites x0 + 2 lane + {0, 1}
         float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // region sums (REG): [region][Mre, Mim, P, dMSD of each MSD axis in order]
+        float preg[REG ? LPC_MAX_REGIONS : 1][3 + NMSD];
+#pragma unroll
+        for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
+#pragma unroll
+            for (int q = 0; q < 3 + NMSD; ++q) preg[r][q] = 0.f;
         bool ok = true;
         Cursor w1{0, 0u}, w2{0, 0u};
         unsigned int kitem = 0;                          // items this warp has finished
@@ -338,6 +358,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     site_rho_m(q1, sp.y, ro1, mo1);
                 }
                 float muo0[3], muo1[3];
+                float dd0[3] = {0.f, 0.f, 0.f}, dd1[3] = {0.f, 0.f, 0.f};
+                int lab0 = 0, lab1 = 0;
+                if (REG) {
+                    const unsigned int l2 = *reinterpret_cast<const unsigned short*>(ss + SL.lab + os);
+                    lab0 = (int)(l2 & 0xffu);
+                    lab1 = (int)(l2 >> 8);
+                }
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n) {
                     const int a = axis_of[n];
@@ -353,8 +380,10 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     float wo0[6], wo1[6];
                     wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
                     wo1[2 * a] = dm.z; wo1[2 * a + 1] = dm.w;
-                    if (site0) part[3 + a] += site_dmsd(wo0, muc[n].x, q0.rc, a);
-                    if (site1) part[3 + a] += site_dmsd(wo1, muc[n].y, q1.rc, a);
+                    dd0[n] = site_dmsd(wo0, muc[n].x, q0.rc, a);
+                    dd1[n] = site_dmsd(wo1, muc[n].y, q1.rc, a);
+                    if (site0) part[3 + a] += dd0[n];
+                    if (site1) part[3 + a] += dd1[n];
                 }
                 // both slots are read: release them before the stores
                 __syncwarp();
@@ -386,6 +415,18 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 }
                 if (site0) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
                 if (site1) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
+                if (REG) {
+                    // sites outside the lattice (ragged tiles) are skipped as in the totals
+#pragma unroll
+                    for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
+                        const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
+                        preg[r][0] += (s0r ? mo0.x : 0.f) + (s1r ? mo1.x : 0.f);
+                        preg[r][1] += (s0r ? mo0.y : 0.f) + (s1r ? mo1.y : 0.f);
+                        preg[r][2] += (s0r ? ro0 : 0.f) + (s1r ? ro1 : 0.f);
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) preg[r][3 + n] += (s0r ? dd0[n] : 0.f) + (s1r ? dd1[n] : 0.f);
+                    }
+                }
                 // this plane is the next one's "below"
                 br = r_c;
                 bm = m_c;
@@ -408,8 +449,30 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
 #pragma unroll
             for (int qq = 0; qq < kNumSums; ++qq) {
                 const float t = warp_sum_f32(part[qq]);
-                if (lane == 0) ired[(b * NC + warp) * 8 + qq] = (double)t;
+                if (lane == 0) ired[(b * NC + warp) * KSP + qq] = (double)t;
                 part[qq] = 0.f;
+            }
+            if (REG) {
+#pragma unroll
+                for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
+                    double* dst = ired + (b * NC + warp) * KSP + kNumSums * (1 + r);
+#pragma unroll
+                    for (int qq = 0; qq < 3; ++qq) {
+                        const float t = warp_sum_f32(preg[r][qq]);
+                        if (lane == 0) dst[qq] = (double)t;
+                        preg[r][qq] = 0.f;
+                    }
+#pragma unroll
+                    for (int a = 0, n = 0; a < 3; ++a) {
+                        float t = 0.f;
+                        if (MSD >> a & 1) {
+                            t = warp_sum_f32(preg[r][3 + n]);
+                            preg[r][3 + n] = 0.f;
+                            ++n;
+                        }
+                        if (lane == 0) dst[3 + a] = (double)t;
+                    }
+                }
             }
             __syncwarp();
             unsigned int last = 0u;
@@ -420,11 +483,11 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 __threadfence_block();
-                if (lane < kNumSums) {
+                if (lane < KS) {
                     double sum = 0.0;
-                    for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * 8 + lane];
+                    for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * KSP + lane];
                     const int item = (h.za / g.cz) * g.tiles + h.tile;
-                    v.partials[(long long)item * kNumSums + lane] = sum;
+                    v.partials[(long long)item * KS + lane] = sum;
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -451,26 +514,31 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         return;
     }
     // the rings are idle now: their memory is the final reduction's scratch
-    items_finish<NC + 1>(v, g.n_items, reinterpret_cast<double*>(ring1));
+    if constexpr (REG)
+        items_finish_regions<NC + 1, KS>(v, g.n_items, reinterpret_cast<double*>(ring1));
+    else
+        items_finish<NC + 1>(v, g.n_items, reinterpret_cast<double*>(ring1));
 }
 
-template <typename WT, int MSD, int NC>
-void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false>); }
+template <typename WT, int MSD, int NC, bool REG>
+void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false, REG>); }
 
 template <int NC>
 void* t1_rho_kernel(int wdtype) {
-    return wdtype == LPC_WEIGHTS_BF16 ? reinterpret_cast<void*>(&k_step_tma1<__nv_bfloat16, 0, NC, true>)
-                                      : reinterpret_cast<void*>(&k_step_tma1<float, 0, NC, true>);
+    return wdtype == LPC_WEIGHTS_BF16 ? reinterpret_cast<void*>(&k_step_tma1<__nv_bfloat16, 0, NC, true, false>)
+                                      : reinterpret_cast<void*>(&k_step_tma1<float, 0, NC, true, false>);
 }
 
-template <int NC>
+template <int NC, bool REG>
 void* t1_kernel_shape(int wdtype, int msd) {
     static void* tab[2][8] = {
-        {t1_fn<float, 0, NC>(), t1_fn<float, 1, NC>(), t1_fn<float, 2, NC>(), t1_fn<float, 3, NC>(),
-         t1_fn<float, 4, NC>(), t1_fn<float, 5, NC>(), t1_fn<float, 6, NC>(), t1_fn<float, 7, NC>()},
-        {t1_fn<__nv_bfloat16, 0, NC>(), t1_fn<__nv_bfloat16, 1, NC>(), t1_fn<__nv_bfloat16, 2, NC>(),
-         t1_fn<__nv_bfloat16, 3, NC>(), t1_fn<__nv_bfloat16, 4, NC>(), t1_fn<__nv_bfloat16, 5, NC>(),
-         t1_fn<__nv_bfloat16, 6, NC>(), t1_fn<__nv_bfloat16, 7, NC>()}};
+        {t1_fn<float, 0, NC, REG>(), t1_fn<float, 1, NC, REG>(), t1_fn<float, 2, NC, REG>(),
+         t1_fn<float, 3, NC, REG>(), t1_fn<float, 4, NC, REG>(), t1_fn<float, 5, NC, REG>(),
+         t1_fn<float, 6, NC, REG>(), t1_fn<float, 7, NC, REG>()},
+        {t1_fn<__nv_bfloat16, 0, NC, REG>(), t1_fn<__nv_bfloat16, 1, NC, REG>(),
+         t1_fn<__nv_bfloat16, 2, NC, REG>(), t1_fn<__nv_bfloat16, 3, NC, REG>(),
+         t1_fn<__nv_bfloat16, 4, NC, REG>(), t1_fn<__nv_bfloat16, 5, NC, REG>(),
+         t1_fn<__nv_bfloat16, 6, NC, REG>(), t1_fn<__nv_bfloat16, 7, NC, REG>()}};
     return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
 }
 
@@ -491,9 +559,10 @@ int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 // Ring depth d and shared memory of a tile height: S1 = d + 2 state slots
 // (centre and above held), S2 = d + 1 static slots (centre held); per slot one
 // full and one empty barrier, and a header per state slot.
-void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only) {
-    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only);
-    const int fixed = 128 + 3 * 8 + 2 * TY * 8 * 8 + 64;     // slack, item barriers/counts/sums, flags
+void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg = false) {
+    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg);
+    const int ksp = reg ? ItemSums<true>::KSP : ItemSums<false>::KSP;
+    const int fixed = 128 + 3 * 8 + 2 * TY * ksp * 8 + 64;   // slack, item barriers/counts/sums, flags
     const int budget = device_props().max_smem_optin - 1024 - fixed;
     const int per1 = L.bytes1 + 16 + 16, per2 = L.bytes2 + 16;
     int d = (budget - 2 * per1 - per2) / (per1 + per2);
@@ -506,9 +575,10 @@ void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only) {
     c.smem = fixed + c.S1 * per1 + c.S2 * per2;
 }
 
-// The tile height comes from the full step (so that one set of tensor maps
-// serves both modes); the rho-only step re-sizes its rings for it.
-T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false) {
+// The tile height comes from the full step without regions (so that one set
+// of tensor maps serves every mode); the rho-only step and the step with
+// region sums re-size their rings for it.
+T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool reg = false) {
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     T1Choice c{};
@@ -518,18 +588,24 @@ T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false) {
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
     if (rho_only) t1_rings(c, c.TY, 0, wb, true);
+    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true);
     return c;
 }
 
-void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false) {
+void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false, bool reg = false) {
     if (rho_only) {
         if (TY == 16) return t1_rho_kernel<16>(wdtype);
         if (TY == 12) return t1_rho_kernel<12>(wdtype);
         return t1_rho_kernel<8>(wdtype);
     }
-    if (TY == 16) return t1_kernel_shape<16>(wdtype, msd);
-    if (TY == 12) return t1_kernel_shape<12>(wdtype, msd);
-    return t1_kernel_shape<8>(wdtype, msd);
+    if (reg) {
+        if (TY == 16) return t1_kernel_shape<16, true>(wdtype, msd);
+        if (TY == 12) return t1_kernel_shape<12, true>(wdtype, msd);
+        return t1_kernel_shape<8, true>(wdtype, msd);
+    }
+    if (TY == 16) return t1_kernel_shape<16, false>(wdtype, msd);
+    if (TY == 12) return t1_kernel_shape<12, false>(wdtype, msd);
+    return t1_kernel_shape<8, false>(wdtype, msd);
 }
 
 }  // namespace
@@ -538,8 +614,8 @@ cudaError_t t1_prepare(int wdtype, int msd) {
     static bool done[2][8] = {};
     bool& d = done[wdtype == LPC_WEIGHTS_BF16][msd & 7];
     if (d) return cudaSuccess;
-    for (int i = 0; i < 6; ++i) {
-        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, i >= 3);
+    for (int i = 0; i < 9; ++i) {
+        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, i / 3 == 1, i / 3 == 2);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, fn);
         if (e != cudaSuccess) return e;
@@ -554,6 +630,17 @@ cudaError_t t1_prepare(int wdtype, int msd) {
 // Item partials fit the lattice's partials buffer (sm_count * 32 * kMaxTB
 // entries of kNumSums doubles).
 static int t1_max_items() { return device_props().sm_count * 32 * kMaxTB; }
+
+// The fused region sums need labels of width 64 per tile row, ring memory for
+// the final reduction's scratch (KS doubles per thread) and a ring depth of
+// at least one plane.
+bool t1_fused_regions(const LatticeView& v, int wdtype) {
+    if (v.nreg <= 0 || !v.region) return false;
+    const T1Choice c = t1_choose(v, wdtype, false, true);
+    const long long scratch = (long long)ItemSums<true>::KS * (c.TY + 1) * 32 * 8;
+    const long long rings = (long long)c.S1 * c.L.bytes1 + (long long)c.S2 * c.L.bytes2;
+    return c.depth >= 1 && scratch <= rings && v.Xr == v.Xs;
+}
 
 bool t1_supported(const LatticeView& v, int wdtype) {
     const T1Choice c = t1_choose(v, wdtype);
@@ -605,6 +692,12 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
             const cuuint32_t bd[4] = {(cuuint32_t)(2 * kTX), TY, 1, 1};
             ok = ok && tma_encode(&maps->gdm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.gdm, dd, sd, bd);
         }
+        if (v.region && v.Xr == v.Xs) {
+            const cuuint64_t dl[3] = {Xs, ny, nz};
+            const cuuint64_t sl[2] = {Xs, Xs * ny};
+            const cuuint32_t bl[3] = {(cuuint32_t)kTX, TY, 1};
+            ok = ok && tma_encode(&maps->glab, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, v.region, dl, sl, bl);
+        }
     }
     return ok;
 }
@@ -612,7 +705,8 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st, bool rho_only) {
     if (!v.gwin) return cudaErrorInvalidValue;
-    const T1Choice c = t1_choose(v, wdtype, rho_only);
+    const bool reg = !rho_only && t1_fused_regions(v, wdtype);
+    const T1Choice c = t1_choose(v, wdtype, rho_only, reg);
     const int nmsd = rho_only ? 0 : popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     T1Geom g;
@@ -623,7 +717,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.slot1 = c.L.bytes1;
     g.slot2 = c.L.bytes2;
     g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
-    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 8 * nmsd));
+    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 8 * nmsd) + (reg ? 1 : 0));
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
@@ -646,7 +740,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     LatticeView vv = v;
     TBMaps mm = maps;
     void* args[] = {&mm, &vv, &g};
-    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes, rho_only), dim3((unsigned)grid),
+    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes, rho_only, reg), dim3((unsigned)grid),
                             dim3((c.TY + 1) * 32), args, (size_t)c.smem, st);
 }
 

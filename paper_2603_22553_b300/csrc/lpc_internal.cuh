@@ -280,6 +280,59 @@ __device__ void items_finish(const LatticeView& v, int n_items, double* scratch)
     }
 }
 
+// items_finish for items that also carry region sums: per item KS values,
+// the kNumSums totals followed by kNumSums values for each of
+// LPC_MAX_REGIONS regions (M_r and P_r of the output state, dMSD_r of the
+// input state, like the totals); region r < v.nreg goes to history set 1 + r.
+// `scratch` holds KS * blockDim doubles.
+template <int NW, int KS>
+__device__ void items_finish_regions(const LatticeView& v, int n_items, double* scratch) {
+    static_assert(KS == kNumSums * (1 + LPC_MAX_REGIONS), "totals and every region slot");
+    const int T = NW * 32;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    __shared__ unsigned int is_last_r;
+    __syncthreads();
+    if (tid == 0) is_last_r = (atomicAdd(v.counter, 1u) == (unsigned)nblk - 1u);
+    __syncthreads();
+    if (!is_last_r) return;
+    __threadfence();
+    for (int q0 = 0; q0 < KS; q0 += kNumSums) {
+        double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int b = tid; b < n_items; b += T) {
+            const double* p = v.partials + (long long)b * KS + q0;
+#pragma unroll
+            for (int q = 0; q < kNumSums; ++q) acc[q] += __ldcg(p + q);
+        }
+#pragma unroll
+        for (int q = 0; q < kNumSums; ++q) scratch[(q0 + q) * T + tid] = acc[q];
+    }
+    __syncthreads();
+    const long long n = *v.step;
+    for (int q = warp; q < KS; q += NW) {
+        double s = 0.0;
+        for (int t = lane; t < T; t += 32) s += scratch[q * T + t];
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            const int set = q / kNumSums, qq = q % kNumSums;
+            if (set <= v.nreg) {
+                if (qq == 0) v.histM[set * v.cap + n + 1].x = s;
+                else if (qq == 1) v.histM[set * v.cap + n + 1].y = s;
+                else if (qq == 2) v.histP[set * v.cap + n + 1] = s;
+                else if (n >= 0 && (v.msd_axes >> (qq - 3) & 1))
+                    v.histD[((long long)set * 3 + (qq - 3)) * v.cap + n] = s;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *v.step = n + 1;
+        *v.counter = 0u;
+    }
+}
+
 // Same, starting from per-warp sums in registers (lane 0 of every warp).
 template <int NW>
 __device__ void block_finish(const LatticeView& v, double (*acc)[kNumSums], int levels,
@@ -313,10 +366,11 @@ cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const
 // both state buffers.
 cudaError_t launch_reservoir_ghosts(const LatticeView& v, const ResFaces& rf, cudaStream_t st);
 // Region-resolved sums of the current state (index *v.step): M_r, P_r and
-// dMSD_a,r into the region histories; part: [region_blocks(v)][6 * nreg]
-// doubles, done: a zeroed completion counter.
+// dMSD_a,r into the region histories (dmsd_only: dMSD_a,r alone); part:
+// [region_blocks()][6 * LPC_MAX_REGIONS] doubles, done: a zeroed completion
+// counter.
 cudaError_t launch_region_sums(const LatticeView& v, int wdtype, double* part, unsigned int* done,
-                               cudaStream_t st);
+                               bool dmsd_only, cudaStream_t st);
 int region_blocks();
 cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
                               const double* F, const uint8_t* solid, double kT, double* scratch,
@@ -365,6 +419,10 @@ bool tb_box_dims(const LatticeView& v, int wdtype, int K, int* W, int* H);
 // equilibration phase.
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st, bool rho_only = false);
+// The one-step TMA kernel takes the region sums itself for this lattice
+// (labels staged with the static data); otherwise the separate region pass
+// runs after it.
+bool t1_fused_regions(const LatticeView& v, int wdtype);
 cudaError_t t1_prepare(int wdtype, int msd);
 bool t1_supported(const LatticeView& v, int wdtype);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);

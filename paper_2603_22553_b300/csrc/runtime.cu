@@ -278,8 +278,10 @@ lpc_status launch_one(lpc_lattice* h, cudaStream_t st, bool tb = false) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     h->cur ^= 1;
-    if (h->nreg > 0) {
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, st);
+    // region sums: taken by the one-step TMA kernel itself where it can,
+    // else by the separate pass over the new state
+    if (h->nreg > 0 && !(tb && h->kdepth == 1 && t1_fused_regions(make_view(h, h->cur), h->p.weight_dtype))) {
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "region sums launch");
     }
     return LPC_OK;
@@ -486,7 +488,9 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     ok = ok && (h->w = dalloc(h, Np * 6 * wbytes(h)));
     ok = ok && (h->R = (float2*)dalloc(h, Np * 8));
     ok = ok && (h->solid = (uint8_t*)dalloc(h, (size_t)N));
-    h->partials_doubles = (size_t)device_props().sm_count * 32 * kMaxTB * kNumSums;
+    // per-item sums of the one-step kernels: the totals, and with regions each region's
+    h->partials_doubles = (size_t)device_props().sm_count * 32 * kMaxTB * kNumSums *
+                          (o.region ? 1 + LPC_MAX_REGIONS : 1);
     ok = ok && (h->partials = (double*)dalloc(h, h->partials_doubles * 8));
     ok = ok && (h->counter = (unsigned int*)dalloc(h, 256));
     ok = ok && (h->scratch = (double*)dalloc(h, 8 * 1024));
@@ -538,7 +542,7 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
             h->cur = 0;
             if (e == cudaSuccess) e = launch_sum_state(make_view(h, 0), h->wstream);
             if (e == cudaSuccess)
-                e = launch_region_sums(make_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, h->wstream);
+                e = launch_region_sums(make_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     }
@@ -1150,10 +1154,9 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
     const long long dstep = hd.steps;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &dstep, 8, cudaMemcpyHostToDevice, h->wstream);
     // the region pass takes dMSD_r of the current state ahead of its step (the
-    // blob holds steps entries): recompute entry `steps` (M_r and P_r come out
-    // the same bits)
+    // blob holds steps entries): recompute entry `steps` of dMSD_r only
     if (e == cudaSuccess)
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, h->wstream);
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, true, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     dfree(h, tmp, N * 8);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_set_state");
@@ -1215,7 +1218,7 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
     if (e == cudaSuccess) e = launch_reservoir_ghosts(make_view(h, h->cur), h->rf, h->wstream);
     if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
     if (e == cudaSuccess)
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, h->wstream);
+        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
     {

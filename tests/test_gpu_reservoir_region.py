@@ -203,7 +203,7 @@ def test_supercapacitor_slab_regions_and_reservoirs():
     inp.reservoirs = ((0.0, 1.0, 1.0), (0.0, 1.0, 1.0), None, None, None, None)
     lab, names = lpc_inputs.region_labels(inp)
     assert names == ("electrode_minus", "bulk", "electrode_plus")
-    lat = _lattice(inp, "auto", region=lab, n_regions=3)
+    lat = _lattice(inp, "tb1", region=lab, n_regions=3)
     lat.step(inp.steps)
     o = oracle.run(oracle.pack_input(inp, oracle.MODE_BF16), inp.uniform_rho0(), inp.steps, msd_axes=1,
                    region=lab, n_regions=3)
@@ -215,3 +215,54 @@ def test_supercapacitor_slab_regions_and_reservoirs():
         assert H.rel_l2(S, So) <= 1e-5
     assert H.rel_l2(lat.fid(), o.M) <= 1e-5
     lat.close()
+
+
+@pytest.mark.parametrize("msd_axes,wdt", [(0, 0), (1, 1), (7, 0)])
+def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
+    """The one-step TMA kernel takes the region sums itself (labels staged with
+    the static data): states and totals are bit-identical to the same kernel
+    without regions, and the region sums agree with the separate region pass
+    of the register-pipelined schedule to FP32 summation order; the
+    checkpoint of a fused run resumes bit for bit."""
+    from paper_2603_22553_b300 import binding as B
+    shape = (40, 64, 200)
+    inp = lpc_inputs.random_case(shape, 331, periodic=(1, 1, 0), alpha=0.7, msd_axes=msd_axes,
+                                 weight_dtype=wdt)
+    lab = lpc_inputs.random_regions(shape, 332, 4)
+    steps = 64
+    fused = _lattice(inp, "auto", region=lab, n_regions=4)
+    assert fused.info()["kernel"] == B.LPC_KERNEL_TB and fused.info()["block_steps"] == 1
+    plain = _lattice(inp, "auto")
+    sep = _lattice(inp, "step1", region=lab, n_regions=4)
+    for lat in (fused, plain, sep):
+        lat.step(steps)
+    assert np.array_equal(fused.density(), plain.density())
+    assert np.array_equal(fused.density(), sep.density())
+    assert np.array_equal(fused.fid(), plain.fid())
+    assert np.array_equal(fused.population(), plain.population())
+    P0 = fused.population()[0]
+    for r in range(4):
+        assert np.max(np.abs(fused.fid_region(r) - sep.fid_region(r))) <= 1e-6 * P0
+        assert np.max(np.abs(fused.population_region(r) - sep.population_region(r))) <= 1e-6 * P0
+        for a in range(3):
+            if msd_axes >> a & 1:
+                ref = sep.msd_region(r, a)
+                assert np.max(np.abs(fused.msd_region(r, a) - ref)) <= 1e-6 * np.max(np.abs(ref))
+                assert np.array_equal(fused.msd(a), plain.msd(a))
+    o = oracle.run(oracle.pack_input(inp, H.MODE_OF_DTYPE[wdt]), inp.uniform_rho0(), steps,
+                   msd_axes=msd_axes, region=lab, n_regions=4)
+    for r in range(4):
+        assert H.rel_l2(fused.fid_region(r), o.Mr[r]) <= 1e-5
+    blob = fused.get_state()
+    fused.step(10)
+    again = _lattice(inp, "auto", region=lab, n_regions=4)
+    again.set_state(blob)
+    again.step(10)
+    for r in range(4):
+        assert np.array_equal(fused.fid_region(r), again.fid_region(r))
+        assert np.array_equal(fused.population_region(r), again.population_region(r))
+        for a in range(3):
+            if msd_axes >> a & 1:
+                assert np.array_equal(fused.msd_region(r, a), again.msd_region(r, a))
+    for lat in (fused, plain, sep, again):
+        lat.close()
