@@ -44,9 +44,29 @@ WORKLOADS = {
     "supercapacitor_2048x256x256": dict(make=lambda: lpc_inputs.supercapacitor(),
                                         desc="2048x256x256 electrode/bulk/electrode slab, x walls, "
                                              "BF16 weights, MSD along x", sub=64),
+    "supercapacitor_regions_2048x256x256": dict(
+        make=lambda: _with_bulk_reservoirs(lpc_inputs.supercapacitor()),
+        desc="2048x256x256 electrode/bulk/electrode slab, BF16 weights, MSD along x, bulk-electrolyte "
+             "reservoirs (F = 0, rho = m = 1) on both x faces, FID/population/MSD per region "
+             "(electrode-, bulk, electrode+)", sub=64, regions=True),
     "particle_32": dict(make=lambda: lpc_inputs.particle(msd_axes=0), desc="32^3 particle, FP32",
                         sub=32),
 }
+
+
+def _with_bulk_reservoirs(inp):
+    """Reservoir faces at x = -1 and x = nx holding bulk electrolyte
+    (F = 0, rho = 1, m = 1)."""
+    inp.reservoirs = ((0.0, 1.0, 1.0), (0.0, 1.0, 1.0), None, None, None, None)
+    return inp
+
+
+def region_kwargs(wl, inp):
+    """Lattice keyword arguments for a workload with region-resolved sums."""
+    if not wl.get("regions"):
+        return {}
+    lab, names = lpc_inputs.region_labels(inp)
+    return {"region": lab, "n_regions": len(names)}
 
 
 def parse():
@@ -263,7 +283,8 @@ def run_ours(args):
     sched = parse_schedule(args.schedule)
     ghost = (sched[1] + 1) // 2 * 2 if sched and sched[0] == B.LPC_KERNEL_TB else 0
 
-    lat = Lattice.from_input(inp, ghost=ghost)
+    rkw = region_kwargs(wl, inp)
+    lat = Lattice.from_input(inp, ghost=ghost, **rkw)
     if sched:
         lat.set_schedule(*sched)
     info = lat.info()
@@ -345,7 +366,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         lat = Lattice(inp.nx, inp.ny, inp.nz, Fp.numpy(), Op.numpy(), Sp.numpy(),
                       periodic=inp.periodic, alpha=inp.alpha, dt=inp.dt, kT=inp.kT,
-                      weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes, ghost=ghost)
+                      weight_dtype=inp.weight_dtype, msd_axes=inp.msd_axes, ghost=ghost,
+                      reservoirs=inp.reservoirs, **rkw)
         if sched:
             lat.set_schedule(*sched)
         for _ in range(args.steps):
@@ -359,7 +381,7 @@ def run_ours(args):
             t = torch.tensor([te], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        h2d = Fp.numel() * 8 + Op.numel() * 8 + Sp.numel()
+        h2d = Fp.numel() * 8 + Op.numel() * 8 + Sp.numel() + (inp.n_sites if rkw else 0)
         d2h = M.size * 16 + rho.size * 4
         e2e = {"value": ws * N * lattice_steps / te, "unit": "site-updates/s",
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),

@@ -114,7 +114,8 @@ typedef struct {
     int32_t block_steps;      /* time steps per launch of that kernel */
     int32_t reserved;
     int64_t device_bytes;     /* device memory held by the lattice */
-    int64_t bytes_per_site_update; /* algorithmic HBM bytes of one site update */
+    int64_t bytes_per_site_update; /* algorithmic HBM bytes of one site update (state
+                                      read + write, hop weights, R, moments, region label) */
 } lpc_info;
 
 /*

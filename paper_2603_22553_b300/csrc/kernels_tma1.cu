@@ -416,15 +416,37 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 if (site0) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
                 if (site1) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
                 if (REG) {
-                    // sites outside the lattice (ragged tiles) are skipped as in the totals
+                    // sites outside the lattice (ragged tiles) are skipped as in the
+                    // totals.  Regions are mostly large connected parts, so a warp's
+                    // 64 sites usually share one label: then the pair sums go to that
+                    // region alone (a warp-uniform branch), else every region takes
+                    // its masked share.
+                    const int labw = __shfl_sync(0xffffffffu, lab0, 0);
+                    const bool uni = __all_sync(0xffffffffu, (!site0 || lab0 == labw) && (!site1 || lab1 == labw));
+                    if (uni) {
+                        float pv[3 + NMSD];
+                        pv[0] = (site0 ? mo0.x : 0.f) + (site1 ? mo1.x : 0.f);
+                        pv[1] = (site0 ? mo0.y : 0.f) + (site1 ? mo1.y : 0.f);
+                        pv[2] = (site0 ? ro0 : 0.f) + (site1 ? ro1 : 0.f);
 #pragma unroll
-                    for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
-                        const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
-                        preg[r][0] += (s0r ? mo0.x : 0.f) + (s1r ? mo1.x : 0.f);
-                        preg[r][1] += (s0r ? mo0.y : 0.f) + (s1r ? mo1.y : 0.f);
-                        preg[r][2] += (s0r ? ro0 : 0.f) + (s1r ? ro1 : 0.f);
+                        for (int n = 0; n < NMSD; ++n) pv[3 + n] = (site0 ? dd0[n] : 0.f) + (site1 ? dd1[n] : 0.f);
 #pragma unroll
-                        for (int n = 0; n < NMSD; ++n) preg[r][3 + n] += (s0r ? dd0[n] : 0.f) + (s1r ? dd1[n] : 0.f);
+                        for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
+                            if (labw == r) {
+#pragma unroll
+                                for (int q = 0; q < 3 + NMSD; ++q) preg[r][q] += pv[q];
+                            }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
+                            const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
+                            preg[r][0] += (s0r ? mo0.x : 0.f) + (s1r ? mo1.x : 0.f);
+                            preg[r][1] += (s0r ? mo0.y : 0.f) + (s1r ? mo1.y : 0.f);
+                            preg[r][2] += (s0r ? ro0 : 0.f) + (s1r ? ro1 : 0.f);
+#pragma unroll
+                            for (int n = 0; n < NMSD; ++n)
+                                preg[r][3 + n] += (s0r ? dd0[n] : 0.f) + (s1r ? dd1[n] : 0.f);
+                        }
                     }
                 }
                 // this plane is the next one's "below"

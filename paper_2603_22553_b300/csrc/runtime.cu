@@ -863,6 +863,7 @@ lpc_status lattice_info(lpc_lattice* h, lpc_info* out) {
     out->device_bytes = h->device_bytes;
     long long b = 24 + 6 * (long long)wbytes(h) + 8;
     for (int a = 0; a < 3; ++a) if (h->p.msd_axes >> a & 1) b += 8;
+    if (h->nreg > 0) b += 1;      // the region label of the site
     out->bytes_per_site_update = b;
     return LPC_OK;
 }
