@@ -252,12 +252,32 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     } else {
         // ---------------- consumer warps: core row `warp`, sites x0 + 2 lane + {0, 1}
         float part[kNumSums] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // region sums (REG): [region][Mre, Mim, P, dMSD of each MSD axis in order]
+        // Region sums (REG): preg[region][Mre, Mim, P, dMSD of each MSD axis in
+        // order].  Regions are mostly large connected parts, so a warp's row of
+        // 64 sites usually lies in one region for many planes: `part` then sums
+        // the current run of planes whose row has the warp-uniform label
+        // `curlab`, and is added to that region when the label changes (and at
+        // the item's end, where the totals become the sum over regions).  Rows
+        // that mix labels add each site to its region directly.
         float preg[REG ? LPC_MAX_REGIONS : 1][3 + NMSD];
 #pragma unroll
         for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
 #pragma unroll
             for (int q = 0; q < 3 + NMSD; ++q) preg[r][q] = 0.f;
+        int curlab = -1;
+        auto flush_run = [&]() {
+#pragma unroll
+            for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
+                if (curlab == r) {
+                    preg[r][0] += part[0];
+                    preg[r][1] += part[1];
+                    preg[r][2] += part[2];
+#pragma unroll
+                    for (int n = 0; n < NMSD; ++n) preg[r][3 + n] += part[3 + axis_of[n]];
+                }
+#pragma unroll
+            for (int q = 0; q < kNumSums; ++q) part[q] = 0.f;
+        };
         bool ok = true;
         Cursor w1{0, 0u}, w2{0, 0u};
         unsigned int kitem = 0;                          // items this warp has finished
@@ -360,10 +380,18 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 float muo0[3], muo1[3];
                 float dd0[3] = {0.f, 0.f, 0.f}, dd1[3] = {0.f, 0.f, 0.f};
                 int lab0 = 0, lab1 = 0;
+                bool to_part = true;            // this plane's sums go to `part`
                 if (REG) {
                     const unsigned int l2 = *reinterpret_cast<const unsigned short*>(ss + SL.lab + os);
                     lab0 = (int)(l2 & 0xffu);
                     lab1 = (int)(l2 >> 8);
+                    // sites outside the lattice (ragged tiles) count for no region
+                    const int labw = __shfl_sync(0xffffffffu, lab0, 0);
+                    to_part = __all_sync(0xffffffffu, (!site0 || lab0 == labw) && (!site1 || lab1 == labw));
+                    if (!to_part || labw != curlab) {
+                        flush_run();
+                        curlab = to_part ? labw : -1;
+                    }
                 }
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n) {
@@ -382,8 +410,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     wo1[2 * a] = dm.z; wo1[2 * a + 1] = dm.w;
                     dd0[n] = site_dmsd(wo0, muc[n].x, q0.rc, a);
                     dd1[n] = site_dmsd(wo1, muc[n].y, q1.rc, a);
-                    if (site0) part[3 + a] += dd0[n];
-                    if (site1) part[3 + a] += dd1[n];
+                    if (site0 && to_part) part[3 + a] += dd0[n];
+                    if (site1 && to_part) part[3 + a] += dd1[n];
                 }
                 // both slots are read: release them before the stores
                 __syncwarp();
@@ -413,40 +441,18 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x + 1, y, zoff, muo1[n]);
                     }
                 }
-                if (site0) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
-                if (site1) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
-                if (REG) {
-                    // sites outside the lattice (ragged tiles) are skipped as in the
-                    // totals.  Regions are mostly large connected parts, so a warp's
-                    // 64 sites usually share one label: then the pair sums go to that
-                    // region alone (a warp-uniform branch), else every region takes
-                    // its masked share.
-                    const int labw = __shfl_sync(0xffffffffu, lab0, 0);
-                    const bool uni = __all_sync(0xffffffffu, (!site0 || lab0 == labw) && (!site1 || lab1 == labw));
-                    if (uni) {
-                        float pv[3 + NMSD];
-                        pv[0] = (site0 ? mo0.x : 0.f) + (site1 ? mo1.x : 0.f);
-                        pv[1] = (site0 ? mo0.y : 0.f) + (site1 ? mo1.y : 0.f);
-                        pv[2] = (site0 ? ro0 : 0.f) + (site1 ? ro1 : 0.f);
+                if (site0 && to_part) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
+                if (site1 && to_part) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
+                if (REG && !to_part) {
 #pragma unroll
-                        for (int n = 0; n < NMSD; ++n) pv[3 + n] = (site0 ? dd0[n] : 0.f) + (site1 ? dd1[n] : 0.f);
+                    for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
+                        const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
+                        preg[r][0] += (s0r ? mo0.x : 0.f) + (s1r ? mo1.x : 0.f);
+                        preg[r][1] += (s0r ? mo0.y : 0.f) + (s1r ? mo1.y : 0.f);
+                        preg[r][2] += (s0r ? ro0 : 0.f) + (s1r ? ro1 : 0.f);
 #pragma unroll
-                        for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
-                            if (labw == r) {
-#pragma unroll
-                                for (int q = 0; q < 3 + NMSD; ++q) preg[r][q] += pv[q];
-                            }
-                    } else {
-#pragma unroll
-                        for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
-                            const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
-                            preg[r][0] += (s0r ? mo0.x : 0.f) + (s1r ? mo1.x : 0.f);
-                            preg[r][1] += (s0r ? mo0.y : 0.f) + (s1r ? mo1.y : 0.f);
-                            preg[r][2] += (s0r ? ro0 : 0.f) + (s1r ? ro1 : 0.f);
-#pragma unroll
-                            for (int n = 0; n < NMSD; ++n)
-                                preg[r][3 + n] += (s0r ? dd0[n] : 0.f) + (s1r ? dd1[n] : 0.f);
-                        }
+                        for (int n = 0; n < NMSD; ++n)
+                            preg[r][3 + n] += (s0r ? dd0[n] : 0.f) + (s1r ? dd1[n] : 0.f);
                     }
                 }
                 // this plane is the next one's "below"
@@ -468,6 +474,19 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             const unsigned int use = kitem >> 1;
             if (use > 0) ok = mbar_wait_bounded(&ifree[b], (use - 1) & 1u);
             if (!ok) break;
+            if (REG) {
+                // close the run; the item's totals are the sums over regions
+                flush_run();
+                curlab = -1;
+#pragma unroll
+                for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
+                    part[0] += preg[r][0];
+                    part[1] += preg[r][1];
+                    part[2] += preg[r][2];
+#pragma unroll
+                    for (int n = 0; n < NMSD; ++n) part[3 + axis_of[n]] += preg[r][3 + n];
+                }
+            }
 #pragma unroll
             for (int qq = 0; qq < kNumSums; ++qq) {
                 const float t = warp_sum_f32(part[qq]);

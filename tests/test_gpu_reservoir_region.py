@@ -220,10 +220,11 @@ def test_supercapacitor_slab_regions_and_reservoirs():
 @pytest.mark.parametrize("msd_axes,wdt", [(0, 0), (1, 1), (7, 0)])
 def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
     """The one-step TMA kernel takes the region sums itself (labels staged with
-    the static data): states and totals are bit-identical to the same kernel
-    without regions, and the region sums agree with the separate region pass
-    of the register-pipelined schedule to FP32 summation order; the
-    checkpoint of a fused run resumes bit for bit."""
+    the static data): states are bit-identical to the same kernel without
+    regions and its totals (there the sums over regions) agree to FP32
+    summation order, as do the region sums with the separate region pass of
+    the register-pipelined schedule; the checkpoint of a fused run resumes
+    bit for bit."""
     from paper_2603_22553_b300 import binding as B
     shape = (40, 64, 200)
     inp = lpc_inputs.random_case(shape, 331, periodic=(1, 1, 0), alpha=0.7, msd_axes=msd_axes,
@@ -238,9 +239,9 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
         lat.step(steps)
     assert np.array_equal(fused.density(), plain.density())
     assert np.array_equal(fused.density(), sep.density())
-    assert np.array_equal(fused.fid(), plain.fid())
-    assert np.array_equal(fused.population(), plain.population())
     P0 = fused.population()[0]
+    assert np.max(np.abs(fused.fid() - plain.fid())) <= 1e-6 * P0
+    assert np.max(np.abs(fused.population() - plain.population())) <= 1e-6 * P0
     for r in range(4):
         assert np.max(np.abs(fused.fid_region(r) - sep.fid_region(r))) <= 1e-6 * P0
         assert np.max(np.abs(fused.population_region(r) - sep.population_region(r))) <= 1e-6 * P0
@@ -248,7 +249,8 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
             if msd_axes >> a & 1:
                 ref = sep.msd_region(r, a)
                 assert np.max(np.abs(fused.msd_region(r, a) - ref)) <= 1e-6 * np.max(np.abs(ref))
-                assert np.array_equal(fused.msd(a), plain.msd(a))
+                ref = plain.msd(a)
+                assert np.max(np.abs(fused.msd(a) - ref)) <= 1e-6 * np.max(np.abs(ref))
     o = oracle.run(oracle.pack_input(inp, H.MODE_OF_DTYPE[wdt]), inp.uniform_rho0(), steps,
                    msd_axes=msd_axes, region=lab, n_regions=4)
     for r in range(4):
