@@ -673,12 +673,12 @@ cudaError_t t1_prepare(int wdtype, int msd) {
 static int t1_max_items() { return device_props().sm_count * 32 * kMaxTB; }
 
 // The fused region sums need labels of width 64 per tile row, ring memory for
-// the final reduction's scratch (KS doubles per thread) and a ring depth of
-// at least one plane.
+// the final reduction's scratch (32 doubles per warp) and a ring depth of at
+// least one plane.
 bool t1_fused_regions(const LatticeView& v, int wdtype) {
     if (v.nreg <= 0 || !v.region) return false;
     const T1Choice c = t1_choose(v, wdtype, false, true);
-    const long long scratch = (long long)ItemSums<true>::KS * (c.TY + 1) * 32 * 8;
+    const long long scratch = 32LL * (c.TY + 1) * 8;
     const long long rings = (long long)c.S1 * c.L.bytes1 + (long long)c.S2 * c.L.bytes2;
     return c.depth >= 1 && scratch <= rings && v.Xr == v.Xs;
 }

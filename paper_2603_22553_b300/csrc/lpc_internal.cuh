@@ -284,11 +284,14 @@ __device__ void items_finish(const LatticeView& v, int n_items, double* scratch)
 // the kNumSums totals followed by kNumSums values for each of
 // LPC_MAX_REGIONS regions (M_r and P_r of the output state, dMSD_r of the
 // input state, like the totals); region r < v.nreg goes to history set 1 + r.
-// `scratch` holds KS * blockDim doubles.
+// The last block reads n_items * KS doubles: warp w takes a fixed contiguous
+// chunk of items with lane q on value q (coalesced rows), spreading item j of
+// the chunk over 16 accumulators (j mod 16) that are added in a fixed tree,
+// then warp 0 adds the warps in order.  `scratch` holds 32 * NW doubles.
 template <int NW, int KS>
 __device__ void items_finish_regions(const LatticeView& v, int n_items, double* scratch) {
-    static_assert(KS == kNumSums * (1 + LPC_MAX_REGIONS), "totals and every region slot");
-    const int T = NW * 32;
+    static_assert(KS == kNumSums * (1 + LPC_MAX_REGIONS) && KS <= 32, "totals and every region slot");
+    constexpr int A = 16;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
@@ -299,31 +302,36 @@ __device__ void items_finish_regions(const LatticeView& v, int n_items, double* 
     __syncthreads();
     if (!is_last_r) return;
     __threadfence();
-    for (int q0 = 0; q0 < KS; q0 += kNumSums) {
-        double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int b = tid; b < n_items; b += T) {
-            const double* p = v.partials + (long long)b * KS + q0;
+    const int chunk = (n_items + NW - 1) / NW;
+    const int b0 = min(n_items, warp * chunk), b1 = min(n_items, b0 + chunk);
+    double acc[A];
 #pragma unroll
-            for (int q = 0; q < kNumSums; ++q) acc[q] += __ldcg(p + q);
+    for (int j = 0; j < A; ++j) acc[j] = 0.0;
+    if (lane < KS) {
+        const double* p = v.partials + lane;
+        for (int b = b0; b < b1; b += A) {
+#pragma unroll
+            for (int j = 0; j < A; ++j)
+                if (b + j < b1) acc[j] += __ldcg(p + (long long)(b + j) * KS);
         }
-#pragma unroll
-        for (int q = 0; q < kNumSums; ++q) scratch[(q0 + q) * T + tid] = acc[q];
     }
+#pragma unroll
+    for (int w = A / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) acc[j] += acc[j + w];
+    scratch[warp * 32 + lane] = acc[0];
     __syncthreads();
     const long long n = *v.step;
-    for (int q = warp; q < KS; q += NW) {
+    if (warp == 0 && lane < KS) {
         double s = 0.0;
-        for (int t = lane; t < T; t += 32) s += scratch[q * T + t];
-        s = warp_sum_f64(s);
-        if (lane == 0) {
-            const int set = q / kNumSums, qq = q % kNumSums;
-            if (set <= v.nreg) {
-                if (qq == 0) v.histM[set * v.cap + n + 1].x = s;
-                else if (qq == 1) v.histM[set * v.cap + n + 1].y = s;
-                else if (qq == 2) v.histP[set * v.cap + n + 1] = s;
-                else if (n >= 0 && (v.msd_axes >> (qq - 3) & 1))
-                    v.histD[((long long)set * 3 + (qq - 3)) * v.cap + n] = s;
-            }
+        for (int w = 0; w < NW; ++w) s += scratch[w * 32 + lane];
+        const int set = lane / kNumSums, qq = lane % kNumSums;
+        if (set <= v.nreg) {
+            if (qq == 0) v.histM[set * v.cap + n + 1].x = s;
+            else if (qq == 1) v.histM[set * v.cap + n + 1].y = s;
+            else if (qq == 2) v.histP[set * v.cap + n + 1] = s;
+            else if (n >= 0 && (v.msd_axes >> (qq - 3) & 1))
+                v.histD[((long long)set * 3 + (qq - 3)) * v.cap + n] = s;
         }
     }
     __syncthreads();
