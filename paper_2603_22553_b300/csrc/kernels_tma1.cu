@@ -265,7 +265,9 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
 #pragma unroll
             for (int q = 0; q < 3 + NMSD; ++q) preg[r][q] = 0.f;
         int curlab = -1;
+        unsigned int touched = 0u;      // regions with sums in this item (warp-uniform)
         auto flush_run = [&]() {
+            if (curlab >= 0) touched |= 1u << curlab;
 #pragma unroll
             for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r)
                 if (curlab == r) {
@@ -444,6 +446,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 if (site0 && to_part) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }
                 if (site1 && to_part) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro1; }
                 if (REG && !to_part) {
+                    touched |= __reduce_or_sync(0xffffffffu, (site0 ? 1u << lab0 : 0u) | (site1 ? 1u << lab1 : 0u));
 #pragma unroll
                     for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
                         const bool s0r = site0 && lab0 == r, s1r = site1 && lab1 == r;
@@ -494,26 +497,32 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 part[qq] = 0.f;
             }
             if (REG) {
+                // only the regions this warp met in the item need a butterfly
 #pragma unroll
                 for (int r = 0; r < (REG ? LPC_MAX_REGIONS : 1); ++r) {
                     double* dst = ired + (b * NC + warp) * KSP + kNumSums * (1 + r);
+                    if (touched >> r & 1u) {
 #pragma unroll
-                    for (int qq = 0; qq < 3; ++qq) {
-                        const float t = warp_sum_f32(preg[r][qq]);
-                        if (lane == 0) dst[qq] = (double)t;
-                        preg[r][qq] = 0.f;
-                    }
-#pragma unroll
-                    for (int a = 0, n = 0; a < 3; ++a) {
-                        float t = 0.f;
-                        if (MSD >> a & 1) {
-                            t = warp_sum_f32(preg[r][3 + n]);
-                            preg[r][3 + n] = 0.f;
-                            ++n;
+                        for (int qq = 0; qq < 3; ++qq) {
+                            const float t = warp_sum_f32(preg[r][qq]);
+                            if (lane == 0) dst[qq] = (double)t;
+                            preg[r][qq] = 0.f;
                         }
-                        if (lane == 0) dst[3 + a] = (double)t;
+#pragma unroll
+                        for (int a = 0, n = 0; a < 3; ++a) {
+                            float t = 0.f;
+                            if (MSD >> a & 1) {
+                                t = warp_sum_f32(preg[r][3 + n]);
+                                preg[r][3 + n] = 0.f;
+                                ++n;
+                            }
+                            if (lane == 0) dst[3 + a] = (double)t;
+                        }
+                    } else if (lane < kNumSums) {
+                        dst[lane] = 0.0;
                     }
                 }
+                touched = 0u;
             }
             __syncwarp();
             unsigned int last = 0u;
