@@ -49,6 +49,11 @@ WORKLOADS = {
         desc="2048x256x256 electrode/bulk/electrode slab, BF16 weights, MSD along x, bulk-electrolyte "
              "reservoirs (F = 0, rho = m = 1) on both x faces, FID/population/MSD per region "
              "(electrode-, bulk, electrode+)", sub=64, regions=True),
+    "supercapacitor_regions_1024x256x128": dict(
+        make=lambda: _with_bulk_reservoirs(lpc_inputs.supercapacitor(nx=1024, ny=256, nz=128, electrode=448,
+                                                                     bulk=128)),
+        desc="1024x256x128 electrode/bulk/electrode slab (the region workload at a quarter of its sites, "
+             "for profiling), BF16 weights, MSD along x, bulk reservoirs, three regions", sub=64, regions=True),
     "particle_32": dict(make=lambda: lpc_inputs.particle(msd_axes=0), desc="32^3 particle, FP32",
                         sub=32),
 }
