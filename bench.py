@@ -173,15 +173,15 @@ def kernel_source_hash():
 
 def measured_traffic(kernel, workload, sites):
     """DRAM bytes per launch from the committed ncu summary (profiles/), or
-    None when the kernel source changed since the counters were taken.  A
-    capture of a smaller lattice of the same kernel is scaled by the number
-    of sites (the traffic of these kernels is proportional to the sites)."""
+    None when no capture covers this workload's kernel variant or the kernel
+    source changed since the counters were taken.  A capture of a smaller
+    lattice of the same kernel variant is scaled by the number of sites (the
+    traffic of these kernels is proportional to the sites)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        entries = d[kernel]
-        e = entries.get(workload) or next(iter(entries.values()))
+        e = d[kernel][workload]
     except Exception:
         return None
     if e.get("source_hash") != kernel_source_hash():
