@@ -335,7 +335,7 @@ namespace {
 // MSD axis.  Positions x >= nx of the unpadded pitch get zeros.
 template <typename WT>
 __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __restrict__ gs,
-                              float2* __restrict__ gR, float2* __restrict__ gdm) {
+                              float2* __restrict__ gR, WT* __restrict__ gdm) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= v.Ns) return;
     const int x = (int)(g % v.Xs);
@@ -348,7 +348,10 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
         gs[g] = 0.0f;
         gR[g] = make_float2(0.0f, 0.0f);
         for (int a = 0; a < 3; ++a)
-            if (v.msd_axes >> a & 1) gdm[a * v.Ns + g] = make_float2(0.0f, 0.0f);
+            if (v.msd_axes >> a & 1) {
+                gdm[2 * (a * v.Ns + g)] = round_weight<WT>(0.0);
+                gdm[2 * (a * v.Ns + g) + 1] = round_weight<WT>(0.0);
+            }
         return;
     }
     const long long zplane = (long long)v.Xp * v.Yp;
@@ -364,7 +367,11 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
     gs[g] = stay_weight(wo);
     gR[g] = v.R[p];
     for (int a = 0; a < 3; ++a)
-        if (v.msd_axes >> a & 1) gdm[a * v.Ns + g] = make_float2(wo[2 * a], wo[2 * a + 1]);
+        if (v.msd_axes >> a & 1) {
+            // the stored out-weights themselves (exact in their own type)
+            gdm[2 * (a * v.Ns + g)] = W[(2 * a) * v.Np + p];
+            gdm[2 * (a * v.Ns + g) + 1] = W[(2 * a + 1) * v.Np + p];
+        }
 }
 
 }  // namespace
@@ -402,14 +409,15 @@ cudaError_t launch_restart(const LatticeView& v, cudaStream_t st) {
 // Pitch of the gather-form arrays: rows start on 256-byte boundaries.
 int gather_pitch(int nx) { return (nx + 63) / 64 * 64; }
 
-cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, float2* dm,
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,
                                cudaStream_t st) {
     const int B = 256;
     const long long g = (v.Ns + B - 1) / B;
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_gather_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, static_cast<__nv_bfloat16*>(win), s, R, dm);
+        k_gather_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, static_cast<__nv_bfloat16*>(win), s, R,
+                                                                static_cast<__nv_bfloat16*>(dm));
     else
-        k_gather_pack<float><<<(unsigned)g, B, 0, st>>>(v, static_cast<float*>(win), s, R, dm);
+        k_gather_pack<float><<<(unsigned)g, B, 0, st>>>(v, static_cast<float*>(win), s, R, static_cast<float*>(dm));
     return cudaGetLastError();
 }
 

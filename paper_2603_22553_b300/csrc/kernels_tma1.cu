@@ -66,6 +66,17 @@ template <> __device__ __forceinline__ float2 lds_w2<__nv_bfloat16>(const __nv_b
     return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
 }
 
+// Four consecutive weights in shared memory as floats.
+template <typename WT> __device__ __forceinline__ float4 lds_w4(const WT* p);
+template <> __device__ __forceinline__ float4 lds_w4<float>(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+}
+template <> __device__ __forceinline__ float4 lds_w4<__nv_bfloat16>(const __nv_bfloat16* p) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
 }  // namespace
 
 struct T1Geom {
@@ -80,7 +91,7 @@ struct T1Geom {
 namespace {
 
 // state slot:  rho [TY+2][W] f32 | m [TY+2][W] f32x2 | mu_n [TY+2][W] f32
-// static slot: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2 | dm_n [TY][64] f32x2
+// static slot: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2 | dm_n [TY][64] WTx2
 //              | lab [TY][64] u8 (region labels, with regions only)
 // (each part on a 128-byte boundary, as TMA requires)
 struct T1Slots {
@@ -107,7 +118,7 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
     if (!rho_only) off += up128(C * 8);
     for (int n = 0; n < 3; ++n) {
         L.dm[n] = off;
-        if (n < nmsd) off += up128(C * 8);
+        if (n < nmsd) off += up128(C * 2 * wb);
     }
     L.lab = off;
     if (reg) off += up128(C);
@@ -402,7 +413,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const float2 u_u = *reinterpret_cast<const float2*>(uc + o - W);
                     const float2 u_d = *reinterpret_cast<const float2*>(uc + o + W);
                     const float2 u_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv + SL.mu[n]) + o);
-                    const float4 dm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.dm[n]) + os);
+                    const float4 dm = lds_w4<WT>(reinterpret_cast<const WT*>(ss + SL.dm[n]) + 2 * os);
                     const float nb0[6] = {uc[o - 1], muc[n].y, u_u.x, u_d.x, bmu[n].x, u_a.x};
                     const float nb1[6] = {muc[n].x, uc[o + 2], u_u.y, u_d.y, bmu[n].y, u_a.y};
                     muo0[n] = site_mu(q0.win, q0.r, nb0, sp.x, muc[n].x, a);
@@ -738,9 +749,9 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
         ok = ok && tma_encode(&maps->gR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gR, dr, sr, br);
         if (v.msd_axes) {
             const cuuint64_t dd[4] = {2 * Xs, ny, nz, 3};
-            const cuuint64_t sd[3] = {Xs * 8, Xs * ny * 8, Xs * ny * nz * 8};
+            const cuuint64_t sd[3] = {Xs * 2 * e, Xs * ny * 2 * e, Xs * ny * nz * 2 * e};
             const cuuint32_t bd[4] = {(cuuint32_t)(2 * kTX), TY, 1, 1};
-            ok = ok && tma_encode(&maps->gdm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.gdm, dd, sd, bd);
+            ok = ok && tma_encode(&maps->gdm, dt, 4, v.gdm, dd, sd, bd);
         }
         if (v.region && v.Xr == v.Xs) {
             const cuuint64_t dl[3] = {Xs, ny, nz};
@@ -767,7 +778,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.slot1 = c.L.bytes1;
     g.slot2 = c.L.bytes2;
     g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
-    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 8 * nmsd) + (reg ? 1 : 0));
+    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * nmsd) + (reg ? 1 : 0));
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;

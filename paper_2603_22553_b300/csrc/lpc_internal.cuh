@@ -48,7 +48,7 @@ struct LatticeView {
     const void* gwin;                // [6][Ns] in-weights win_k(x) = w_k(x - e_k), float or bf16
     const float* gs;                 // [Ns] stay weight 1 - sum_k w_k(x)
     const float2* gR;                // [Ns] rotation
-    const float2* gdm;               // [3][Ns] (w_+a(x), w_-a(x)) for the MSD axes
+    const void* gdm;                 // [3][Ns][2] (w_+a(x), w_-a(x)) for the MSD axes, float or bf16
     int Xs;
     long long Ns;
     // reductions: per-block partials, completion counter, history
@@ -435,7 +435,7 @@ cudaError_t t1_prepare(int wdtype, int msd);
 bool t1_supported(const LatticeView& v, int wdtype);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
 int gather_pitch(int nx);
-cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, float2* dm,
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,
                                cudaStream_t st);
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st);

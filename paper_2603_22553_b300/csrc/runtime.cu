@@ -88,7 +88,7 @@ struct lpc_lattice {
     void* gwin = nullptr;
     float* gs = nullptr;
     float2* gR = nullptr;
-    float2* gdm = nullptr;
+    void* gdm = nullptr;
     int Xs = 0;
     long long Ns = 0;
 
@@ -215,7 +215,8 @@ lpc_status ensure_history(lpc_lattice* h, long long needed) {
 
 // win (6 planes), s, R and, with any MSD axis, one (w+a, w-a) plane per axis
 size_t gather_bytes(long long Ns, int wdtype, int msd) {
-    return (size_t)Ns * (6 * (wdtype == LPC_WEIGHTS_BF16 ? 2 : 4) + 4 + 8 + (msd ? 3 * 8 : 0));
+    const size_t wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    return (size_t)Ns * (6 * wb + 4 + 8 + (msd ? 3 * 2 * wb : 0));
 }
 
 // The gather-form static arrays: allocated and filled once (outside any
@@ -234,7 +235,7 @@ lpc_status ensure_gather(lpc_lattice* h) {
     blk += (size_t)Ns * 4;
     h->gR = (float2*)blk;
     blk += (size_t)Ns * 8;
-    h->gdm = h->p.msd_axes ? (float2*)blk : nullptr;     // [3][Ns], indexed by axis
+    h->gdm = h->p.msd_axes ? (void*)blk : nullptr;       // [3][Ns][2] weights, indexed by axis
     LatticeView v = make_view(h, h->cur);
     cudaError_t e = launch_gather_pack(v, h->p.weight_dtype, h->gwin, h->gs, h->gR, h->gdm, h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "gather pack");
