@@ -49,6 +49,11 @@ WORKLOADS = {
         desc="2048x256x256 electrode/bulk/electrode slab, BF16 weights, MSD along x, bulk-electrolyte "
              "reservoirs (F = 0, rho = m = 1) on both x faces, FID/population/MSD per region "
              "(electrode-, bulk, electrode+)", sub=64, regions=True),
+    "film_supercapacitor_regions_2048x256x256": dict(
+        make=lambda: _with_bulk_reservoirs(lpc_inputs.film_supercapacitor()),
+        desc="2048x256x256 film-electrode slab (monodisperse porous particles of radius 9 taking 38% of each "
+             "electrode, bulk electrolyte between them), BF16 weights, MSD along x, bulk reservoirs on both x "
+             "faces, FID/population/MSD per region (electrode-, bulk, electrode+)", sub=64, regions=True),
     "supercapacitor_regions_1024x256x128": dict(
         make=lambda: _with_bulk_reservoirs(lpc_inputs.supercapacitor(nx=1024, ny=256, nz=128, electrode=448,
                                                                      bulk=128)),

@@ -172,6 +172,78 @@ def supercapacitor(nx=2048, ny=256, nz=256, electrode=896, bulk=256, seeds=(31, 
                         regions=regions)
 
 
+def sphere_packing(box, radius, fraction, rng):
+    """Centres of non-touching monodisperse spheres filling about ``fraction``
+    of a box (nz, ny, nx): a cubic arrangement whose spacing per axis is the
+    box edge over round(edge / a), a = radius (4 pi / (3 fraction))^(1/3)
+    (the spacing at which the spheres take ``fraction`` of the volume), each
+    centre moved by a seeded uniform jitter of at most half of the spacing's
+    excess over 2 radius + 1, so that no site of one sphere is a neighbour of a
+    site of another (sites belong to a sphere when their centres lie inside
+    it).  Returns an array of (z, y, x) centres (floats, in sites)."""
+    a = radius * (4.0 * math.pi / (3.0 * fraction)) ** (1.0 / 3.0)
+    # per axis floor or ceil of edge / a (spacing >= 2 radius), the combination
+    # whose sphere fraction is closest to the target
+    opts = []
+    for n in box:
+        c = sorted({max(1, int(math.floor(n / a))), max(1, int(math.ceil(n / a)))})
+        c = [k for k in c if n / k >= 2.0 * radius + 1.0] or [max(1, int(n // (2.0 * radius + 1.0)))]
+        opts.append(c)
+    vol = 4.0 / 3.0 * math.pi * radius ** 3
+    cells = min(((i, j, k) for i in opts[0] for j in opts[1] for k in opts[2]),
+                key=lambda c: abs(c[0] * c[1] * c[2] * vol / (box[0] * box[1] * box[2]) - fraction))
+    spacing = [n / c for n, c in zip(box, cells)]
+    gap = min(spacing) - (2.0 * radius + 1.0)
+    if gap < 0:
+        raise ValueError("spheres of this radius do not fit at this fraction")
+    grids = np.meshgrid(*[(np.arange(c) + 0.5) * sp for c, sp in zip(cells, spacing)], indexing="ij")
+    centres = np.stack([g.reshape(-1) for g in grids], axis=1)
+    centres += rng.uniform(-0.5 * gap, 0.5 * gap, centres.shape) * 0.999
+    return centres
+
+
+def film_supercapacitor(nx=2048, ny=256, nz=256, electrode=896, bulk=256, seeds=(41, 42), radius=9.0,
+                        fraction=0.38, sigma=4.0, steps=5000, weight_dtype=1, msd_axes=1, alpha=ALPHA):
+    """Film electrodes (Sec. 4, Fig. 7 bottom): in each electrode slab along x,
+    monodisperse porous carbon particles of radius 9 sites take 38 % of the
+    volume, separated by bulk-like electrolyte; the separator is bulk.  Inside
+    a particle F = -4 (1 - u) kT and shift = -10 (1 - u) ppm from the slab's
+    own correlated field u (its own seed); elsewhere F = shift = 0.  No solid
+    sites; x walls, y and z periodic (particles wrap across y and z).  The
+    attribute ``particles`` marks the particle sites; ``regions`` are the
+    three slabs, as for the monolith slab."""
+    assert 2 * electrode + bulk == nx
+    F = np.zeros((nz, ny, nx))
+    delta = np.zeros((nz, ny, nx))
+    particles = np.zeros((nz, ny, nx), bool)
+    x_lo = (0, electrode + bulk)
+    r2 = radius * radius
+    ext = int(math.ceil(radius))
+    off = np.arange(-ext, ext + 1)
+    for seed, x0 in zip(seeds, x_lo):
+        rng = _rng(seed)
+        centres = sphere_packing((nz, ny, electrode), radius, fraction, rng)
+        inside = np.zeros((nz, ny, electrode), bool)
+        for cz, cy, cx in centres:
+            iz, iy, ix = int(math.floor(cz)), int(math.floor(cy)), int(math.floor(cx))
+            zz, yy, xx = np.meshgrid(iz + off, iy + off, ix + off, indexing="ij")
+            d2 = (zz + 0.5 - cz) ** 2 + (yy + 0.5 - cy) ** 2 + (xx + 0.5 - cx) ** 2
+            sel = (d2 < r2) & (xx >= 0) & (xx < electrode)
+            inside[zz[sel] % nz, yy[sel] % ny, xx[sel]] = True
+        u, _ = correlated_uniform((nz, ny, electrode), sigma, rng)
+        F[:, :, x0:x0 + electrode] = np.where(inside, -4.0 * (1.0 - u), 0.0)
+        delta[:, :, x0:x0 + electrode] = np.where(inside, -10.0 * (1.0 - u), 0.0)
+        particles[:, :, x0:x0 + electrode] = inside
+        del u
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    regions = {"electrode_minus": (0, electrode), "bulk": (electrode, electrode + bulk),
+               "electrode_plus": (electrode + bulk, nx)}
+    inp = LatticeInput("film_supercapacitor", nx, ny, nz, (0, 1, 1), alpha, DT, KT, F,
+                       ppm_to_omega(delta), solid, None, steps, weight_dtype, msd_axes, regions=regions)
+    inp.particles = particles
+    return inp
+
+
 def monolith(edge=512, seed=5, steps=20000, sigma=4.0, solid_quantile=0.40,
              weight_dtype=0, msd_axes=0, alpha=ALPHA, sub=None):
     """Porous monolith: solid where a correlated field is below its 40 % quantile.
@@ -260,6 +332,7 @@ CONFIGS = {
     "supercapacitor_2048x256x256": lambda: supercapacitor(),
     "monolith_512": lambda: monolith(),
     "monolith_512_sub64": lambda: monolith(sub=64),
+    "film_supercapacitor_2048x256x256": lambda: film_supercapacitor(),
 }
 
 

@@ -15,6 +15,9 @@ module marshals numpy arrays into it and adds the plain downstream formulas:
   with the per-step sums M(n) (Eq. 12), P(n) and the MSD increments (Eq. 5).
 * ``msd``: MSD_a(n) = sum_{j<n} dMSD_a(j) / P(0); ``diffusion``: D = MSD/(2 n dt)
   per axis (Eq. 6-7).
+* ``vacf`` / ``kohn_diffusion``: the displacement autocorrelations and the
+  truncated Kohn sum of Eq. 4 from an equilibrium start; ``region_diffusion``:
+  D of the particles in a region.
 * ``spectrum``: the plain DFT of M (Eq. 9), numpy's e^{-2 pi i k n / N}.
 * ``boltzmann``: the equilibrium densities of Eq. 2 over pore sites.
 * reservoir faces (Sec. 3.2 item 1: fixed field values in the ghost layer of a
@@ -264,6 +267,40 @@ def diffusion(msd_n, dt):
     D = np.full(len(msd_n), np.nan)
     D[1:] = msd_n[1:] / (2.0 * n[1:] * dt)
     return D
+
+
+def vacf(dmsd_axis, P0):
+    """Displacement autocorrelations of Eq. 4 from the MSD increments of a run
+    started in equilibrium (a stationary walk): c_0 = <dx_1^2> = dMSD(0)/P0 and,
+    for m >= 1, c_m = <dx_1 dx_(m+1)> = (dMSD(m) - dMSD(m-1)) / (2 P0), since
+    MSD(n) = n c_0 + 2 sum_{m=1}^{n-1} (n - m) c_m."""
+    d = np.asarray(dmsd_axis, dtype=np.float64) / P0
+    c = np.empty(len(d))
+    c[0] = d[0]
+    c[1:] = 0.5 * (d[1:] - d[:-1])
+    return c
+
+
+def kohn_diffusion(dmsd_axis, P0, dt):
+    """Eq. 4 truncated after n + 1 displacements:
+    D_n = <dx^2> / (2 dt) + (1/dt) sum_{j=2}^{n+1} <dx_1 dx_j>, n = 0 .. len - 1."""
+    c = vacf(dmsd_axis, P0)
+    D = np.empty(len(c))
+    acc = c[0] / (2.0 * dt)
+    D[0] = acc
+    for n in range(1, len(c)):
+        acc += c[n] / dt
+        D[n] = acc
+    return D
+
+
+def region_diffusion(dmsd_region_axis, P_region, dt):
+    """Diffusion coefficient of the particles in a region at step n:
+    D_r(n) = dMSD_r(n) / (2 dt P_r(n)), the MSD increment of the particles that
+    are in region r at step n per particle (one axis)."""
+    d = np.asarray(dmsd_region_axis, dtype=np.float64)
+    P = np.asarray(P_region, dtype=np.float64)[:len(d)]
+    return d / (2.0 * dt * P)
 
 
 def spectrum(M, dt):

@@ -268,3 +268,52 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
                 assert np.array_equal(fused.msd_region(r, a), again.msd_region(r, a))
     for lat in (fused, plain, sep, again):
         lat.close()
+
+
+def test_kohn_vacf_and_region_diffusion_parity():
+    """Eq. 4 (Kohn route) from a Boltzmann start and the diffusion of the
+    particles of each region, from the GPU's histories (downstream) against
+    the oracle's estimators on its own run."""
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300 import downstream
+    shape = (16, 24, 70)
+    inp = lpc_inputs.random_case(shape, 341, periodic=(1, 0, 1), solid_frac=0.2, F_sd=1.0, alpha=0.8,
+                                 msd_axes=7)
+    lab = lpc_inputs.random_regions(shape, 342, 2)
+    lat = _lattice(inp, "auto", region=lab, n_regions=2, init=B.LPC_INIT_BOLTZMANN)
+    steps = 300
+    lat.step(steps)
+    rho_eq = oracle.boltzmann(inp.F, inp.solid)
+    o = oracle.run(oracle.pack_input(inp, oracle.MODE_F32), rho_eq, steps, msd_axes=7, region=lab, n_regions=2)
+    P0 = lat.population()[0]
+    for a in range(3):
+        Dg = downstream.kohn_diffusion(lat.msd(a), inp.dt)
+        Do = oracle.kohn_diffusion(o.dmsd[a], o.P[0], inp.dt)
+        assert np.max(np.abs(Dg - Do) / np.abs(Do)) <= 1e-4
+        cg, co = downstream.vacf(lat.msd(a)), oracle.vacf(o.dmsd[a], o.P[0])
+        assert np.max(np.abs(cg - co)) <= 1e-4 * co[0]
+        for r in range(2):
+            Drg = downstream.region_diffusion(lat.msd_region(r, a), lat.population_region(r), P0, inp.dt)
+            Dro = oracle.region_diffusion(o.Dr[r, a], o.Pr[r], inp.dt)
+            assert np.max(np.abs(Drg - Dro) / np.abs(Dro)) <= 1e-4
+    lat.close()
+
+
+def test_film_electrode_slab_parity():
+    """A film-electrode slab (separated monodisperse particles in each
+    electrode) with bulk reservoirs and three regions, BF16 weights and MSD
+    along x: FID, populations and region FIDs against the matched oracle."""
+    inp = lpc_inputs.film_supercapacitor(nx=152, ny=40, nz=40, electrode=60, bulk=32, steps=200)
+    inp.alpha = 0.4
+    inp.reservoirs = ((0.0, 1.0, 1.0), (0.0, 1.0, 1.0), None, None, None, None)
+    lab, names = lpc_inputs.region_labels(inp)
+    for sched in ("auto", "tb1"):
+        lat = _lattice(inp, sched, region=lab, n_regions=3)
+        lat.step(inp.steps)
+        o = oracle.run(oracle.pack_input(inp, oracle.MODE_BF16), inp.uniform_rho0(), inp.steps, msd_axes=1,
+                       region=lab, n_regions=3)
+        assert H.rel_l2(lat.fid(), o.M) <= 1e-5
+        assert H.rel_l2(lat.density().astype(np.float64), o.rho) <= 1e-5
+        for r in range(3):
+            assert H.rel_l2(lat.fid_region(r), o.Mr[r]) <= 1e-5
+        lat.close()

@@ -551,3 +551,53 @@ def test_single_region_equals_the_totals_bitwise():
     r = oracle.run(pk, inp.uniform_rho0(), 30, msd_axes=1, region=lab, n_regions=1)
     assert np.array_equal(r.Mr[0], r.M) and np.array_equal(r.Pr[0], r.P)
     assert np.array_equal(r.Dr[0, 0], r.dmsd[0])
+
+
+# --------------------------------------------------------------------------
+# Kohn / VACF diffusion estimator (Eq. 4) and the diffusion of a region
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_vacf_against_dense_autocorrelations(axis):
+    """c_m of the oracle's run equal the autocorrelations computed with dense
+    matrices (c_0 from the squared displacements, c_m = u T^(m-1) D rho / P)."""
+    inp = lpc_inputs.random_case((4, 5, 3), 101, periodic=(1, 0, 1), solid_frac=0.15, F_sd=1.0, alpha=0.6)
+    pk = oracle.pack_input(inp)
+    rho_eq = oracle.boltzmann(inp.F, inp.solid).reshape(-1)
+    n = 30
+    r = oracle.run(pk, rho_eq.reshape(inp.F.shape), n, msd_axes=1 << axis)
+    T = bf.transition_matrix(inp.F, inp.solid, inp.periodic, inp.alpha)
+    D = bf.displacement_operator(inp.F, inp.solid, inp.periodic, inp.alpha, axis)
+    P0 = rho_eq.sum()
+    c = [np.abs(D).sum(axis=0) @ rho_eq / P0]
+    h = D @ rho_eq
+    u = D.sum(axis=0)
+    for m in range(1, n):
+        c.append(u @ h / P0)
+        h = T @ h
+    got = oracle.vacf(r.dmsd[axis], r.P[0])
+    assert np.allclose(got, c, rtol=1e-9, atol=1e-13 * c[0])
+    # the truncated Kohn sum is the running sum of the autocorrelations
+    Dk = oracle.kohn_diffusion(r.dmsd[axis], r.P[0], inp.dt)
+    for k in (0, 1, 7, n - 1):
+        assert Dk[k] == pytest.approx((c[0] / 2 + sum(c[1:k + 1])) / inp.dt, rel=1e-9)
+
+
+def test_kohn_and_region_diffusion_on_a_uniform_lattice():
+    """Uniform lattice in equilibrium: uncorrelated jumps, c_0 = alpha/3 and
+    c_m = 0, so D = alpha a^2 / (2 d dt) with d = 3 (Eq. 7) at every n, and the
+    same D for the particles of any region."""
+    shape = (5, 6, 7)
+    nz, ny, nx = shape
+    alpha, dt = 0.45, lpc_inputs.DT
+    pk = oracle.pack(nx, ny, nz, (1, 1, 1), alpha, dt, 1.0, np.zeros(shape), np.zeros(shape),
+                     np.zeros(shape, np.uint8))
+    lab = lpc_inputs.random_regions(shape, 102, 3)
+    r = oracle.run(pk, np.full(shape, 2.0), 25, msd_axes=7, region=lab, n_regions=3)
+    for a in range(3):
+        assert np.allclose(oracle.kohn_diffusion(r.dmsd[a], r.P[0], dt), alpha / (6 * dt), rtol=1e-12)
+        c = oracle.vacf(r.dmsd[a], r.P[0])
+        assert c[0] == pytest.approx(alpha / 3, rel=1e-12) and np.max(np.abs(c[1:])) <= 1e-14
+        for g in range(3):
+            Dr = oracle.region_diffusion(r.Dr[g, a], r.Pr[g], dt)
+            assert np.allclose(Dr, alpha / (6 * dt), rtol=1e-12)
