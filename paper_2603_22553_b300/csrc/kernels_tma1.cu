@@ -309,7 +309,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             const bool ok_y = y < v.ny;
             const bool site0 = ok_y && x < v.nx;
             const bool site1 = ok_y && x + 1 < v.nx;
-            const bool inner = x >= G && x + 1 < v.nx - G && y >= G && y < v.ny - G;
+            // the pair has ghost images to write: it lies within G of a periodic face
+            const bool images = (v.per_x && (x < G || x + 1 >= v.nx - G)) || (v.per_y && (y < G || y >= v.ny - G));
             const long long col = (long long)(y + G) * v.Xp + (x + G);
             // plane za-1: keep this lane's two columns as "below"
             float2 br, bmu[3];
@@ -432,26 +433,36 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     mbar_arrive(&empty1[center]);
                     mbar_arrive(&empty2[sslot]);
                 }
-                if (inner) {
+                // every site: its interior position (vector stores for a full
+                // pair); pairs near a periodic face also write their ghost images
+                {
                     const long long p = col + (long long)z * zplane;
-                    *reinterpret_cast<float2*>(v.rho_out + p) = make_float2(ro0, ro1);
-                    if (!RHO) *reinterpret_cast<float4*>(v.m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
+                    if (site0 && site1) {
+                        *reinterpret_cast<float2*>(v.rho_out + p) = make_float2(ro0, ro1);
+                        if (!RHO) *reinterpret_cast<float4*>(v.m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
 #pragma unroll
-                    for (int n = 0; n < NMSD; ++n)
-                        *reinterpret_cast<float2*>(v.mu_out[axis_of[n]] + p) = make_float2(muo0[n], muo1[n]);
-                } else {
+                        for (int n = 0; n < NMSD; ++n)
+                            *reinterpret_cast<float2*>(v.mu_out[axis_of[n]] + p) = make_float2(muo0[n], muo1[n]);
+                    } else if (site0) {
+                        v.rho_out[p] = ro0;
+                        if (!RHO) v.m_out[p] = mo0;
+#pragma unroll
+                        for (int n = 0; n < NMSD; ++n) v.mu_out[axis_of[n]][p] = muo0[n];
+                    }
+                }
+                if (images) {
                     const long long zoff = (long long)z * zplane;
                     if (site0) {
-                        store_images(v.rho_out, v, x, y, zoff, ro0);
-                        if (!RHO) store_images(v.m_out, v, x, y, zoff, mo0);
+                        store_ghost_images(v.rho_out, v, x, y, zoff, ro0);
+                        if (!RHO) store_ghost_images(v.m_out, v, x, y, zoff, mo0);
 #pragma unroll
-                        for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo0[n]);
+                        for (int n = 0; n < NMSD; ++n) store_ghost_images(v.mu_out[axis_of[n]], v, x, y, zoff, muo0[n]);
                     }
                     if (site1) {
-                        store_images(v.rho_out, v, x + 1, y, zoff, ro1);
-                        if (!RHO) store_images(v.m_out, v, x + 1, y, zoff, mo1);
+                        store_ghost_images(v.rho_out, v, x + 1, y, zoff, ro1);
+                        if (!RHO) store_ghost_images(v.m_out, v, x + 1, y, zoff, mo1);
 #pragma unroll
-                        for (int n = 0; n < NMSD; ++n) store_images(v.mu_out[axis_of[n]], v, x + 1, y, zoff, muo1[n]);
+                        for (int n = 0; n < NMSD; ++n) store_ghost_images(v.mu_out[axis_of[n]], v, x + 1, y, zoff, muo1[n]);
                     }
                 }
                 if (site0 && to_part) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro0; }

@@ -183,6 +183,22 @@ __device__ __forceinline__ void store_images(T* base, const LatticeView& v, int 
             base[zoff + (long long)py * v.Xp + px] = val;
 }
 
+// The ghost images of a site on periodic axes, without the site's own
+// interior position (which the caller stores itself, e.g. with a vector
+// store): together with it, the positions store_images writes.
+template <typename T>
+__device__ __forceinline__ void store_ghost_images(T* base, const LatticeView& v, int x, int y, long long zoff,
+                                                   T val) {
+    const int G = v.G;
+    const int px0 = v.per_x ? (x + G) % v.nx : x + G;
+    const int pxe = v.per_x ? v.nx + 2 * G : x + G + 1;
+    const int py0 = v.per_y ? (y + G) % v.ny : y + G;
+    const int pye = v.per_y ? v.ny + 2 * G : y + G + 1;
+    for (int py = py0; py < pye; py += v.ny)
+        for (int px = px0; px < pxe; px += v.nx)
+            if (px != x + G || py != y + G) base[zoff + (long long)py * v.Xp + px] = val;
+}
+
 // Final reduction of per-warp FP64 sums held in shared memory as
 // smem[(level * NW + warp) * kNumSums + q]: each block combines its warps in
 // a fixed order into per-block partials, and the last block to finish sums
