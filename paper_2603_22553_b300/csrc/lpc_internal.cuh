@@ -185,11 +185,22 @@ __device__ __forceinline__ void store_images(T* base, const LatticeView& v, int 
 
 // The ghost images of a site on periodic axes, without the site's own
 // interior position (which the caller stores itself, e.g. with a vector
-// store): together with it, the positions store_images writes.
+// store): together with it, the positions store_images writes.  With
+// nx, ny >= 2G a site has at most one image offset per axis (+n within G of
+// the lower face, -n within G of the upper), so at most three images.
 template <typename T>
 __device__ __forceinline__ void store_ghost_images(T* base, const LatticeView& v, int x, int y, long long zoff,
                                                    T val) {
     const int G = v.G;
+    if (v.nx >= 2 * G && v.ny >= 2 * G) {
+        const int dx = !v.per_x ? 0 : x < G ? v.nx : (x >= v.nx - G ? -v.nx : 0);
+        const int dy = !v.per_y ? 0 : y < G ? v.ny : (y >= v.ny - G ? -v.ny : 0);
+        const long long p = zoff + (long long)(y + G) * v.Xp + (x + G);
+        if (dx) base[p + dx] = val;
+        if (dy) base[p + (long long)dy * v.Xp] = val;
+        if (dx && dy) base[p + (long long)dy * v.Xp + dx] = val;
+        return;
+    }
     const int px0 = v.per_x ? (x + G) % v.nx : x + G;
     const int pxe = v.per_x ? v.nx + 2 * G : x + G + 1;
     const int py0 = v.per_y ? (y + G) % v.ny : y + G;
