@@ -165,24 +165,6 @@ __device__ __forceinline__ float site_dmsd(const float* wout, float mu_c, float 
     return __fmaf_rn(__fmul_rn(2.0f, u), mu_c, __fmul_rn(q, rc));
 }
 
-// Write a site value to its interior position and every ghost image.
-template <typename T>
-__device__ __forceinline__ void store_images(T* base, const LatticeView& v, int x, int y,
-                                             long long zoff, T val) {
-    const int G = v.G;
-    if (x >= G && x < v.nx - G && y >= G && y < v.ny - G) {
-        base[zoff + (long long)(y + G) * v.Xp + (x + G)] = val;
-        return;
-    }
-    const int px0 = v.per_x ? (x + G) % v.nx : x + G;
-    const int pxe = v.per_x ? v.nx + 2 * G : x + G + 1;
-    const int py0 = v.per_y ? (y + G) % v.ny : y + G;
-    const int pye = v.per_y ? v.ny + 2 * G : y + G + 1;
-    for (int py = py0; py < pye; py += v.ny)
-        for (int px = px0; px < pxe; px += v.nx)
-            base[zoff + (long long)py * v.Xp + px] = val;
-}
-
 // The ghost images of a site on periodic axes, without the site's own
 // interior position (which the caller stores itself, e.g. with a vector
 // store): together with it, the positions store_images writes.  With
@@ -208,6 +190,16 @@ __device__ __forceinline__ void store_ghost_images(T* base, const LatticeView& v
     for (int py = py0; py < pye; py += v.ny)
         for (int px = px0; px < pxe; px += v.nx)
             if (px != x + G || py != y + G) base[zoff + (long long)py * v.Xp + px] = val;
+}
+
+// Write a site value to its interior position and every ghost image.
+template <typename T>
+__device__ __forceinline__ void store_images(T* base, const LatticeView& v, int x, int y,
+                                             long long zoff, T val) {
+    const int G = v.G;
+    base[zoff + (long long)(y + G) * v.Xp + (x + G)] = val;
+    if (x >= G && x < v.nx - G && y >= G && y < v.ny - G) return;
+    store_ghost_images(base, v, x, y, zoff, val);
 }
 
 // Final reduction of per-warp FP64 sums held in shared memory as
