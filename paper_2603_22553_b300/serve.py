@@ -8,9 +8,11 @@ Continuous batching on one GPU:
   thread builds its fields and creates the lattice (its state then stays
   resident on the device until it finishes);
 * every round advances all resident lattices together by up to ``quantum``
-  steps with ``lattice_step_many`` (batched launches: one launch per step
-  covers the work items of every resident lattice), so work of requests that
-  arrived at different times overlaps on the device;
+  steps: the small ones with ``lattice_step_many`` (one persistent launch
+  covers the work items of every small resident lattice), the large ones
+  with ``lattice_step_n`` on their own streams (the one-step TMA kernel in
+  captured graphs), so work of requests that arrived at different times
+  overlaps on the device;
 * a lattice that has done its steps has its FID read back and is destroyed,
   which frees its slot and memory for the next admission.
 
@@ -79,7 +81,28 @@ class GpuEngine:
         return lat
 
     def step_many(self, lats, steps):
-        self.L.step_many(lats, steps)
+        """Lattices that the one-step TMA kernel serves (large enough to fill
+        its tiles) advance with lattice_step_n on their own streams (captured
+        graphs); the others share batched launches.  Both kinds are queued
+        before any waits, so their work overlaps on the device."""
+        own, batch = [], []
+        for lat, n in zip(lats, steps):
+            if self._tma(lat):
+                own.append((lat, n))
+            else:
+                batch.append((lat, n))
+        for lat, n in own:
+            lat.step(n)
+        if batch:
+            self.L.step_many([b[0] for b in batch], [b[1] for b in batch])
+
+    def _tma(self, lat):
+        k = getattr(lat, "_serve_tma", None)
+        if k is None:
+            info = lat.info()
+            k = info["kernel"] == B.LPC_KERNEL_TB and info["block_steps"] == 1
+            lat._serve_tma = k
+        return k
 
     def finish(self, lat):
         fid = lat.fid() if self.keep_fid else None
