@@ -317,3 +317,26 @@ def test_film_electrode_slab_parity():
         for r in range(3):
             assert H.rel_l2(lat.fid_region(r), o.Mr[r]) <= 1e-5
         lat.close()
+
+
+@pytest.mark.parametrize("sched", ["auto", "step1"])
+def test_region_edge_cases(sched):
+    """One region covering every site gives the totals (bit for bit in the
+    fused kernel, where the totals are the sum over regions); a label that no
+    site carries gives an all-zero history."""
+    from paper_2603_22553_b300 import binding as B
+    shape = (24, 48, 160)
+    inp = lpc_inputs.random_case(shape, 351, periodic=(1, 1, 1), alpha=0.6, msd_axes=1)
+    lab = np.zeros(shape, np.uint8)
+    lat = _lattice(inp, sched, region=lab, n_regions=2)
+    fused = lat.info()["kernel"] == B.LPC_KERNEL_TB
+    lat.step(40)
+    M, P = lat.fid(), lat.population()
+    if fused:
+        assert np.array_equal(lat.fid_region(0)[1:], M[1:])
+        assert np.array_equal(lat.population_region(0)[1:], P[1:])
+    else:
+        assert np.max(np.abs(lat.fid_region(0) - M)) <= 1e-6 * P[0]
+    assert np.all(lat.fid_region(1) == 0) and np.all(lat.population_region(1) == 0)
+    assert np.all(lat.msd_region(1, 0) == 0)
+    lat.close()
