@@ -112,3 +112,60 @@ def test_precision_sweep_64_subvolume(monolith512):
             assert e_exact <= 1e-4
         g["lattice"].close()
     print("precision sweep (FID matched, FID exact, spectrum):", report)
+
+
+def _box_axes(a, center, r, periodic):
+    """The box of half-width r around `center` (z, y, x): wrapped on periodic
+    axes, cut at the lattice faces on walled ones.  Returns the box and the
+    centre's index in it."""
+    out = a
+    idx_c = []
+    for ax, (c, per) in enumerate(zip(center, periodic)):
+        n = a.shape[ax]
+        if per:
+            idx = np.arange(c - r, c + r + 1) % n
+            idx_c.append(r)
+        else:
+            lo, hi = max(0, c - r), min(n, c + r + 1)
+            idx = np.arange(lo, hi)
+            idx_c.append(c - lo)
+        out = out.take(idx, axis=ax)
+    return out, tuple(idx_c)
+
+
+def test_supercapacitor_full_size_sampled_sites():
+    """The 2048x256x256 slab (BF16 weights, first moment along x, walls in x)
+    in the schedule bench.py times: sampled sites (at the walls, at the
+    electrode/bulk interfaces and at random) against the FP64 oracle on a
+    box of half-width n + 2 with walls on its faces (the walls at the box
+    faces are farther than n sites from the centre; where the box is cut by
+    the real walls, they are the same walls)."""
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.supercapacitor()
+    n = 6
+    lat = Lattice.from_input(inp)
+    lat.step(n)
+    rho, m, mu = lat.density(), lat.magnetization(), lat.moment(0)
+    P = lat.population()
+    assert np.max(np.abs(P / P[0] - 1.0)) <= 1e-5
+    rng = np.random.default_rng(12)
+    pts = [(0, 0, 0), (255, 255, 2047), (7, 100, 895), (9, 3, 896), (200, 50, 1151), (1, 254, 1152),
+           (128, 128, 1), (60, 0, 2046)]
+    pts += [(int(rng.integers(0, 256)), int(rng.integers(0, 256)), int(rng.integers(0, 2048))) for _ in range(24)]
+    r = n + 2
+    per = (1, 1, 0)            # z, y periodic; x walls (array axes z, y, x)
+    worst = 0.0
+    for c in pts:
+        Fb, cc = _box_axes(inp.F, c, r, per)
+        Ob, _ = _box_axes(inp.omega, c, r, per)
+        Sb, _ = _box_axes(inp.solid, c, r, per)
+        nzb, nyb, nxb = Fb.shape
+        pk = oracle.pack(nxb, nyb, nzb, (0, 0, 0), inp.alpha, inp.dt, inp.kT, Fb, Ob, Sb, oracle.MODE_BF16)
+        res = oracle.run(pk, (Sb == 0).astype(np.float64), n, msd_axes=1)
+        z, y, x = c
+        scale = max(1.0, abs(res.rho[cc]))
+        err = max(abs(rho[z, y, x] - res.rho[cc]), abs(m[z, y, x] - res.m[cc]),
+                  abs(mu[z, y, x] - res.mu[0][cc])) / scale
+        worst = max(worst, err)
+    assert worst <= 1e-5, worst
+    lat.close()
