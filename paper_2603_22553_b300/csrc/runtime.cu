@@ -2,11 +2,14 @@
 // device memory through the caller's allocator, the step schedule (direct
 // launches or replay of captured CUDA graphs), history buffers and queries.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "lpc_internal.cuh"
 
@@ -343,10 +346,32 @@ void auto_schedule(lpc_lattice* h) {
     drop_graphs(h);
 }
 
+// pred(i) for every i < n, on up to 16 host threads for large inputs (the
+// argument checks of create read every input value once).
+template <typename Pred>
+bool all_of_parallel(long long n, Pred pred) {
+    unsigned T = std::thread::hardware_concurrency();
+    T = T < 1 ? 1 : (T > 16 ? 16 : T);
+    if (n < (1LL << 20)) T = 1;
+    std::atomic<bool> ok{true};
+    auto part = [&](unsigned t) {
+        const long long lo = n * t / T, hi = n * (t + 1) / T;
+        for (long long i = lo; i < hi; ++i)
+            if (!pred(i)) { ok.store(false, std::memory_order_relaxed); return; }
+    };
+    if (T == 1) {
+        part(0);
+        return ok.load();
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (unsigned t = 0; t < T; ++t) th.emplace_back(part, t);
+    for (auto& x : th) x.join();
+    return ok.load();
+}
+
 bool finite_all(const double* a, const uint8_t* solid, long long n, bool pore_only) {
-    for (long long i = 0; i < n; ++i)
-        if ((!pore_only || !solid[i]) && !std::isfinite(a[i])) return false;
-    return true;
+    return all_of_parallel(n, [=](long long i) { return (pore_only && solid[i]) || std::isfinite(a[i]); });
 }
 
 void release_all(lpc_lattice* h) {
@@ -422,9 +447,10 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     if (!finite_all(F, solid, N, true)) { set_error("lattice_create: non-finite F on a pore site"); return LPC_ERR_INVALID; }
     if (!finite_all(omega, solid, N, false)) { set_error("lattice_create: non-finite omega"); return LPC_ERR_INVALID; }
     if (rho0 && !finite_all(rho0, solid, N, true)) { set_error("lattice_create: non-finite rho0 on a pore site"); return LPC_ERR_INVALID; }
-    if (alpha_links)
-        for (long long i = 0; i < 3 * N; ++i)
-            if (!(alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0)) { set_error("lattice_create_links: link factors must be in [0, 1]"); return LPC_ERR_INVALID; }
+    if (alpha_links && !all_of_parallel(3 * N, [=](long long i) { return alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0; })) {
+        set_error("lattice_create_links: link factors must be in [0, 1]");
+        return LPC_ERR_INVALID;
+    }
     if (o.reserved != 0) { set_error("lattice_create_ex: reserved option fields must be 0"); return LPC_ERR_INVALID; }
     ResFaces rf{};
     for (int f = 0; f < 6; ++f) {
@@ -446,9 +472,14 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
         set_error("lattice_create_ex: n_regions must be 1..4 with region labels and 0 without");
         return LPC_ERR_INVALID;
     }
-    if (o.region)
-        for (long long i = 0; i < N; ++i)
-            if (o.region[i] >= o.n_regions) { set_error("lattice_create_ex: a region label is >= n_regions"); return LPC_ERR_INVALID; }
+    if (o.region) {
+        const uint8_t* reg = o.region;
+        const int nr = o.n_regions;
+        if (!all_of_parallel(N, [=](long long i) { return reg[i] < nr; })) {
+            set_error("lattice_create_ex: a region label is >= n_regions");
+            return LPC_ERR_INVALID;
+        }
+    }
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }

@@ -250,10 +250,22 @@ class Lattice:
         return out
 
     # -- fields ----------------------------------------------------------------
-    def density(self):
-        out = np.empty(self.N, np.float32)
-        B.check(self.lib.lattice_density(self.h, out.ctypes.data_as(ctypes.c_void_p), 0), self.lib)
-        return out.reshape(self.shape)
+    def _host_out(self, out, count):
+        """A caller-provided float32 host buffer of ``count`` values (e.g. a
+        reused or pinned one: a fresh buffer's page faults cost more than the
+        copy), or a new one."""
+        if out is None:
+            return np.empty(count, np.float32)
+        out = np.asarray(out)
+        if out.dtype != np.float32 or out.size != count or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float32 array of %d values" % count)
+        return out.reshape(-1)
+
+    def density(self, out=None):
+        """Populations rho(x, n) as float32 (nz, ny, nx); ``out``: optional host buffer."""
+        buf = self._host_out(out, self.N)
+        B.check(self.lib.lattice_density(self.h, buf.ctypes.data_as(ctypes.c_void_p), 0), self.lib)
+        return buf.reshape(self.shape)
 
     def density_device(self):
         """Densities as a torch CUDA tensor (copied on the lattice's stream)."""
