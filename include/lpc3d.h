@@ -253,8 +253,9 @@ lpc_status lattice_step_n(lpc_lattice* h, int64_t n);
 lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count);
 
 /* Choose the step kernel: LPC_KERNEL_AUTO (the default: the TMA-fed
- * one-step kernel for lattices of at least 2^18 sites with nx >= 32 and
- * ny >= 16, else the register-pipelined one), STEP1, or TB with block depth
+ * one-step kernel for lattices of at least 2^20 sites with nx >= 64 and
+ * ny >= 16, else the register-pipelined one, which is faster on smaller
+ * lattices), STEP1, or TB with block depth
  * k (1..min(4, ghost); k = 1 is the TMA-fed one-step kernel).
  * LPC_ERR_INVALID if the combination is impossible. */
 lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps);

@@ -794,7 +794,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
     long long cz = (long long)g.tiles * v.nz / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
-    if (cz < 16) cz = 16;
+    if (cz < 8) cz = 8;
     if (cz > v.nz) cz = v.nz;
     while ((long long)g.tiles * ((v.nz + cz - 1) / cz) > t1_max_items() && cz < v.nz) cz *= 2;
     if (cz > v.nz) cz = v.nz;

@@ -334,7 +334,7 @@ lpc_status build_graph(lpc_lattice* h, int parity) {
 // Default schedule: the TMA-fed one-step kernel for lattices large enough to
 // fill its tiles, else the register-pipelined one-step kernel.
 void auto_schedule(lpc_lattice* h) {
-    const bool big = h->p.nx >= 64 && h->p.ny >= 16 && h->N >= (1LL << 18);
+    const bool big = h->p.nx >= 64 && h->p.ny >= 16 && h->N >= (1LL << 20);
     if (big && tb_supported(make_view(h, 0), h->p.weight_dtype, 1) &&
         tb_prepare(h->p.weight_dtype, 1, h->p.msd_axes) == cudaSuccess) {
         h->kernel = LPC_KERNEL_TB;
@@ -611,7 +611,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     b += (long long)device_props().sm_count * 32 * kMaxTB * kNumSums * 8 + 256 + 8 * 1024;
     b += (long long)history_bytes(cap, 1);
     b += 16 * N;    // transient copies of F and omega during create
-    if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 18))     // the automatic schedule's gather form
+    if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 20))     // the automatic schedule's gather form
         b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, p->msd_axes);
     *bytes = b;
     return LPC_OK;

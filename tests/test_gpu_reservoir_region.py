@@ -231,9 +231,9 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
                                  weight_dtype=wdt)
     lab = lpc_inputs.random_regions(shape, 332, 4)
     steps = 64
-    fused = _lattice(inp, "auto", region=lab, n_regions=4)
+    fused = _lattice(inp, "tb1", region=lab, n_regions=4)
     assert fused.info()["kernel"] == B.LPC_KERNEL_TB and fused.info()["block_steps"] == 1
-    plain = _lattice(inp, "auto")
+    plain = _lattice(inp, "tb1")
     sep = _lattice(inp, "step1", region=lab, n_regions=4)
     for lat in (fused, plain, sep):
         lat.step(steps)
@@ -257,7 +257,7 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
         assert H.rel_l2(fused.fid_region(r), o.Mr[r]) <= 1e-5
     blob = fused.get_state()
     fused.step(10)
-    again = _lattice(inp, "auto", region=lab, n_regions=4)
+    again = _lattice(inp, "tb1", region=lab, n_regions=4)
     again.set_state(blob)
     again.step(10)
     for r in range(4):
@@ -319,7 +319,7 @@ def test_film_electrode_slab_parity():
         lat.close()
 
 
-@pytest.mark.parametrize("sched", ["auto", "step1"])
+@pytest.mark.parametrize("sched", ["tb1", "step1"])
 def test_region_edge_cases(sched):
     """One region covering every site gives the totals (bit for bit in the
     fused kernel, where the totals are the sum over regions); a label that no
