@@ -106,6 +106,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest value of ``x`` over the ranks (the slowest rank's time):
+    an all-reduce with MAX when more than one rank runs."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(ws, sites, lattice_steps, seconds):
+    """Site updates of all ranks (one replica each) per second of the slowest."""
+    return ws * sites * lattice_steps / seconds
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -322,12 +339,9 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
     lattice_steps = args.steps * args.block
-    value = ws * N * lattice_steps / (ms / 1e3)
+    value = aggregate_rate(ws, N, lattice_steps, ms / 1e3)
     if info["kernel"] == B.LPC_KERNEL_TB:
         kernel_name = "k_step_tma1" if info["block_steps"] == 1 else "k_step_tb"
     else:
@@ -389,14 +403,10 @@ def run_ours(args):
         rho = lat.density(out=Rp.numpy())
         t1 = time.perf_counter()
         lat.close()
-        te = t1 - t0
-        if ws > 1:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(t1 - t0, ws, "cuda")
         h2d = Fp.numel() * 8 + Op.numel() * 8 + Sp.numel() + (inp.n_sites if rkw else 0)
         d2h = M.size * 16 + rho.size * 4
-        e2e = {"value": ws * N * lattice_steps / te, "unit": "site-updates/s",
+        e2e = {"value": aggregate_rate(ws, N, lattice_steps, te), "unit": "site-updates/s",
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "seconds": te}
 
