@@ -169,3 +169,35 @@ def test_supercapacitor_full_size_sampled_sites():
         worst = max(worst, err)
     assert worst <= 1e-5, worst
     lat.close()
+
+
+def test_particle_in_bath_256_sampled_sites():
+    """The 256^3 bath (porous sphere of radius 80 in electrolyte) in the
+    benchmarked schedule: sampled sites inside the sphere, at its surface, in
+    the bath and at the periodic faces against the FP64 oracle on boxes."""
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.particle_in_bath()
+    n = 6
+    lat = Lattice.from_input(inp)
+    lat.step(n)
+    rho, m = lat.density(), lat.magnetization()
+    P = lat.population()
+    assert np.max(np.abs(P / P[0] - 1.0)) <= 1e-5
+    rng = np.random.default_rng(13)
+    pts = [(0, 0, 0), (255, 255, 255), (128, 128, 128), (128, 128, 48), (128, 48, 128), (40, 128, 128),
+           (0, 128, 255), (200, 3, 77)]
+    pts += [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(24)]
+    r = n + 2
+    worst = 0.0
+    for c in pts:
+        Fb, cc = _box_axes(inp.F, c, r, (1, 1, 1))
+        Ob, _ = _box_axes(inp.omega, c, r, (1, 1, 1))
+        Sb, _ = _box_axes(inp.solid, c, r, (1, 1, 1))
+        e = 2 * r + 1
+        pk = oracle.pack(e, e, e, (0, 0, 0), inp.alpha, inp.dt, inp.kT, Fb, Ob, Sb, oracle.MODE_F32)
+        res = oracle.run(pk, (Sb == 0).astype(np.float64), n, msd_axes=0)
+        z, y, x = c
+        err = max(abs(rho[z, y, x] - res.rho[cc]), abs(m[z, y, x] - res.m[cc])) / max(1.0, abs(res.rho[cc]))
+        worst = max(worst, err)
+    assert worst <= 1e-5, worst
+    lat.close()
