@@ -340,3 +340,26 @@ def test_region_edge_cases(sched):
     assert np.all(lat.fid_region(1) == 0) and np.all(lat.population_region(1) == 0)
     assert np.all(lat.msd_region(1, 0) == 0)
     lat.close()
+
+
+@pytest.mark.parametrize("sched", ["tb1", "step1"])
+def test_equilibration_then_region_sums(sched):
+    """The equilibration phase on a lattice with reservoirs and regions, then
+    the propagation phase: region FIDs and populations from the restart
+    against the oracle run from the equilibrated populations."""
+    shape = (16, 32, 96)
+    inp = lpc_inputs.random_case(shape, 361, periodic=(0, 1, 1), solid_frac=0.1, F_sd=0.8, alpha=0.9, msd_axes=1)
+    inp.reservoirs = ((0.0, 1.0, 1.0), (-0.5, 0.75, 0.5j), None, None, None, None)
+    lab = lpc_inputs.random_regions(shape, 362, 3)
+    lat = _lattice(inp, sched, region=lab, n_regions=3)
+    it, _ = lat.equilibrate(0.0, 2000, check_every=500)
+    assert it == 2000 and lat.steps_done == 0
+    rho = lat.density().astype(np.float64)
+    steps = 60
+    lat.step(steps)
+    o = oracle.run(oracle.pack_input(inp, oracle.MODE_F32), rho, steps, msd_axes=1, region=lab, n_regions=3)
+    assert H.rel_l2(lat.fid(), o.M) <= 1e-5
+    for r in range(3):
+        assert H.rel_l2(lat.fid_region(r), o.Mr[r]) <= 1e-5
+        assert H.rel_l2(lat.population_region(r), o.Pr[r]) <= 1e-5
+    lat.close()
