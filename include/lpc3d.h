@@ -220,7 +220,10 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* o, const do
  * Device bytes lattice_create would hold for these parameters, plus the
  * history of `steps` steps and the transient input copies of create (used to
  * admit requests by HBM footprint).  No device work.  LPC_ERR_INVALID on bad
- * parameters.
+ * parameters.  Options of lattice_create_ex add to it: per-link factors
+ * 24 bytes per site during create; region labels 1 byte per site, one more
+ * history set (48 bytes per step) per region and 4x the per-item partial
+ * sums (about 7 MB).
  */
 lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes);
 
