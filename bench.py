@@ -141,9 +141,12 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
+        import tempfile
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % gpu_index)
+        # the raw samples go to a scratch file (LPC_BENCH_CLOCKS_DIR to keep them)
+        out_dir = os.environ.get("LPC_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "bench_clocks_%d_%d.csv" % (gpu_index, os.getpid()))
 
     def start(self):
         try:

@@ -34,7 +34,7 @@ def lib():
     return B.load()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = declared_functions()
     for n in ("lattice_create", "lattice_step_n", "lattice_fid", "lattice_density",
               "lattice_msd", "lattice_destroy", "lpc_last_error"):
