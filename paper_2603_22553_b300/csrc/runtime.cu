@@ -441,6 +441,16 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     if (p->msd_axes < 0 || p->msd_axes > 7) { set_error("lattice_create: msd_axes must be a mask of 1, 2, 4"); return LPC_ERR_INVALID; }
     if (p->init != LPC_INIT_UNIFORM && p->init != LPC_INIT_BOLTZMANN) { set_error("lattice_create: init must be 0 or 1"); return LPC_ERR_INVALID; }
     if (p->ghost < 0 || p->ghost > kMaxGhost || (p->ghost & 1)) { set_error("lattice_create: ghost must be 0 (automatic) or even in 2..8"); return LPC_ERR_INVALID; }
+    {
+        // the kernels address the padded arrays with 32-bit offsets; checked
+        // before any input array is read
+        const long long Gp = p->ghost == 0 ? 2 : p->ghost;
+        const long long Np = ((p->nx + 2 * Gp) + 31) / 32 * 32 * (p->ny + 2 * Gp) * (long long)p->nz;
+        if (Np > 2147483647LL) {
+            set_error("lattice_create: more than 2^31-1 sites including the ghost layers");
+            return LPC_ERR_INVALID;
+        }
+    }
     for (int i = 0; i < 3; ++i)
         if (p->periodic[i] != 0 && p->periodic[i] != 1) { set_error("lattice_create: periodic flags must be 0 or 1"); return LPC_ERR_INVALID; }
     if (a && (!a->alloc || !a->free)) { set_error("lattice_create: allocator needs alloc and free"); return LPC_ERR_INVALID; }

@@ -170,3 +170,20 @@ def test_region_queries_reject_null_handle(lib):
     assert lib.lattice_fid_region(None, 0, 0, 1, dp) == B.LPC_ERR_INVALID
     assert lib.lattice_population_region(None, 0, 0, 1, dp) == B.LPC_ERR_INVALID
     assert lib.lattice_msd_region(None, 0, 0, 0, 1, dp) == B.LPC_ERR_INVALID
+
+
+def test_padded_size_limit_rejected_on_host(lib):
+    """The ghost-padded arrays must hold fewer than 2^31 sites (32-bit plane
+    offsets in the kernels): 2048 x 1020 x 1020 pads to 2080 x 1024 x 1020."""
+    N = 2048 * 1020 * 1020
+    p = _params(nx=2048, ny=1020, nz=1020)
+    z = np.zeros(1)
+    h = ctypes.c_void_p()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    # valid pointers are never read: the size check comes first
+    F = np.zeros(16)
+    st = lib.lattice_create(ctypes.byref(p), dp(F), dp(F), np.zeros(16, np.uint8).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_uint8)), None, None, None, ctypes.byref(h))
+    assert st == B.LPC_ERR_INVALID and not h.value
+    assert b"2^31" in lib.lpc_last_error()
+    assert N < 2 ** 31 - 1       # the interior alone would fit

@@ -201,3 +201,63 @@ def test_particle_in_bath_256_sampled_sites():
         worst = max(worst, err)
     assert worst <= 1e-5, worst
     lat.close()
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_near_maximum_padded_size():
+    """The largest lattices the library takes: 2040 x 1020 x 1020 sites, whose
+    ghost-padded arrays hold 2^31 - 8.4e6 sites (the limit of the kernels'
+    32-bit plane offsets); BF16 weights.  Two steps of the default schedule:
+    populations conserved, and sampled sites near the far corner (the largest
+    offsets) and elsewhere against the FP64 oracle on boxes."""
+    import ctypes
+    import torch
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+    nx, ny, nz = 2040, 1020, 1020
+    torch.cuda.empty_cache()
+    p = B.lpc_params(nx, ny, nz, (ctypes.c_int32 * 3)(1, 1, 1), 0.6, 5e-6, 1.0, 1, 0, 0, 0)
+    need = ctypes.c_int64()
+    B.check(B.load().lattice_footprint(ctypes.byref(p), 8, ctypes.byref(need)))
+    if torch.cuda.mem_get_info()[0] < need.value * 1.1 or _mem_available_gb() < 100:
+        pytest.skip("needs %.0f GB of device memory and 100 GB of host memory" % (need.value / 1e9))
+    N = nx * ny * nz
+    rng = np.random.default_rng(21)
+    F = rng.random(N, dtype=np.float64)
+    F *= -2.0
+    om = np.empty(N)
+    np.multiply(F, 3.0e4, out=om)
+    solid = np.zeros(N, np.uint8)
+    solid[rng.integers(0, N, N // 10)] = 1
+    shape = (nz, ny, nx)
+    lat = Lattice(nx, ny, nz, F, om, solid, alpha=0.6, weight_dtype=1)
+    n = 2
+    lat.step(n)
+    P = lat.population()
+    assert np.max(np.abs(P / P[0] - 1.0)) <= 1e-5
+    rho = lat.density()
+    pts = [(nz - 1, ny - 1, nx - 1), (nz - 1, ny - 1, 0), (nz - 1, 0, nx - 1), (0, 0, 0), (nz - 2, ny - 3, nx - 5),
+           (nz // 2, ny // 2, nx // 2), (nz - 1, ny // 3, 1000)]
+    pts += [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(12)]
+    r = n + 2
+    F3, om3, so3 = F.reshape(shape), om.reshape(shape), solid.reshape(shape)
+    worst = 0.0
+    for c in pts:
+        Fb, cc = _box_axes(F3, c, r, (1, 1, 1))
+        Ob, _ = _box_axes(om3, c, r, (1, 1, 1))
+        Sb, _ = _box_axes(so3, c, r, (1, 1, 1))
+        e = 2 * r + 1
+        pk = oracle.pack(e, e, e, (0, 0, 0), 0.6, 5e-6, 1.0, Fb, Ob, Sb, oracle.MODE_BF16)
+        res = oracle.run(pk, (Sb == 0).astype(np.float64), n, msd_axes=0)
+        worst = max(worst, abs(rho[c] - res.rho[cc]) / max(1.0, abs(res.rho[cc])))
+    assert worst <= 1e-5, worst
+    lat.close()
