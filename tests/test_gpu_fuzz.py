@@ -34,7 +34,7 @@ def _config(i):
     return inp, lab, nreg
 
 
-@pytest.mark.parametrize("i", range(12))
+@pytest.mark.parametrize("i", range(40))
 def test_random_configuration_all_schedules(i):
     from paper_2603_22553_b300 import binding as B
     from paper_2603_22553_b300.lattice import Lattice, step_many
