@@ -348,7 +348,7 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
         gs[g] = 0.0f;
         gR[g] = make_float2(0.0f, 0.0f);
         for (int a = 0; a < 3; ++a)
-            if (v.msd_axes >> a & 1) {
+            if (gdm && (v.msd_axes >> a & 1)) {
                 gdm[2 * (a * v.Ns + g)] = round_weight<WT>(0.0);
                 gdm[2 * (a * v.Ns + g) + 1] = round_weight<WT>(0.0);
             }
@@ -367,7 +367,7 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
     gs[g] = stay_weight(wo);
     gR[g] = v.R[p];
     for (int a = 0; a < 3; ++a)
-        if (v.msd_axes >> a & 1) {
+        if (gdm && (v.msd_axes >> a & 1)) {
             // the stored out-weights themselves (exact in their own type)
             gdm[2 * (a * v.Ns + g)] = W[(2 * a) * v.Np + p];
             gdm[2 * (a * v.Ns + g) + 1] = W[(2 * a + 1) * v.Np + p];

@@ -81,6 +81,7 @@ template <> __device__ __forceinline__ float4 lds_w4<__nv_bfloat16>(const __nv_b
 
 struct T1Geom {
     int W, TY, S1, S2;
+    int dm_src;                 // stage the MSD out-weight pairs (source-attributed MSD sums)
     int tiles_x, tiles, cz, n_items;
     int slot1, slot2;           // bytes of a state / static slot
     int tx1, tx2;               // transaction bytes of a state / static load
@@ -99,7 +100,8 @@ struct T1Slots {
     int s, R, dm[3], lab, bytes2;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
-__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg = false) {
+// ndm: MSD axes whose out-weight pairs are staged (source-attributed MSD sums)
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm) {
     T1Slots L;
     const int H = TY + 2;
     int off = up128(H * W * 4);
@@ -118,7 +120,7 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
     if (!rho_only) off += up128(C * 8);
     for (int n = 0; n < 3; ++n) {
         L.dm[n] = off;
-        if (n < nmsd) off += up128(C * 2 * wb);
+        if (n < ndm) off += up128(C * 2 * wb);
     }
     L.lab = off;
     if (reg) off += up128(C);
@@ -149,7 +151,12 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     constexpr int KS = ItemSums<REG>::KS, KSP = ItemSums<REG>::KSP;
     static_assert(KS <= 32, "one lane per item sum");
     const int W = g.W, S1 = g.S1, S2 = g.S2;
-    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG);
+    // MSD increments: summed over the source sites with their out-weights
+    // (staged pairs) where regions or reservoir faces need that attribution,
+    // else over the destination sites with the in-weights and source states
+    // the gather already holds (the same total, without the pair traffic)
+    const int ndm = (REG || g.dm_src) ? NMSD : 0;
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG, ndm);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
@@ -247,7 +254,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         tma3(st + SL.s, &maps.gs, fb, sx, sy, z);
                         if (!RHO) tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
 #pragma unroll
-                        for (int m = 0; m < NMSD; ++m) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
+                        for (int m = 0; m < NMSD; ++m)
+                            if (ndm) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
                         if (REG) tma3(st + SL.lab, &maps.glab, fb, sx, sy, z);
                         *issued2 = ++n2;
                         c2.next(S2);
@@ -414,16 +422,21 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const float2 u_u = *reinterpret_cast<const float2*>(uc + o - W);
                     const float2 u_d = *reinterpret_cast<const float2*>(uc + o + W);
                     const float2 u_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv + SL.mu[n]) + o);
-                    const float4 dm = lds_w4<WT>(reinterpret_cast<const WT*>(ss + SL.dm[n]) + 2 * os);
                     const float nb0[6] = {uc[o - 1], muc[n].y, u_u.x, u_d.x, bmu[n].x, u_a.x};
                     const float nb1[6] = {muc[n].x, uc[o + 2], u_u.y, u_d.y, bmu[n].y, u_a.y};
                     muo0[n] = site_mu(q0.win, q0.r, nb0, sp.x, muc[n].x, a);
                     muo1[n] = site_mu(q1.win, q1.r, nb1, sp.y, muc[n].y, a);
-                    float wo0[6], wo1[6];
-                    wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
-                    wo1[2 * a] = dm.z; wo1[2 * a + 1] = dm.w;
-                    dd0[n] = site_dmsd(wo0, muc[n].x, q0.rc, a);
-                    dd1[n] = site_dmsd(wo1, muc[n].y, q1.rc, a);
+                    if (ndm) {
+                        const float4 dm = lds_w4<WT>(reinterpret_cast<const WT*>(ss + SL.dm[n]) + 2 * os);
+                        float wo0[6], wo1[6];
+                        wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
+                        wo1[2 * a] = dm.z; wo1[2 * a + 1] = dm.w;
+                        dd0[n] = site_dmsd(wo0, muc[n].x, q0.rc, a);
+                        dd1[n] = site_dmsd(wo1, muc[n].y, q1.rc, a);
+                    } else {
+                        dd0[n] = site_dmsd_in(q0.win, q0.r, nb0, a);
+                        dd1[n] = site_dmsd_in(q1.win, q1.r, nb1, a);
+                    }
                     if (site0 && to_part) part[3 + a] += dd0[n];
                     if (site1 && to_part) part[3 + a] += dd1[n];
                 }
@@ -631,8 +644,8 @@ int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 // Ring depth d and shared memory of a tile height: S1 = d + 2 state slots
 // (centre and above held), S2 = d + 1 static slots (centre held); per slot one
 // full and one empty barrier, and a header per state slot.
-void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg = false) {
-    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg);
+void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm) {
+    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg, ndm);
     const int ksp = reg ? ItemSums<true>::KSP : ItemSums<false>::KSP;
     const int fixed = 128 + 3 * 8 + 2 * TY * ksp * 8 + 64;   // slack, item barriers/counts/sums, flags
     const int budget = device_props().max_smem_optin - 1024 - fixed;
@@ -653,14 +666,15 @@ void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg = f
 T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool reg = false) {
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    const int ndm = v.gdm ? nmsd : 0;          // pairs staged where the lattice keeps them
     T1Choice c{};
     c.W = t1_box_width(v.G);
     for (int i = 0; i < 3; ++i) {
-        t1_rings(c, kShapes[i], nmsd, wb, false);
+        t1_rings(c, kShapes[i], nmsd, wb, false, false, ndm);
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
-    if (rho_only) t1_rings(c, c.TY, 0, wb, true);
-    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true);
+    if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0);
+    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, nmsd);
     return c;
 }
 
@@ -758,7 +772,7 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
         const cuuint64_t sr[2] = {Xs * 8, Xs * ny * 8};
         const cuuint32_t br[3] = {(cuuint32_t)(2 * kTX), TY, 1};
         ok = ok && tma_encode(&maps->gR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gR, dr, sr, br);
-        if (v.msd_axes) {
+        if (v.gdm) {
             const cuuint64_t dd[4] = {2 * Xs, ny, nz, 3};
             const cuuint64_t sd[3] = {Xs * 2 * e, Xs * ny * 2 * e, Xs * ny * nz * 2 * e};
             const cuuint32_t bd[4] = {(cuuint32_t)(2 * kTX), TY, 1, 1};
@@ -789,7 +803,9 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.slot1 = c.L.bytes1;
     g.slot2 = c.L.bytes2;
     g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
-    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * nmsd) + (reg ? 1 : 0));
+    g.dm_src = (!rho_only && v.gdm) ? 1 : 0;
+    const int ndm = (reg || g.dm_src) ? nmsd : 0;
+    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;

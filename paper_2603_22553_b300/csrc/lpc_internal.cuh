@@ -158,6 +158,16 @@ __device__ __forceinline__ float site_mu(const float* win, const float* r, const
     return u;
 }
 
+// The same MSD increment summed over destinations: the hops into a site
+// along +a and -a from its sources, win_+a (2 mu + rho) + win_-a (-2 mu + rho)
+// at those sources (each link's term, attributed to its destination; over
+// the lattice the same total where every link joins two lattice sites).
+__device__ __forceinline__ float site_dmsd_in(const float* win, const float* r, const float* mu_nb, int a) {
+    const float up = __fmaf_rn(2.0f, mu_nb[2 * a], r[2 * a]);
+    const float dn = __fmaf_rn(-2.0f, mu_nb[2 * a + 1], r[2 * a + 1]);
+    return __fmaf_rn(win[2 * a], up, __fmul_rn(win[2 * a + 1], dn));
+}
+
 // dMSD contribution of a site: 2 (w+a - w-a) mu + (w+a + w-a) rho.
 __device__ __forceinline__ float site_dmsd(const float* wout, float mu_c, float rc, int a) {
     float u = __fsub_rn(wout[2 * a], wout[2 * a + 1]);

@@ -222,13 +222,18 @@ size_t gather_bytes(long long Ns, int wdtype, int msd) {
     return (size_t)Ns * (6 * wb + 4 + 8 + (msd ? 3 * 2 * wb : 0));
 }
 
+// The gather form keeps the MSD out-weight pairs only where the MSD sums are
+// taken over source sites: with regions (the site's region at the step) or
+// reservoir faces (hops into a reservoir count, hops out of one do not).
+bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h->rf.any()); }
+
 // The gather-form static arrays: allocated and filled once (outside any
 // stream capture), from the padded weight planes.
 lpc_status ensure_gather(lpc_lattice* h) {
     if (h->gwin) return LPC_OK;
     const int Xs = gather_pitch(h->p.nx);
     const long long Ns = (long long)Xs * h->p.ny * h->p.nz;
-    char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, h->p.msd_axes));
+    char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
     if (!blk) { set_error("gather-form allocation failed"); return LPC_ERR_OOM; }
     h->Xs = Xs;
     h->Ns = Ns;
@@ -238,7 +243,7 @@ lpc_status ensure_gather(lpc_lattice* h) {
     blk += (size_t)Ns * 4;
     h->gR = (float2*)blk;
     blk += (size_t)Ns * 8;
-    h->gdm = h->p.msd_axes ? (void*)blk : nullptr;       // [3][Ns][2] weights, indexed by axis
+    h->gdm = gather_dm(h) ? (void*)blk : nullptr;       // [3][Ns][2] weights, indexed by axis
     LatticeView v = make_view(h, h->cur);
     cudaError_t e = launch_gather_pack(v, h->p.weight_dtype, h->gwin, h->gs, h->gR, h->gdm, h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "gather pack");
@@ -385,7 +390,7 @@ void release_all(lpc_lattice* h) {
     }
     dfree(h, h->w, Np * 6 * wbytes(h));
     dfree(h, h->R, Np * 8);
-    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, h->p.msd_axes));
+    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
     dfree(h, h->solid, (size_t)h->N);
     if (h->region) dfree(h, h->region, (size_t)h->Xr * h->p.ny * h->p.nz);
     if (h->rpart) dfree(h, h->rpart, (size_t)region_blocks() * LPC_MAX_REGIONS * 6 * 8);
@@ -622,7 +627,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     b += (long long)history_bytes(cap, 1);
     b += 16 * N;    // transient copies of F and omega during create
     if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 20))     // the automatic schedule's gather form
-        b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, p->msd_axes);
+        b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, 0);
     *bytes = b;
     return LPC_OK;
 }
