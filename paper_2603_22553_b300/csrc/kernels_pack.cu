@@ -406,6 +406,80 @@ cudaError_t launch_restart(const LatticeView& v, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+namespace {
+
+template <typename WT> __device__ __forceinline__ float wt_to_float(WT w);
+template <> __device__ __forceinline__ float wt_to_float<float>(float w) { return w; }
+template <> __device__ __forceinline__ float wt_to_float<__nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
+
+// Link form of the static data of a plain lattice (one jump factor, no
+// reservoir face): for every site y and axis a the link to y + e_a as one
+// signed value L (0: closed; L > 0: the hop y -> y + e_a weighs L and the hop
+// back A; L < 0: the hop y -> y + e_a weighs A and the hop back -L), A =
+// alpha/6 rounded like the hop weights (the weight of a downhill or level
+// Metropolis move, Eq. 1).  Read from the padded out-weights (ghost images and
+// walls included), so the weights the kernel rebuilds are the stored ones.
+// Rows of pitch Xs, ny + 1 rows per plane (row 0: the image of row ny - 1 on
+// a periodic y axis, else closed).  R is copied to rows of pitch Xs.  `bad`
+// is set when a link does not fit the form (an open link whose small hop
+// rounded to zero, or no hop equal to A); `a_out` receives A as a float.
+template <typename WT>
+__global__ void k_link_pack(LatticeView v, WT* __restrict__ L, float2* __restrict__ Rl, double alpha,
+                            unsigned int* __restrict__ bad, float* __restrict__ a_out) {
+    const WT* W = static_cast<const WT*>(v.w);
+    const float A = wt_to_float<WT>(round_weight<WT>(alpha / 6.0 * 1.0));
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (gid == 0) *a_out = A;
+    const long long zp = (long long)v.Xp * v.Yp;
+    const long long total = 3LL * v.nz * v.ny1 * v.Xs;
+    for (long long g = gid; g < total; g += stride) {
+        const int x = (int)(g % v.Xs);
+        const long long t = g / v.Xs;
+        const int row = (int)(t % v.ny1);
+        const long long t2 = t / v.ny1;
+        const int z = (int)(t2 % v.nz);
+        const int a = (int)(t2 / v.nz);
+        int y = row - 1;
+        if (row == 0) y = v.per_y ? v.ny - 1 : -1;
+        float val = 0.0f;
+        if (x < v.nx && y >= 0) {
+            const long long p = z * zp + (long long)(y + v.G) * v.Xp + (x + v.G);
+            const long long pn = a == 0 ? p + 1
+                                 : a == 1 ? p + v.Xp
+                                          : (long long)(z + 1 == v.nz ? 0 : z + 1) * zp + (p - z * zp);
+            const float wf = ldw<WT>(W + (long long)(2 * a) * v.Np + p);
+            const float wb = ldw<WT>(W + (long long)(2 * a + 1) * v.Np + pn);
+            if (wf == 0.0f && wb == 0.0f) val = 0.0f;
+            else if (wb == A && wf > 0.0f) val = wf;
+            else if (wf == A && wb > 0.0f) val = -wb;
+            else atomicOr(bad, 1u);
+        }
+        L[g] = round_weight<WT>((double)val);
+    }
+    const long long nr = (long long)v.nz * v.ny * v.Xs;
+    for (long long g = gid; g < nr; g += stride) {
+        const int x = (int)(g % v.Xs);
+        const long long t = g / v.Xs;
+        const int y = (int)(t % v.ny);
+        const int z = (int)(t / v.ny);
+        Rl[g] = x < v.nx ? v.R[z * zp + (long long)(y + v.G) * v.Xp + (x + v.G)] : make_float2(0.0f, 0.0f);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, float2* Rl, double alpha,
+                             unsigned int* bad, float* a_out, cudaStream_t st) {
+    const long long total = 3LL * v.nz * v.ny1 * v.Xs;
+    const int g = grid_for(total, 256);
+    if (wdtype == LPC_WEIGHTS_BF16)
+        k_link_pack<__nv_bfloat16><<<g, 256, 0, st>>>(v, static_cast<__nv_bfloat16*>(L), Rl, alpha, bad, a_out);
+    else
+        k_link_pack<float><<<g, 256, 0, st>>>(v, static_cast<float*>(L), Rl, alpha, bad, a_out);
+    return cudaGetLastError();
+}
+
 // Pitch of the gather-form arrays: rows start on 256-byte boundaries.
 int gather_pitch(int nx) { return (nx + 63) / 64 * 64; }
 

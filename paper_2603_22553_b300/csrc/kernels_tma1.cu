@@ -87,21 +87,26 @@ struct T1Geom {
     int tx1, tx2;               // transaction bytes of a state / static load
     unsigned int* err;
     unsigned int* work;
+    float abig;                 // link form: the weight of a downhill or level hop, alpha/6 as stored
 };
 
 namespace {
 
 // state slot:  rho [TY+2][W] f32 | m [TY+2][W] f32x2 | mu_n [TY+2][W] f32
-// static slot: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2 | dm_n [TY][64] WTx2
-//              | lab [TY][64] u8 (region labels, with regions only)
+// static slot, gather form: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2
+//              | dm_n [TY][64] WTx2 | lab [TY][64] u8 (region labels, with regions only)
+// static slot, link form:   lx [TY][64] WT | ly [TY+1][64] WT (the row above too) | lz [TY][64] WT
+//              | R [TY][64] f32x2
 // (each part on a 128-byte boundary, as TMA requires)
 struct T1Slots {
     int m, mu[3], bytes1;
     int s, R, dm[3], lab, bytes2;
+    int lx, ly, lz;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
 // ndm: MSD axes whose out-weight pairs are staged (source-attributed MSD sums)
-__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm) {
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm,
+                                            bool lnk = false) {
     T1Slots L;
     const int H = TY + 2;
     int off = up128(H * W * 4);
@@ -113,6 +118,21 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
     }
     L.bytes1 = off;
     const int C = TY * kTX;
+    if (lnk) {
+        L.lx = 0;
+        off = up128(C * wb);
+        L.ly = off;
+        off += up128(C * wb + kTX * wb);
+        L.lz = off;
+        off += up128(C * wb);
+        L.R = off;
+        if (!rho_only) off += up128(C * 8);
+        L.s = L.lab = off;
+        for (int n = 0; n < 3; ++n) L.dm[n] = off;
+        L.bytes2 = off;
+        return L;
+    }
+    L.lx = L.ly = L.lz = 0;
     off = up128(6 * C * wb);
     L.s = off;
     off += up128(C * 4);
@@ -139,11 +159,22 @@ struct SlotHdr {
     int tile, za, n, pad;
 };
 
-template <typename WT, int MSD, int NC, bool RHO, bool REG>
+// Link form (LNK): the static data of a plain lattice (one jump factor,
+// no reservoir face, no regions) as one signed value per link and axis,
+// L_a(y) for the link between y and y + e_a: 0 = closed; L > 0: the hop
+// y -> y + e_a has weight L and the hop back the weight A = alpha/6 of a
+// downhill or level Metropolis move (Eq. 1); L < 0: the hop y -> y + e_a has
+// weight A and the hop back -L.  One of the two hops of an open link is
+// always A, so these are exactly the stored weights.
+__device__ __forceinline__ float link_fwd(float L, float A) { return L > 0.f ? L : (L < 0.f ? A : 0.f); }
+__device__ __forceinline__ float link_bwd(float L, float A) { return L > 0.f ? A : (L < 0.f ? -L : 0.f); }
+
+template <typename WT, int MSD, int NC, bool RHO, bool REG, bool LNK>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
 k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     static_assert(!RHO || MSD == 0, "the rho-only step carries no moments");
     static_assert(!RHO || !REG, "the rho-only step takes no sums");
+    static_assert(!REG || !LNK, "lattices with regions keep the gather form");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc(MSD);
@@ -155,8 +186,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     // (staged pairs) where regions or reservoir faces need that attribution,
     // else over the destination sites with the in-weights and source states
     // the gather already holds (the same total, without the pair traffic)
-    const int ndm = (REG || g.dm_src) ? NMSD : 0;
-    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG, ndm);
+    const int ndm = LNK ? 0 : ((REG || g.dm_src) ? NMSD : 0);
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG, ndm, LNK);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
@@ -250,8 +281,15 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         const int z = za + q;
                         fence_proxy_async();
                         mbar_expect_tx(fb, (uint32_t)g.tx2);
-                        tma4(st, &maps.gwin, fb, sx, sy, z, 0);
-                        tma3(st + SL.s, &maps.gs, fb, sx, sy, z);
+                        if (LNK) {
+                            // link planes in rows of ny + 1 (row 0: the image of row ny - 1)
+                            tma4(st + SL.lx, &maps.glnk1, fb, sx, sy + 1, z, 0);
+                            tma4(st + SL.ly, &maps.glnk2, fb, sx, sy, z, 1);
+                            tma4(st + SL.lz, &maps.glnk1, fb, sx, sy + 1, z, 2);
+                        } else {
+                            tma4(st, &maps.gwin, fb, sx, sy, z, 0);
+                            tma3(st + SL.s, &maps.gs, fb, sx, sy, z);
+                        }
                         if (!RHO) tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
 #pragma unroll
                         for (int m = 0; m < NMSD; ++m)
@@ -320,6 +358,21 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             // the pair has ghost images to write: it lies within G of a periodic face
             const bool images = (v.per_x && (x < G || x + 1 >= v.nx - G)) || (v.per_y && (y < G || y >= v.ny - G));
             const long long col = (long long)(y + G) * v.Xp + (x + G);
+            // link form: the +z links of the plane below (they end in this
+            // plane) and, for lane 0, the +x link of the site left of the tile
+            // (it ends in site 0), read from global memory; later planes take
+            // the +z links from the previous plane's slot
+            float lzb0 = 0.f, lzb1 = 0.f, lxe = 0.f;
+            const WT* lnk = static_cast<const WT*>(v.lnk);
+            const long long lplane = (long long)v.ny1 * v.Xs;     // one axis, one plane
+            const int xe = (x == 0 ? v.nx : x) - 1;                // lane 0: the column left of the tile
+            if (LNK) {
+                const int zb = h.za == 0 ? nz - 1 : h.za - 1;
+                const long long lb = (2LL * nz + zb) * lplane + (long long)(y + 1) * v.Xs + x;
+                if (site0) lzb0 = ldw<WT>(lnk + lb);
+                if (site1) lzb1 = ldw<WT>(lnk + lb + 1);
+                if (lane == 0 && ok_y) lxe = ldw<WT>(lnk + (long long)h.za * lplane + (long long)(y + 1) * v.Xs + xe);
+            }
             // plane za-1: keep this lane's two columns as "below"
             float2 br, bmu[3];
             float4 bm;
@@ -356,19 +409,51 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 const float2 r_u = *reinterpret_cast<const float2*>(rc + o - W);
                 const float2 r_d = *reinterpret_cast<const float2*>(rc + o + W);
                 const float2 r_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv) + o);
-                const WT* win = reinterpret_cast<const WT*>(ss);
-                const float2 sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
                 float2 muc[3];
 #pragma unroll
                 for (int n = 0; n < NMSD; ++n)
                     muc[n] = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sc + SL.mu[n]) + o);
 
                 SiteIn q0, q1;
+                float2 sp;
+                float lwo0[6], lwo1[6];          // link form: the two sites' out-weights
+                if constexpr (LNK) {
+                    const float A = g.abig;
+                    const float2 lx = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.lx) + os);
+                    const float2 lyb = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.ly) + os);       // row above
+                    const float2 ly = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.ly) + os + kTX);  // own row
+                    const float2 lz = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.lz) + os);
+                    float lxm = __shfl_up_sync(0xffffffffu, lx.y, 1);   // +x link ending in site 0
+                    if (lane == 0) lxm = lxe;
+                    // in-weights: the +a hop from y - e_a, the -a hop back over y's own link
+                    q0.win[0] = link_fwd(lxm, A);   q1.win[0] = link_fwd(lx.x, A);
+                    q0.win[1] = link_bwd(lx.x, A);  q1.win[1] = link_bwd(lx.y, A);
+                    q0.win[2] = link_fwd(lyb.x, A); q1.win[2] = link_fwd(lyb.y, A);
+                    q0.win[3] = link_bwd(ly.x, A);  q1.win[3] = link_bwd(ly.y, A);
+                    q0.win[4] = link_fwd(lzb0, A);  q1.win[4] = link_fwd(lzb1, A);
+                    q0.win[5] = link_bwd(lz.x, A);  q1.win[5] = link_bwd(lz.y, A);
+                    // out-weights: forward over the own link, backward over y - e_a's
+                    lwo0[0] = link_fwd(lx.x, A);  lwo1[0] = link_fwd(lx.y, A);
+                    lwo0[1] = link_bwd(lxm, A);   lwo1[1] = link_bwd(lx.x, A);
+                    lwo0[2] = link_fwd(ly.x, A);  lwo1[2] = link_fwd(ly.y, A);
+                    lwo0[3] = link_bwd(lyb.x, A); lwo1[3] = link_bwd(lyb.y, A);
+                    lwo0[4] = link_fwd(lz.x, A);  lwo1[4] = link_fwd(lz.y, A);
+                    lwo0[5] = link_bwd(lzb0, A);  lwo1[5] = link_bwd(lzb1, A);
+                    sp = make_float2(stay_weight(lwo0), stay_weight(lwo1));
+                    // for the next plane: its +z links from below, lane 0's left link
+                    lzb0 = lz.x;
+                    lzb1 = lz.y;
+                    if (lane == 0 && ok_y && q + 1 < h.n)
+                        lxe = ldw<WT>(lnk + (long long)(z + 1) * lplane + (long long)(y + 1) * v.Xs + xe);
+                } else {
+                    const WT* win = reinterpret_cast<const WT*>(ss);
+                    sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float2 wk = lds_w2<WT>(win + k * C + os);
-                    q0.win[k] = wk.x;
-                    q1.win[k] = wk.y;
+                    for (int k = 0; k < 6; ++k) {
+                        const float2 wk = lds_w2<WT>(win + k * C + os);
+                        q0.win[k] = wk.x;
+                        q1.win[k] = wk.y;
+                    }
                 }
                 q0.r[0] = r_l;   q0.r[1] = r_c.y; q0.r[2] = r_u.x; q0.r[3] = r_d.x; q0.r[4] = br.x; q0.r[5] = r_a.x;
                 q1.r[0] = r_c.x; q1.r[1] = r_r;   q1.r[2] = r_u.y; q1.r[3] = r_d.y; q1.r[4] = br.y; q1.r[5] = r_a.y;
@@ -426,7 +511,10 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const float nb1[6] = {muc[n].x, uc[o + 2], u_u.y, u_d.y, bmu[n].y, u_a.y};
                     muo0[n] = site_mu(q0.win, q0.r, nb0, sp.x, muc[n].x, a);
                     muo1[n] = site_mu(q1.win, q1.r, nb1, sp.y, muc[n].y, a);
-                    if (ndm) {
+                    if (LNK) {
+                        dd0[n] = site_dmsd(lwo0, muc[n].x, q0.rc, a);
+                        dd1[n] = site_dmsd(lwo1, muc[n].y, q1.rc, a);
+                    } else if (ndm) {
                         const float4 dm = lds_w4<WT>(reinterpret_cast<const WT*>(ss + SL.dm[n]) + 2 * os);
                         float wo0[6], wo1[6];
                         wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
@@ -605,25 +693,25 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         items_finish<NC + 1>(v, g.n_items, reinterpret_cast<double*>(ring1));
 }
 
-template <typename WT, int MSD, int NC, bool REG>
-void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false, REG>); }
+template <typename WT, int MSD, int NC, bool REG, bool LNK>
+void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false, REG, LNK>); }
 
-template <int NC>
+template <int NC, bool LNK>
 void* t1_rho_kernel(int wdtype) {
-    return wdtype == LPC_WEIGHTS_BF16 ? reinterpret_cast<void*>(&k_step_tma1<__nv_bfloat16, 0, NC, true, false>)
-                                      : reinterpret_cast<void*>(&k_step_tma1<float, 0, NC, true, false>);
+    return wdtype == LPC_WEIGHTS_BF16 ? reinterpret_cast<void*>(&k_step_tma1<__nv_bfloat16, 0, NC, true, false, LNK>)
+                                      : reinterpret_cast<void*>(&k_step_tma1<float, 0, NC, true, false, LNK>);
 }
 
-template <int NC, bool REG>
+template <int NC, bool REG, bool LNK>
 void* t1_kernel_shape(int wdtype, int msd) {
     static void* tab[2][8] = {
-        {t1_fn<float, 0, NC, REG>(), t1_fn<float, 1, NC, REG>(), t1_fn<float, 2, NC, REG>(),
-         t1_fn<float, 3, NC, REG>(), t1_fn<float, 4, NC, REG>(), t1_fn<float, 5, NC, REG>(),
-         t1_fn<float, 6, NC, REG>(), t1_fn<float, 7, NC, REG>()},
-        {t1_fn<__nv_bfloat16, 0, NC, REG>(), t1_fn<__nv_bfloat16, 1, NC, REG>(),
-         t1_fn<__nv_bfloat16, 2, NC, REG>(), t1_fn<__nv_bfloat16, 3, NC, REG>(),
-         t1_fn<__nv_bfloat16, 4, NC, REG>(), t1_fn<__nv_bfloat16, 5, NC, REG>(),
-         t1_fn<__nv_bfloat16, 6, NC, REG>(), t1_fn<__nv_bfloat16, 7, NC, REG>()}};
+        {t1_fn<float, 0, NC, REG, LNK>(), t1_fn<float, 1, NC, REG, LNK>(), t1_fn<float, 2, NC, REG, LNK>(),
+         t1_fn<float, 3, NC, REG, LNK>(), t1_fn<float, 4, NC, REG, LNK>(), t1_fn<float, 5, NC, REG, LNK>(),
+         t1_fn<float, 6, NC, REG, LNK>(), t1_fn<float, 7, NC, REG, LNK>()},
+        {t1_fn<__nv_bfloat16, 0, NC, REG, LNK>(), t1_fn<__nv_bfloat16, 1, NC, REG, LNK>(),
+         t1_fn<__nv_bfloat16, 2, NC, REG, LNK>(), t1_fn<__nv_bfloat16, 3, NC, REG, LNK>(),
+         t1_fn<__nv_bfloat16, 4, NC, REG, LNK>(), t1_fn<__nv_bfloat16, 5, NC, REG, LNK>(),
+         t1_fn<__nv_bfloat16, 6, NC, REG, LNK>(), t1_fn<__nv_bfloat16, 7, NC, REG, LNK>()}};
     return tab[wdtype == LPC_WEIGHTS_BF16 ? 1 : 0][msd & 7];
 }
 
@@ -644,8 +732,8 @@ int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 // Ring depth d and shared memory of a tile height: S1 = d + 2 state slots
 // (centre and above held), S2 = d + 1 static slots (centre held); per slot one
 // full and one empty barrier, and a header per state slot.
-void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm) {
-    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg, ndm);
+void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm, bool lnk) {
+    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg, ndm, lnk);
     const int ksp = reg ? ItemSums<true>::KSP : ItemSums<false>::KSP;
     const int fixed = 128 + 3 * 8 + 2 * TY * ksp * 8 + 64;   // slack, item barriers/counts/sums, flags
     const int budget = device_props().max_smem_optin - 1024 - fixed;
@@ -666,32 +754,39 @@ void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, in
 T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool reg = false) {
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
-    const int ndm = v.gdm ? nmsd : 0;          // pairs staged where the lattice keeps them
+    const bool lnk = v.lnk != nullptr;         // the lattice's static data is in link form
+    const int ndm = (!lnk && v.gdm) ? nmsd : 0;  // pairs staged where the lattice keeps them
     T1Choice c{};
     c.W = t1_box_width(v.G);
     for (int i = 0; i < 3; ++i) {
-        t1_rings(c, kShapes[i], nmsd, wb, false, false, ndm);
+        t1_rings(c, kShapes[i], nmsd, wb, false, false, ndm, lnk);
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
-    if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0);
-    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, nmsd);
+    if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0, lnk);
+    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, nmsd, false);
     return c;
 }
 
-void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false, bool reg = false) {
+void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false, bool reg = false, bool lnk = false) {
     if (rho_only) {
-        if (TY == 16) return t1_rho_kernel<16>(wdtype);
-        if (TY == 12) return t1_rho_kernel<12>(wdtype);
-        return t1_rho_kernel<8>(wdtype);
+        if (lnk) return TY == 16 ? t1_rho_kernel<16, true>(wdtype)
+                                 : (TY == 12 ? t1_rho_kernel<12, true>(wdtype) : t1_rho_kernel<8, true>(wdtype));
+        return TY == 16 ? t1_rho_kernel<16, false>(wdtype)
+                        : (TY == 12 ? t1_rho_kernel<12, false>(wdtype) : t1_rho_kernel<8, false>(wdtype));
     }
     if (reg) {
-        if (TY == 16) return t1_kernel_shape<16, true>(wdtype, msd);
-        if (TY == 12) return t1_kernel_shape<12, true>(wdtype, msd);
-        return t1_kernel_shape<8, true>(wdtype, msd);
+        if (TY == 16) return t1_kernel_shape<16, true, false>(wdtype, msd);
+        if (TY == 12) return t1_kernel_shape<12, true, false>(wdtype, msd);
+        return t1_kernel_shape<8, true, false>(wdtype, msd);
     }
-    if (TY == 16) return t1_kernel_shape<16, false>(wdtype, msd);
-    if (TY == 12) return t1_kernel_shape<12, false>(wdtype, msd);
-    return t1_kernel_shape<8, false>(wdtype, msd);
+    if (lnk) {
+        if (TY == 16) return t1_kernel_shape<16, false, true>(wdtype, msd);
+        if (TY == 12) return t1_kernel_shape<12, false, true>(wdtype, msd);
+        return t1_kernel_shape<8, false, true>(wdtype, msd);
+    }
+    if (TY == 16) return t1_kernel_shape<16, false, false>(wdtype, msd);
+    if (TY == 12) return t1_kernel_shape<12, false, false>(wdtype, msd);
+    return t1_kernel_shape<8, false, false>(wdtype, msd);
 }
 
 }  // namespace
@@ -700,8 +795,10 @@ cudaError_t t1_prepare(int wdtype, int msd) {
     static bool done[2][8] = {};
     bool& d = done[wdtype == LPC_WEIGHTS_BF16][msd & 7];
     if (d) return cudaSuccess;
-    for (int i = 0; i < 9; ++i) {
-        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, i / 3 == 1, i / 3 == 2);
+    // per tile height: full step, rho-only step, with regions, link form, link-form rho-only step
+    for (int i = 0; i < 15; ++i) {
+        const int mode = i / 3;
+        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, mode == 1 || mode == 4, mode == 2, mode >= 3);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, fn);
         if (e != cudaSuccess) return e;
@@ -735,7 +832,7 @@ bool t1_supported(const LatticeView& v, int wdtype) {
 }
 
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
-    if (!v.gwin) return false;
+    if (!v.gwin && !v.lnk) return false;
     const T1Choice c = t1_choose(v, wdtype);
     const cuuint64_t Xp = (cuuint64_t)v.Xp, Yp = (cuuint64_t)v.Yp, nz = (cuuint64_t)v.nz;
     const cuuint32_t W = (cuuint32_t)c.W, TY = (cuuint32_t)c.TY;
@@ -760,14 +857,26 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
         const cuuint64_t e = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
         const CUtensorMapDataType dt =
             wdtype == LPC_WEIGHTS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-        const cuuint64_t dw[4] = {Xs, ny, nz, 6};
-        const cuuint64_t sw[3] = {Xs * e, Xs * ny * e, Xs * ny * nz * e};
-        const cuuint32_t bw[4] = {(cuuint32_t)kTX, TY, 1, 6};
-        ok = ok && tma_encode(&maps->gwin, dt, 4, v.gwin, dw, sw, bw);
-        const cuuint64_t ds[3] = {Xs, ny, nz};
-        const cuuint64_t ss[2] = {Xs * 4, Xs * ny * 4};
-        const cuuint32_t bs[3] = {(cuuint32_t)kTX, TY, 1};
-        ok = ok && tma_encode(&maps->gs, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gs, ds, ss, bs);
+        if (v.lnk) {
+            // link planes [3][nz][ny + 1][Xs]: boxes of TY rows (x and z links)
+            // and TY + 1 rows (y links, with the row above)
+            const cuuint64_t ny1 = (cuuint64_t)v.ny1;
+            const cuuint64_t dl[4] = {Xs, ny1, nz, 3};
+            const cuuint64_t sl[3] = {Xs * e, Xs * ny1 * e, Xs * ny1 * nz * e};
+            const cuuint32_t bl1[4] = {(cuuint32_t)kTX, TY, 1, 1};
+            const cuuint32_t bl2[4] = {(cuuint32_t)kTX, TY + 1, 1, 1};
+            ok = ok && tma_encode(&maps->glnk1, dt, 4, v.lnk, dl, sl, bl1);
+            ok = ok && tma_encode(&maps->glnk2, dt, 4, v.lnk, dl, sl, bl2);
+        } else {
+            const cuuint64_t dw[4] = {Xs, ny, nz, 6};
+            const cuuint64_t sw[3] = {Xs * e, Xs * ny * e, Xs * ny * nz * e};
+            const cuuint32_t bw[4] = {(cuuint32_t)kTX, TY, 1, 6};
+            ok = ok && tma_encode(&maps->gwin, dt, 4, v.gwin, dw, sw, bw);
+            const cuuint64_t ds[3] = {Xs, ny, nz};
+            const cuuint64_t ss[2] = {Xs * 4, Xs * ny * 4};
+            const cuuint32_t bs[3] = {(cuuint32_t)kTX, TY, 1};
+            ok = ok && tma_encode(&maps->gs, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, v.gs, ds, ss, bs);
+        }
         const cuuint64_t dr[3] = {2 * Xs, ny, nz};
         const cuuint64_t sr[2] = {Xs * 8, Xs * ny * 8};
         const cuuint32_t br[3] = {(cuuint32_t)(2 * kTX), TY, 1};
@@ -790,8 +899,9 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
 
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st, bool rho_only) {
-    if (!v.gwin) return cudaErrorInvalidValue;
-    const bool reg = !rho_only && t1_fused_regions(v, wdtype);
+    if (!v.gwin && !v.lnk) return cudaErrorInvalidValue;
+    const bool lnk = v.lnk != nullptr;
+    const bool reg = !rho_only && !lnk && t1_fused_regions(v, wdtype);
     const T1Choice c = t1_choose(v, wdtype, rho_only, reg);
     const int nmsd = rho_only ? 0 : popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
@@ -803,9 +913,13 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.slot1 = c.L.bytes1;
     g.slot2 = c.L.bytes2;
     g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
-    g.dm_src = (!rho_only && v.gdm) ? 1 : 0;
+    g.dm_src = (!rho_only && !lnk && v.gdm) ? 1 : 0;
     const int ndm = (reg || g.dm_src) ? nmsd : 0;
-    g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
+    g.abig = v.link_a;
+    if (lnk)   // three link boxes (one with the row above) and R
+        g.tx2 = c.TY * kTX * (3 * wb + (rho_only ? 0 : 8)) + kTX * wb;
+    else
+        g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
@@ -828,7 +942,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     LatticeView vv = v;
     TBMaps mm = maps;
     void* args[] = {&mm, &vv, &g};
-    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes, rho_only, reg), dim3((unsigned)grid),
+    return cudaLaunchKernel(t1_kernel(c.TY, wdtype, v.msd_axes, rho_only, reg, lnk), dim3((unsigned)grid),
                             dim3((c.TY + 1) * 32), args, (size_t)c.smem, st);
 }
 

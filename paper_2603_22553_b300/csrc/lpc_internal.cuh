@@ -51,6 +51,12 @@ struct LatticeView {
     const void* gdm;                 // [3][Ns][2] (w_+a(x), w_-a(x)) for the MSD axes, float or bf16
     int Xs;
     long long Ns;
+    // link form of the static data (plain lattices; one-step TMA kernel), null
+    // unless used: [3][nz][ny1][Xs] signed link weights (ny1 = ny + 1 rows,
+    // row 0 the image of row ny - 1), R in gR; link_a: alpha/6 as stored
+    const void* lnk;
+    int ny1;
+    float link_a;
     // reductions: per-block partials, completion counter, history
     double* partials;                // [levels][grid][kNumSums]
     unsigned int* counter;
@@ -466,6 +472,10 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
 int gather_pitch(int nx);
 cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,
                                cudaStream_t st);
+// Link form of a plain lattice's static data (v.Xs, v.ny1 set); bad / a_out:
+// device words (a link that does not fit the form; alpha/6 as stored).
+cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, float2* Rl, double alpha,
+                             unsigned int* bad, float* a_out, cudaStream_t st);
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st);
 int tb_grid(const LatticeView& v, int wdtype, int K);

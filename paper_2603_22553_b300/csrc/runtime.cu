@@ -94,6 +94,12 @@ struct lpc_lattice {
     void* gdm = nullptr;
     int Xs = 0;
     long long Ns = 0;
+    // link form of the static data (plain lattices), instead of the gather form
+    void* lnk = nullptr;
+    size_t lnk_bytes = 0;
+    int ny1 = 0;
+    float link_a = 0.0f;
+    bool links_given = false;           // created with per-link jump factors
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -171,6 +177,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     for (int a = 0; a < 3; ++a) { v.mu_in[a] = h->mu[in][a]; v.mu_out[a] = h->mu[in ^ 1][a]; }
     v.w = h->w; v.R = h->R;
     v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.Xs = h->Xs; v.Ns = h->Ns;
+    v.lnk = h->lnk; v.ny1 = h->ny1; v.link_a = h->link_a;
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
     v.region = h->region; v.nreg = h->nreg; v.Xr = h->Xr;
@@ -227,12 +234,48 @@ size_t gather_bytes(long long Ns, int wdtype, int msd) {
 // reservoir faces (hops into a reservoir count, hops out of one do not).
 bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h->rf.any()); }
 
-// The gather-form static arrays: allocated and filled once (outside any
-// stream capture), from the padded weight planes.
+// The static data of the one-step TMA kernel, made once (outside any stream
+// capture) from the padded weight planes: the link form for plain lattices
+// (one jump factor, no reservoir face, no regions: 12 + 8 bytes per site with
+// FP32 weights, 6 + 8 with BF16), else the gather form (or when a link does
+// not fit the link form).
 lpc_status ensure_gather(lpc_lattice* h) {
-    if (h->gwin) return LPC_OK;
+    if (h->gwin || h->lnk) return LPC_OK;
     const int Xs = gather_pitch(h->p.nx);
     const long long Ns = (long long)Xs * h->p.ny * h->p.nz;
+    if (!h->links_given && !h->rf.any() && h->nreg == 0) {
+        const int ny1 = h->p.ny + 1;
+        const size_t lb = (size_t)3 * h->p.nz * ny1 * Xs * wbytes(h);
+        const size_t bytes = (lb + 255) / 256 * 256 + (size_t)Ns * 8;
+        char* blk = (char*)dalloc(h, bytes);
+        if (blk) {
+            h->Xs = Xs;
+            h->ny1 = ny1;
+            LatticeView v = make_view(h, h->cur);
+            v.Xs = Xs;
+            v.ny1 = ny1;
+            float2* Rl = reinterpret_cast<float2*>(blk + (lb + 255) / 256 * 256);
+            unsigned int* bad = reinterpret_cast<unsigned int*>(h->scratch);
+            float* a_out = reinterpret_cast<float*>(h->scratch) + 1;
+            cudaError_t e = cudaMemsetAsync(bad, 0, 4, h->wstream);
+            if (e == cudaSuccess)
+                e = launch_link_pack(v, h->p.weight_dtype, blk, Rl, h->p.alpha, bad, a_out, h->wstream);
+            unsigned int hb[2] = {1u, 0u};
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, h->wstream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+            if (e != cudaSuccess) { dfree(h, blk, bytes); return cuda_fail(e, "link pack"); }
+            if (hb[0] == 0u) {
+                h->lnk = blk;
+                h->lnk_bytes = bytes;
+                h->gR = Rl;
+                h->Ns = Ns;
+                memcpy(&h->link_a, &hb[1], 4);
+                return LPC_OK;
+            }
+            dfree(h, blk, bytes);     // a link outside the form: use the gather form
+            h->ny1 = 0;
+        }
+    }
     char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
     if (!blk) { set_error("gather-form allocation failed"); return LPC_ERR_OOM; }
     h->Xs = Xs;
@@ -391,6 +434,7 @@ void release_all(lpc_lattice* h) {
     dfree(h, h->w, Np * 6 * wbytes(h));
     dfree(h, h->R, Np * 8);
     if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
+    if (h->lnk) dfree(h, h->lnk, h->lnk_bytes);
     dfree(h, h->solid, (size_t)h->N);
     if (h->region) dfree(h, h->region, (size_t)h->Xr * h->p.ny * h->p.nz);
     if (h->rpart) dfree(h, h->rpart, (size_t)region_blocks() * LPC_MAX_REGIONS * 6 * 8);
@@ -501,6 +545,7 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     h->p = *p;
     h->N = N;
     h->rf = rf;
+    h->links_given = alpha_links != nullptr;
     h->nreg = o.n_regions;
     h->Xr = gather_pitch(p->nx);
     cudaGetDevice(&h->device);
