@@ -362,7 +362,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             // plane) and, for lane 0, the +x link of the site left of the tile
             // (it ends in site 0), read from global memory; later planes take
             // the +z links from the previous plane's slot
-            float lzb0 = 0.f, lzb1 = 0.f, lxe = 0.f;
+            float lzb0 = 0.f, lzb1 = 0.f, lxe = 0.f, lxe1 = 0.f;   // lane 0: this plane's and the next
             const WT* lnk = static_cast<const WT*>(v.lnk);
             const long long lplane = (long long)v.ny1 * v.Xs;     // one axis, one plane
             const int xe = (x == 0 ? v.nx : x) - 1;                // lane 0: the column left of the tile
@@ -371,7 +371,10 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 const long long lb = (2LL * nz + zb) * lplane + (long long)(y + 1) * v.Xs + x;
                 if (site0) lzb0 = ldw<WT>(lnk + lb);
                 if (site1) lzb1 = ldw<WT>(lnk + lb + 1);
-                if (lane == 0 && ok_y) lxe = ldw<WT>(lnk + (long long)h.za * lplane + (long long)(y + 1) * v.Xs + xe);
+                if (lane == 0 && ok_y) {
+                    lxe = ldw<WT>(lnk + (long long)h.za * lplane + (long long)(y + 1) * v.Xs + xe);
+                    if (h.n > 1) lxe1 = ldw<WT>(lnk + (long long)(h.za + 1) * lplane + (long long)(y + 1) * v.Xs + xe);
+                }
             }
             // plane za-1: keep this lane's two columns as "below"
             float2 br, bmu[3];
@@ -440,11 +443,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     lwo0[4] = link_fwd(lz.x, A);  lwo1[4] = link_fwd(lz.y, A);
                     lwo0[5] = link_bwd(lzb0, A);  lwo1[5] = link_bwd(lzb1, A);
                     sp = make_float2(stay_weight(lwo0), stay_weight(lwo1));
-                    // for the next plane: its +z links from below, lane 0's left link
+                    // for the next plane: its +z links from below; lane 0's left
+                    // links are read two planes ahead
                     lzb0 = lz.x;
                     lzb1 = lz.y;
-                    if (lane == 0 && ok_y && q + 1 < h.n)
-                        lxe = ldw<WT>(lnk + (long long)(z + 1) * lplane + (long long)(y + 1) * v.Xs + xe);
+                    lxe = lxe1;
+                    if (lane == 0 && ok_y && q + 2 < h.n)
+                        lxe1 = ldw<WT>(lnk + (long long)(z + 2) * lplane + (long long)(y + 1) * v.Xs + xe);
                 } else {
                     const WT* win = reinterpret_cast<const WT*>(ss);
                     sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
