@@ -112,7 +112,9 @@ typedef struct {
     int32_t pitch_y;          /* padded y extent */
     int32_t kernel;           /* LPC_KERNEL_* chosen for lattice_step_n */
     int32_t block_steps;      /* time steps per launch of that kernel */
-    int32_t reserved;
+    int32_t static_form;      /* static data of the TMA one-step kernel: 0 not made yet,
+                                 1 gather form (in-weights, stay weight, R), 2 link form
+                                 (one signed weight per link and axis, R) */
     int64_t device_bytes;     /* device memory held by the lattice */
     int64_t bytes_per_site_update; /* algorithmic HBM bytes of one site update (state
                                       read + write, hop weights, R, moments, region label) */

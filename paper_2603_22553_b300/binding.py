@@ -55,7 +55,7 @@ class lpc_info(ctypes.Structure):
     _fields_ = [("n_sites", ctypes.c_int64), ("n_padded", ctypes.c_int64),
                 ("ghost", ctypes.c_int32), ("pitch_x", ctypes.c_int32),
                 ("pitch_y", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("block_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("block_steps", ctypes.c_int32), ("static_form", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("bytes_per_site_update", ctypes.c_int64)]
 
 

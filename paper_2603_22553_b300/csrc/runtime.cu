@@ -955,7 +955,7 @@ lpc_status lattice_info(lpc_lattice* h, lpc_info* out) {
     out->pitch_y = h->Yp;
     out->kernel = h->kernel;
     out->block_steps = h->kdepth;
-    out->reserved = 0;
+    out->static_form = h->lnk ? 2 : (h->gwin ? 1 : 0);
     out->device_bytes = h->device_bytes;
     long long b = 24 + 6 * (long long)wbytes(h) + 8;
     for (int a = 0; a < 3; ++a) if (h->p.msd_axes >> a & 1) b += 8;

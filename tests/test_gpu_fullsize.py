@@ -261,3 +261,60 @@ def test_near_maximum_padded_size():
         worst = max(worst, abs(rho[c] - res.rho[cc]) / max(1.0, abs(res.rho[cc])))
     assert worst <= 1e-5, worst
     lat.close()
+
+
+@pytest.mark.parametrize("cfg", [
+    ((320, 400, 400), (1, 1, 1), 0, 0),
+    ((320, 400, 400), (0, 1, 1), 1, 1),          # x walls, BF16, first moment along x
+    ((320, 397, 403), (1, 0, 0), 7, 0),          # ragged x and y, y and z walls, every moment
+    ((336, 389, 392), (1, 1, 1), 3, 1),          # ragged, BF16, x and y moments
+])
+def test_link_form_matches_register_pipelined_kernel(cfg):
+    """Lattices of more than 5e7 sites keep their static data in link form
+    (one signed weight per link): the one-step TMA kernel rebuilds every hop
+    and stay weight exactly, so its states equal those of the register-
+    pipelined kernel bit for bit; the sums agree to FP32 rounding, and
+    sampled sites agree with the FP64 oracle on boxes."""
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice
+    shape, per, msd, wdt = cfg
+    nz, ny, nx = shape
+    rng = np.random.default_rng(sum(shape) + msd)
+    F = rng.normal(-1.0, 1.0, shape)
+    om = rng.normal(0.0, 3.0e4, shape)
+    solid = (rng.random(shape) < 0.25).astype(np.uint8)
+    n = 6
+    out = []
+    for sched in ((B.LPC_KERNEL_AUTO, 1), (B.LPC_KERNEL_STEP1, 1)):
+        lat = Lattice(nx, ny, nz, F, om, solid, periodic=per, alpha=0.7, weight_dtype=wdt, msd_axes=msd)
+        lat.set_schedule(*sched)
+        lat.step(n)
+        if sched[0] == B.LPC_KERNEL_AUTO:
+            info = lat.info()
+            assert info["kernel"] == B.LPC_KERNEL_TB and info["block_steps"] == 1 and info["static_form"] == 2
+        res = dict(rho=lat.density(), m=lat.magnetization(), M=lat.fid(), P=lat.population())
+        for a in range(3):
+            if msd >> a & 1:
+                res["mu%d" % a] = lat.moment(a)
+                res["msd%d" % a] = lat.msd(a)
+        out.append(res)
+        lat.close()
+    a, b = out
+    assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["m"], b["m"])
+    assert np.allclose(a["M"], b["M"], rtol=1e-6, atol=1e-6 * abs(b["M"][0]))
+    assert np.allclose(a["P"], b["P"], rtol=1e-6)
+    for ax in range(3):
+        if msd >> ax & 1:
+            assert np.array_equal(a["mu%d" % ax], b["mu%d" % ax])
+            assert np.allclose(a["msd%d" % ax][1:], b["msd%d" % ax][1:], rtol=1e-5)
+    r = n + 2
+    pts = [(nz - 1, ny - 1, nx - 1), (0, 0, 0), (nz // 2, 0, nx - 1)] + \
+          [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(8)]
+    for c in pts:
+        Fb, cc = _box_axes(F, c, r, per[::-1])
+        Ob, _ = _box_axes(om, c, r, per[::-1])
+        Sb, _ = _box_axes(solid, c, r, per[::-1])
+        nzb, nyb, nxb = Fb.shape
+        pk = oracle.pack(nxb, nyb, nzb, (0, 0, 0), 0.7, 5e-6, 1.0, Fb, Ob, Sb, H.MODE_OF_DTYPE[wdt])
+        res = oracle.run(pk, (Sb == 0).astype(np.float64), n, msd_axes=0)
+        assert abs(a["rho"][c] - res.rho[cc]) <= 1e-5 * max(1.0, abs(res.rho[cc]))
