@@ -37,6 +37,9 @@ WORKLOADS = {
                          desc="512^3 porous monolith, 40% solid (correlated noise sigma 4), "
                               "F in [-5,0] kT, shift in [-12,0] ppm, periodic, FP32 state, "
                               "FP32 hop weights", sub=64),
+    "monolith_384": dict(make=lambda: lpc_inputs.monolith(edge=384, msd_axes=0),
+                         desc="384^3 porous monolith (the 512^3 recipe at 0.42 of the sites, for "
+                              "profiling), FP32 state and hop weights", sub=64),
     "monolith_512_bf16": dict(make=lambda: lpc_inputs.monolith(edge=512, msd_axes=0, weight_dtype=1),
                               desc="512^3 porous monolith, FP32 state, BF16 hop weights", sub=64),
     "particle_in_bath_256": dict(make=lambda: lpc_inputs.particle_in_bath(),
