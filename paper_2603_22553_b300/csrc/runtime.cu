@@ -239,15 +239,19 @@ bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h
 // lattices (one jump factor, no reservoir face, no regions: 12 + 8 bytes per
 // site with FP32 weights, 6 + 8 with BF16), else the gather form (or when a
 // link does not fit the link form).  The link form saves bytes but spends
-// instructions rebuilding the weights; measured per site update it wins from
-// about 50M sites (1.07e11 vs 1.09e11 site-updates/s at 384^3, 1.09e11 vs
-// 1.27e11 at 512^3) and loses below (9.7e10 vs 9.2e10 at 256^3).
+// instructions rebuilding the weights; measured per site update with FP32
+// weights it wins from about 50M sites (1.07e11 vs 1.09e11 site-updates/s at
+// 384^3, 1.09e11 vs 1.27e11 at 512^3) and loses below (9.7e10 vs 9.2e10 at
+// 256^3).  BF16 weights already make the gather form small (24 bytes per
+// site); there the rebuild costs more than the bytes it saves (1.34e11 vs
+// 1.25e11 on the 512^3 monolith), so BF16 lattices keep the gather form.
 constexpr long long kLinkFormSites = 3LL << 24;
 lpc_status ensure_gather(lpc_lattice* h) {
     if (h->gwin || h->lnk) return LPC_OK;
     const int Xs = gather_pitch(h->p.nx);
     const long long Ns = (long long)Xs * h->p.ny * h->p.nz;
-    if (!h->links_given && !h->rf.any() && h->nreg == 0 && h->N >= kLinkFormSites) {
+    if (!h->links_given && !h->rf.any() && h->nreg == 0 && h->N >= kLinkFormSites &&
+        h->p.weight_dtype == LPC_WEIGHTS_F32) {
         const int ny1 = h->p.ny + 1;
         const size_t lb = (size_t)3 * h->p.nz * ny1 * Xs * wbytes(h);
         const size_t bytes = (lb + 255) / 256 * 256 + (size_t)Ns * 8;
