@@ -165,9 +165,10 @@ struct SlotHdr {
 // y -> y + e_a has weight L and the hop back the weight A = alpha/6 of a
 // downhill or level Metropolis move (Eq. 1); L < 0: the hop y -> y + e_a has
 // weight A and the hop back -L.  One of the two hops of an open link is
-// always A, so these are exactly the stored weights.
-__device__ __forceinline__ float link_fwd(float L, float A) { return L > 0.f ? L : (L < 0.f ? A : 0.f); }
-__device__ __forceinline__ float link_bwd(float L, float A) { return L > 0.f ? A : (L < 0.f ? -L : 0.f); }
+// always A, so these are exactly the stored weights.  A closed link is
+// stored as +0 (never -0), so one comparison per direction decides.
+__device__ __forceinline__ float link_fwd(float L, float A) { return L < 0.f ? A : L; }
+__device__ __forceinline__ float link_bwd(float L, float A) { return L > 0.f ? A : fabsf(L); }
 
 template <typename WT, int MSD, int NC, bool RHO, bool REG, bool LNK>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
@@ -358,19 +359,23 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             // the pair has ghost images to write: it lies within G of a periodic face
             const bool images = (v.per_x && (x < G || x + 1 >= v.nx - G)) || (v.per_y && (y < G || y >= v.ny - G));
             const long long col = (long long)(y + G) * v.Xp + (x + G);
-            // link form: the +z links of the plane below (they end in this
-            // plane) and, for lane 0, the +x link of the site left of the tile
-            // (it ends in site 0), read from global memory; later planes take
-            // the +z links from the previous plane's slot
-            float lzb0 = 0.f, lzb1 = 0.f, lxe = 0.f, lxe1 = 0.f;   // lane 0: this plane's and the next
+            // link form: the weights of the +z links of the plane below (they
+            // end in this plane: in-weight along +z, out-weight along -z) and,
+            // for lane 0, the +x link of the site left of the tile (it ends in
+            // site 0), read from global memory; later planes take the +z
+            // weights from the previous plane
+            float2 zin = make_float2(0.f, 0.f), zout = make_float2(0.f, 0.f);
+            float lxe = 0.f, lxe1 = 0.f;                           // lane 0: this plane's and the next
             const WT* lnk = static_cast<const WT*>(v.lnk);
             const long long lplane = (long long)v.ny1 * v.Xs;     // one axis, one plane
             const int xe = (x == 0 ? v.nx : x) - 1;                // lane 0: the column left of the tile
             if (LNK) {
                 const int zb = h.za == 0 ? nz - 1 : h.za - 1;
                 const long long lb = (2LL * nz + zb) * lplane + (long long)(y + 1) * v.Xs + x;
-                if (site0) lzb0 = ldw<WT>(lnk + lb);
-                if (site1) lzb1 = ldw<WT>(lnk + lb + 1);
+                const float lzb0 = site0 ? ldw<WT>(lnk + lb) : 0.f;
+                const float lzb1 = site1 ? ldw<WT>(lnk + lb + 1) : 0.f;
+                zin = make_float2(link_fwd(lzb0, g.abig), link_fwd(lzb1, g.abig));
+                zout = make_float2(link_bwd(lzb0, g.abig), link_bwd(lzb1, g.abig));
                 if (lane == 0 && ok_y) {
                     lxe = ldw<WT>(lnk + (long long)h.za * lplane + (long long)(y + 1) * v.Xs + xe);
                     if (h.n > 1) lxe1 = ldw<WT>(lnk + (long long)(h.za + 1) * lplane + (long long)(y + 1) * v.Xs + xe);
@@ -419,7 +424,9 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
 
                 SiteIn q0, q1;
                 float2 sp;
-                float lwo0[6], lwo1[6];          // link form: the two sites' out-weights
+                float2 win2[6];                  // in-weights of the two sites (.x site 0, .y site 1)
+                float2 wo2[6];                   // link form: their out-weights
+                float lwo0[6], lwo1[6];
                 if constexpr (LNK) {
                     const float A = g.abig;
                     const float2 lx = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.lx) + os);
@@ -428,25 +435,34 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const float2 lz = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.lz) + os);
                     float lxm = __shfl_up_sync(0xffffffffu, lx.y, 1);   // +x link ending in site 0
                     if (lane == 0) lxm = lxe;
+                    // each link's two weights: forward (+a) and backward (-a)
+                    const float xf = link_fwd(lx.x, A), xb = link_bwd(lx.x, A);
+                    const float2 zf = make_float2(link_fwd(lz.x, A), link_fwd(lz.y, A));
+                    const float2 zb = make_float2(link_bwd(lz.x, A), link_bwd(lz.y, A));
                     // in-weights: the +a hop from y - e_a, the -a hop back over y's own link
-                    q0.win[0] = link_fwd(lxm, A);   q1.win[0] = link_fwd(lx.x, A);
-                    q0.win[1] = link_bwd(lx.x, A);  q1.win[1] = link_bwd(lx.y, A);
-                    q0.win[2] = link_fwd(lyb.x, A); q1.win[2] = link_fwd(lyb.y, A);
-                    q0.win[3] = link_bwd(ly.x, A);  q1.win[3] = link_bwd(ly.y, A);
-                    q0.win[4] = link_fwd(lzb0, A);  q1.win[4] = link_fwd(lzb1, A);
-                    q0.win[5] = link_bwd(lz.x, A);  q1.win[5] = link_bwd(lz.y, A);
+                    win2[0] = make_float2(link_fwd(lxm, A), xf);
+                    win2[1] = make_float2(xb, link_bwd(lx.y, A));
+                    win2[2] = make_float2(link_fwd(lyb.x, A), link_fwd(lyb.y, A));
+                    win2[3] = make_float2(link_bwd(ly.x, A), link_bwd(ly.y, A));
+                    win2[4] = zin;
+                    win2[5] = zb;
                     // out-weights: forward over the own link, backward over y - e_a's
-                    lwo0[0] = link_fwd(lx.x, A);  lwo1[0] = link_fwd(lx.y, A);
-                    lwo0[1] = link_bwd(lxm, A);   lwo1[1] = link_bwd(lx.x, A);
-                    lwo0[2] = link_fwd(ly.x, A);  lwo1[2] = link_fwd(ly.y, A);
-                    lwo0[3] = link_bwd(lyb.x, A); lwo1[3] = link_bwd(lyb.y, A);
-                    lwo0[4] = link_fwd(lz.x, A);  lwo1[4] = link_fwd(lz.y, A);
-                    lwo0[5] = link_bwd(lzb0, A);  lwo1[5] = link_bwd(lzb1, A);
-                    sp = make_float2(stay_weight(lwo0), stay_weight(lwo1));
-                    // for the next plane: its +z links from below; lane 0's left
-                    // links are read two planes ahead
-                    lzb0 = lz.x;
-                    lzb1 = lz.y;
+                    wo2[0] = make_float2(xf, link_fwd(lx.y, A));
+                    wo2[1] = make_float2(link_bwd(lxm, A), xb);
+                    wo2[2] = make_float2(link_fwd(ly.x, A), link_fwd(ly.y, A));
+                    wo2[3] = make_float2(link_bwd(lyb.x, A), link_bwd(lyb.y, A));
+                    wo2[4] = zf;
+                    wo2[5] = zout;
+                    sp = stay_weight2(wo2);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        lwo0[k] = wo2[k].x;
+                        lwo1[k] = wo2[k].y;
+                    }
+                    // for the next plane: the weights of its +z links from
+                    // below; lane 0's left links are read two planes ahead
+                    zin = zf;
+                    zout = zb;
                     lxe = lxe1;
                     if (lane == 0 && ok_y && q + 2 < h.n)
                         lxe1 = ldw<WT>(lnk + (long long)(z + 2) * lplane + (long long)(y + 1) * v.Xs + xe);
@@ -454,12 +470,15 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const WT* win = reinterpret_cast<const WT*>(ss);
                     sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const float2 wk = lds_w2<WT>(win + k * C + os);
-                        q0.win[k] = wk.x;
-                        q1.win[k] = wk.y;
-                    }
+                    for (int k = 0; k < 6; ++k) win2[k] = lds_w2<WT>(win + k * C + os);
                 }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    q0.win[k] = win2[k].x;
+                    q1.win[k] = win2[k].y;
+                }
+                // the populations of the sources, in pairs (.x for site 0, .y for site 1)
+                const float2 rn2[6] = {make_float2(r_l, r_c.x), make_float2(r_c.y, r_r), r_u, r_d, br, r_a};
                 q0.r[0] = r_l;   q0.r[1] = r_c.y; q0.r[2] = r_u.x; q0.r[3] = r_d.x; q0.r[4] = br.x; q0.r[5] = r_a.x;
                 q1.r[0] = r_c.x; q1.r[1] = r_r;   q1.r[2] = r_u.y; q1.r[3] = r_d.y; q1.r[4] = br.y; q1.r[5] = r_a.y;
                 q0.rc = r_c.x;
@@ -467,10 +486,12 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 float ro0, ro1;
                 float2 mo0 = make_float2(0.f, 0.f), mo1 = make_float2(0.f, 0.f);
                 float4 m_c = make_float4(0.f, 0.f, 0.f, 0.f);
-                if constexpr (RHO) {
-                    ro0 = site_rho(q0.win, q0.r, q0.rc, sp.x);
-                    ro1 = site_rho(q1.win, q1.r, q1.rc, sp.y);
-                } else {
+                {
+                    const float2 ro = pair_rho(win2, rn2, r_c, sp);
+                    ro0 = ro.x;
+                    ro1 = ro.y;
+                }
+                if constexpr (!RHO) {
                     const float2* mc = reinterpret_cast<const float2*>(sc + SL.m);
                     m_c = *reinterpret_cast<const float4*>(mc + o);
                     const float2 m_l = mc[o - 1], m_r = mc[o + 2];
@@ -486,8 +507,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     q0.m[5] = make_float2(m_a.x, m_a.y);   q1.m[5] = make_float2(m_a.z, m_a.w);
                     q0.mc = make_float2(m_c.x, m_c.y); q0.R = make_float2(Rp.x, Rp.y);
                     q1.mc = make_float2(m_c.z, m_c.w); q1.R = make_float2(Rp.z, Rp.w);
-                    site_rho_m(q0, sp.x, ro0, mo0);
-                    site_rho_m(q1, sp.y, ro1, mo1);
+                    site_m(q0, sp.x, mo0);
+                    site_m(q1, sp.y, mo1);
                 }
                 float muo0[3], muo1[3];
                 float dd0[3] = {0.f, 0.f, 0.f}, dd1[3] = {0.f, 0.f, 0.f};
@@ -514,8 +535,11 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     const float2 u_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv + SL.mu[n]) + o);
                     const float nb0[6] = {uc[o - 1], muc[n].y, u_u.x, u_d.x, bmu[n].x, u_a.x};
                     const float nb1[6] = {muc[n].x, uc[o + 2], u_u.y, u_d.y, bmu[n].y, u_a.y};
-                    muo0[n] = site_mu(q0.win, q0.r, nb0, sp.x, muc[n].x, a);
-                    muo1[n] = site_mu(q1.win, q1.r, nb1, sp.y, muc[n].y, a);
+                    const float2 nb2[6] = {make_float2(nb0[0], nb1[0]), make_float2(nb0[1], nb1[1]), u_u, u_d,
+                                           bmu[n], u_a};
+                    const float2 mo = pair_mu(win2, rn2, nb2, sp, muc[n], a);
+                    muo0[n] = mo.x;
+                    muo1[n] = mo.y;
                     if (LNK) {
                         dd0[n] = site_dmsd(lwo0, muc[n].x, q0.rc, a);
                         dd1[n] = site_dmsd(lwo1, muc[n].y, q1.rc, a);

@@ -153,6 +153,51 @@ __device__ __forceinline__ float site_rho(const float* win, const float* r, floa
     return v;
 }
 
+// The magnetisation part of site_rho_m alone (same operations in the same
+// order): kernels that update the populations of two sites at once with
+// pair_rho take the magnetisation of each site here.
+__device__ __forceinline__ void site_m(const SiteIn& q, float s, float2& m_out) {
+    float ar = __fmul_rn(s, q.mc.x);
+    float ai = __fmul_rn(s, q.mc.y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ar = __fmaf_rn(q.win[k], q.m[k].x, ar);
+        ai = __fmaf_rn(q.win[k], q.m[k].y, ai);
+    }
+    m_out.x = __fmaf_rn(q.R.x, ar, __fmul_rn(-q.R.y, ai));
+    m_out.y = __fmaf_rn(q.R.x, ai, __fmul_rn(q.R.y, ar));
+}
+
+// Two neighbouring sites at once (.x and .y) with the paired FP32
+// instructions of sm_100 and later: every element is rounded as the scalar
+// _rn instruction rounds it, so these give the bits of stay_weight, site_rho
+// and site_mu site by site, in half the instructions.
+__device__ __forceinline__ float2 stay_weight2(const float2* wout) {
+    float2 t = __fadd2_rn(wout[0], wout[1]);
+    t = __fadd2_rn(t, wout[2]);
+    t = __fadd2_rn(t, wout[3]);
+    t = __fadd2_rn(t, wout[4]);
+    t = __fadd2_rn(t, wout[5]);
+    // 1 - t: the product -1 * t is exact, so the fused form rounds once, as
+    // the subtraction does
+    return __ffma2_rn(make_float2(-1.0f, -1.0f), t, make_float2(1.0f, 1.0f));
+}
+__device__ __forceinline__ float2 pair_rho(const float2* win, const float2* r, float2 rc, float2 s) {
+    float2 v = __fmul2_rn(s, rc);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v = __ffma2_rn(win[k], r[k], v);
+    return v;
+}
+__device__ __forceinline__ float2 pair_mu(const float2* win, const float2* r, const float2* mu_nb, float2 s,
+                                          float2 mu_c, int a) {
+    float2 u = __fmul2_rn(s, mu_c);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u = __ffma2_rn(win[k], mu_nb[k], u);
+    u = __ffma2_rn(win[2 * a], r[2 * a], u);
+    u = __ffma2_rn(make_float2(-win[2 * a + 1].x, -win[2 * a + 1].y), r[2 * a + 1], u);
+    return u;
+}
+
 // First moment along axis a: mu'(y) = s mu(y) + sum_k win_k [mu_k + d_ka r_k].
 __device__ __forceinline__ float site_mu(const float* win, const float* r, const float* mu_nb,
                                          float s, float mu_c, int a) {
