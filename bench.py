@@ -464,10 +464,8 @@ def run_serving(args):
     cache = {r.rid: r.lattice() for r in reqs}
 
     class CachedEngine(GpuEngine):
-        def create(self, req):
-            inp = cache[req.rid]
-            with self.torch.cuda.stream(self.create_stream):
-                return self.L.Lattice.from_input(inp, stream=self.create_stream.cuda_stream)
+        def lattice_input(self, req):
+            return cache[req.rid]
 
     eng = CachedEngine(keep_fid=True)
     budget = int(args.serve_budget_gb * (1 << 30))

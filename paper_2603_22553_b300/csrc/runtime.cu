@@ -245,6 +245,11 @@ bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h
 // 256^3).  BF16 weights already make the gather form small (24 bytes per
 // site); there the rebuild costs more than the bytes it saves (1.34e11 vs
 // 1.25e11 on the 512^3 monolith), so BF16 lattices keep the gather form.
+// Since the kernel pairs the FP32 arithmetic of a lane's two sites, the two
+// forms are within a few per cent of each other where the rule switches:
+// 9.72e10 (gather) vs 9.83e10 (link) at 256^3, and with BF16 weights
+// 1.340e11 vs 1.326e11 on the 512^3 monolith, 1.126e11 vs 1.160e11 on the
+// 2048x256x256 slab with the x moment; the rule is kept as it is.
 constexpr long long kLinkFormSites = 3LL << 24;
 lpc_status ensure_gather(lpc_lattice* h) {
     if (h->gwin || h->lnk) return LPC_OK;

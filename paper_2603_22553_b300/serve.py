@@ -11,8 +11,8 @@ Continuous batching on one GPU:
   steps: the small ones with ``lattice_step_many`` (one persistent launch
   covers the work items of every small resident lattice), the large ones
   with ``lattice_step_n`` on their own streams (the one-step TMA kernel in
-  captured graphs), so work of requests that arrived at different times
-  overlaps on the device;
+  captured graphs), each on its own stream, so work of requests that
+  arrived at different times overlaps on the device;
 * a lattice that has done its steps has its FID read back and is destroyed,
   which frees its slot and memory for the next admission.
 
@@ -61,7 +61,16 @@ def footprint(edge, steps, weight_dtype=0, msd_axes=0):
 
 
 class GpuEngine:
-    """Creates, advances and reads lattices through the C ABI."""
+    """Creates, advances and reads lattices through the C ABI.
+
+    Every live lattice has a caller stream of its own, taken from a pool at
+    create and returned at finish.  The library orders a lattice's work after
+    its caller stream and the caller stream after that work, so lattices
+    that shared one caller stream would run one after another; with their
+    own streams, the launches of different lattices (and the creation of new
+    ones) overlap on the device.  Reusing pooled streams lets PyTorch's
+    caching allocator hand a finished lattice's memory to the next one.
+    """
 
     def __init__(self, keep_fid=True):
         import torch
@@ -69,15 +78,28 @@ class GpuEngine:
         self.L = L
         self.torch = torch
         self.keep_fid = keep_fid
-        self.create_stream = torch.cuda.Stream()
+        self._streams = []
+        self._lock = threading.Lock()
 
     def footprint(self, req):
         return footprint(req.edge, req.steps)
 
+    def lattice_input(self, req):
+        """The request's fields (``lpc_inputs.LatticeInput``)."""
+        return req.lattice()
+
     def create(self, req):
-        inp = req.lattice()
-        with self.torch.cuda.stream(self.create_stream):
-            lat = self.L.Lattice.from_input(inp, stream=self.create_stream.cuda_stream)
+        inp = self.lattice_input(req)
+        with self._lock:
+            s = self._streams.pop() if self._streams else self.torch.cuda.Stream()
+        try:
+            with self.torch.cuda.stream(s):
+                lat = self.L.Lattice.from_input(inp, stream=s.cuda_stream)
+        except Exception:
+            with self._lock:
+                self._streams.append(s)
+            raise
+        lat._serve_stream = s
         return lat
 
     def step_many(self, lats, steps):
@@ -107,6 +129,11 @@ class GpuEngine:
     def finish(self, lat):
         fid = lat.fid() if self.keep_fid else None
         lat.close()
+        s = getattr(lat, "_serve_stream", None)
+        if s is not None:
+            lat._serve_stream = None
+            with self._lock:
+                self._streams.append(s)
         return fid
 
 

@@ -110,3 +110,4 @@ def test_request_stream_recipe():
     assert steps.min() >= 1000 and steps.max() <= 20000
     gaps = np.diff([r.arrival_s for r in reqs])
     assert np.all(gaps >= 0) and abs(gaps.mean() - 0.02) < 0.003
+
