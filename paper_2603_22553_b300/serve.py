@@ -78,6 +78,7 @@ class GpuEngine:
         self.L = L
         self.torch = torch
         self.keep_fid = keep_fid
+        self.device = torch.cuda.current_device()    # preparation threads start on device 0
         self._streams = []
         self._lock = threading.Lock()
 
@@ -91,7 +92,7 @@ class GpuEngine:
     def create(self, req):
         inp = self.lattice_input(req)
         with self._lock:
-            s = self._streams.pop() if self._streams else self.torch.cuda.Stream()
+            s = self._streams.pop() if self._streams else self.torch.cuda.Stream(device=self.device)
         try:
             with self.torch.cuda.stream(s):
                 lat = self.L.Lattice.from_input(inp, stream=s.cuda_stream)
