@@ -129,13 +129,17 @@ class GpuEngine:
 
     def finish(self, lat):
         fid = lat.fid() if self.keep_fid else None
+        self.discard(lat)
+        return fid
+
+    def discard(self, lat):
+        """Destroy a lattice without reading it and return its stream to the pool."""
         lat.close()
         s = getattr(lat, "_serve_stream", None)
         if s is not None:
             lat._serve_stream = None
             with self._lock:
                 self._streams.append(s)
-        return fid
 
 
 class Server:
@@ -235,9 +239,27 @@ class Server:
                     else:
                         still.append(a)
                 active = still
-        finally:
+        except BaseException:
+            # a failed run releases what it still holds: the resident
+            # lattices and those whose creation ends after the failure
+            discard = getattr(eng, "discard", None)
             for _ in threads:
                 work.put(None)
+            for th in threads:
+                th.join()
+            if discard is not None:
+                for a in active:
+                    discard(a[1])
+                while True:
+                    try:
+                        _, lat = ready.get_nowait()
+                    except queue.Empty:
+                        break
+                    if lat is not None:
+                        discard(lat)
+            raise
+        for _ in threads:
+            work.put(None)
         return [recs[r.rid] for r in reqs]
 
 

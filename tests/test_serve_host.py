@@ -46,10 +46,13 @@ class FakeEngine:
 
     def finish(self, lat):
         assert lat.done == lat.req.steps
+        self.discard(lat)
+        return np.arange(lat.done + 1, dtype=float)
+
+    def discard(self, lat):
         lat.closed = True
         self.bytes -= self.footprint(lat.req)
         del self.live[lat.req.rid]
-        return np.arange(lat.done + 1, dtype=float)
 
 
 def _stream(n=60, seed=4, rate=2e5):
@@ -111,3 +114,26 @@ def test_request_stream_recipe():
     gaps = np.diff([r.arrival_s for r in reqs])
     assert np.all(gaps >= 0) and abs(gaps.mean() - 0.02) < 0.003
 
+
+class FailingEngine(FakeEngine):
+    """Creation of one request fails (as a device allocation might)."""
+
+    def __init__(self, bad_rid):
+        super().__init__()
+        self.bad_rid = bad_rid
+
+    def create(self, req):
+        if req.rid == self.bad_rid:
+            raise RuntimeError("creation failed")
+        return super().create(req)
+
+
+@pytest.mark.parametrize("prefetch", [1, 3])
+def test_failed_creation_releases_every_lattice(prefetch):
+    reqs = _stream(30)
+    order = sorted(reqs, key=lambda r: r.arrival_s)
+    eng = FailingEngine(order[12].rid)
+    with pytest.raises(RuntimeError, match="creation failed"):
+        Server(eng, 10 ** 12, max_active=8, quantum=50, prefetch=prefetch).run(reqs, realtime=False)
+    # resident lattices and those created after the failure were destroyed
+    assert eng.order and not eng.live and eng.bytes == 0
