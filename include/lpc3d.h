@@ -399,6 +399,24 @@ lpc_status lpc_step_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* p
                             const float* w, const float* R, const float* rho_in, const float* m_in,
                             float* rho_out, float* m_out, double* sums, void* stream);
 
+/*
+ * Failure-detection self-test (the paper has no counterpart).  Every
+ * spin-wait of the step kernels is bounded by an SM clock budget: a wait that
+ * runs out writes LPC_ERR_TIMEOUT to the lattice's status word and the kernel
+ * returns, so the context stays usable and the next query reports the error.
+ * This call runs one such bounded wait in a one-thread kernel on `stream`
+ * (cudaStream_t, NULL = default stream) and waits for it:
+ *   mode 0   a shared-memory mbarrier that never completes (no arrival);
+ *   mode 1   a device flag that nothing sets;
+ *   mode 2   an mbarrier that completes before the wait (control).
+ * budget_cycles (1 .. 4e9; 4e9 is the step kernels' bound, about 2 s) is
+ * the SM clock cycles the wait may take.  Returns LPC_ERR_TIMEOUT when the
+ * wait ran out (modes 0 and 1), LPC_OK when it ended (mode 2).  Allocates
+ * and frees 8 bytes of device memory.  Errors: LPC_ERR_INVALID (mode or
+ * budget out of range), LPC_ERR_CUDA.
+ */
+lpc_status lpc_wait_selftest(int32_t mode, int64_t budget_cycles, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lpc_last_error(void);
 

@@ -107,6 +107,7 @@ SIGNATURES = {
                                            _I64P, _DP]),
     "lpc_step_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32)] + [ctypes.c_void_p] * 8),
+    "lpc_wait_selftest": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
     "lpc_last_error": (ctypes.c_char_p, []),
     "lpc_version": (ctypes.c_char_p, []),
 }

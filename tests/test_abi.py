@@ -187,3 +187,11 @@ def test_padded_size_limit_rejected_on_host(lib):
     assert st == B.LPC_ERR_INVALID and not h.value
     assert b"2^31" in lib.lpc_last_error()
     assert N < 2 ** 31 - 1       # the interior alone would fit
+
+
+def test_wait_selftest_rejects_bad_arguments_on_host(lib):
+    assert lib.lpc_wait_selftest(3, 100, None) == B.LPC_ERR_INVALID
+    assert b"mode" in lib.lpc_last_error()
+    assert lib.lpc_wait_selftest(0, 0, None) == B.LPC_ERR_INVALID
+    assert lib.lpc_wait_selftest(1, 4_000_000_001, None) == B.LPC_ERR_INVALID
+    assert b"budget" in lib.lpc_last_error()
