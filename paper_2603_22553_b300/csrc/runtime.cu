@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lpc_internal.cuh"
 
 #define LPC_VERSION "lpc3d-b300 0.1 (sm_103a)"
@@ -114,6 +116,15 @@ struct lpc_lattice {
 };
 
 namespace {
+
+// NVTX range over one ABI call (host timeline of nsys / ncu --nvtx; a no-op
+// when no tool is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct Entry {
     // Orders the private stream after the caller's stream on entry and the
@@ -488,6 +499,7 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
 lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const double* F,
                              const double* omega, const uint8_t* solid, const double* rho0,
                              const lpc_allocator* a, void* stream, lpc_lattice** out) {
+    Range nvtx("lattice_create");
     if (out) *out = nullptr;
     lpc_options o;
     memset(&o, 0, sizeof o);
@@ -733,6 +745,7 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
 }
 
 lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
+    Range nvtx("lattice_step_n");
     if (!h) { set_error("lattice_step_n: NULL handle"); return LPC_ERR_INVALID; }
     if (n < 0) { set_error("lattice_step_n: n must be >= 0"); return LPC_ERR_INVALID; }
     if (n == 0) return LPC_OK;
@@ -765,6 +778,7 @@ lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
 }
 
 lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t count) {
+    Range nvtx("lattice_step_many");
     if (count < 0 || (count > 0 && (!hs || !n))) { set_error("lattice_step_many: bad arguments"); return LPC_ERR_INVALID; }
     if (count == 0) return LPC_OK;
     long long max_n = 0;
@@ -862,6 +876,7 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
 
 lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* kernel, int32_t* block_steps,
                             double* rate) {
+    Range nvtx("lattice_autotune");
     if (!h || trial_launches < 1) { set_error("lattice_autotune: bad arguments"); return LPC_ERR_INVALID; }
     Entry en(h);
     const size_t Np = (size_t)h->Np;
@@ -1099,6 +1114,7 @@ static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* ou
 }
 
 lpc_status lattice_density(lpc_lattice* h, float* out, int32_t out_is_device) {
+    Range nvtx("lattice_density");
     if (!h) { set_error("lattice_density: NULL handle"); return LPC_ERR_INVALID; }
     return read_field(h, h->rho[h->cur], 4, out, out_is_device, "lattice_density");
 }
@@ -1167,6 +1183,7 @@ lpc_status lattice_state_size(lpc_lattice* h, size_t* bytes) {
 }
 
 lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
+    Range nvtx("lattice_get_state");
     if (!h || !buf) { set_error("lattice_get_state: NULL argument"); return LPC_ERR_INVALID; }
     if (bytes < state_bytes(h)) { set_error("lattice_get_state: buffer too small"); return LPC_ERR_INVALID; }
     char* p = (char*)buf;
@@ -1207,6 +1224,7 @@ lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
 }
 
 lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
+    Range nvtx("lattice_set_state");
     if (!h || !buf) { set_error("lattice_set_state: NULL argument"); return LPC_ERR_INVALID; }
     if (bytes < sizeof(StateHeader)) { set_error("lattice_set_state: buffer too small"); return LPC_ERR_INVALID; }
     StateHeader hd;
@@ -1272,6 +1290,7 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
 
 lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_iter, int32_t check_every,
                                int64_t* iters, double* max_diff) {
+    Range nvtx("lattice_equilibrate");
     if (!h) { set_error("lattice_equilibrate: NULL handle"); return LPC_ERR_INVALID; }
     if (!(threshold >= 0.0) || max_iter < 0 || check_every < 1) { set_error("lattice_equilibrate: bad arguments"); return LPC_ERR_INVALID; }
     if (h->steps != 0) { set_error("lattice_equilibrate: only before the propagation phase (steps_done must be 0)"); return LPC_ERR_STATE; }
