@@ -383,17 +383,28 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
  *   rho_in / m_in    state at step n (m as (re, im) float pairs).
  *   rho_out / m_out  state at step n+1; must not alias the inputs.
  *   sums     3 doubles written with M(n+1) re, M(n+1) im, P(n+1).
- *   periodic[3]      1 = periodic, 0 = wall, per axis.
+ *   periodic[3]      1 = periodic, 0 = wall, per axis; must be the flags the
+ *            weights were packed with (weights packed for a periodic axis but
+ *            stepped as a wall lose the population that hops out of the
+ *            domain, and nothing detects it).
  *   stream   cudaStream_t (NULL = default stream); the call is asynchronous.
- * The result equals lattice_step_n by one step (same per-site arithmetic).
+ * Alignment: R, m_in, m_out and sums 8-byte aligned; w, rho_in and rho_out
+ * 4-byte aligned (LPC_ERR_INVALID otherwise, before any launch).
+ * The state equals lattice_step_n by one step bit for bit (the same per-site
+ * arithmetic); M and P are FP64 sums of FP32 per-row partials in plane order,
+ * equal to lattice_fid / lattice_population to FP32 summation order.
+ * One 256-thread block per z plane: throughput scales with nz (an nz = 1
+ * lattice runs on one SM), so the call suits callers bound by their
+ * allocation rules rather than by speed; lattice_step_n is the fast path.
  * Scratch: per-plane partial sums and a completion counter in a fixed
  * device array of this library (about 98 KB, held by every GPU that loads
  * the library until exit); hence nz <= 4096, and larger nz is rejected with
- * LPC_ERR_INVALID.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress), so make a first call before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race and
- * give wrong sums, so order them.  No MSD moments.  Errors: LPC_ERR_INVALID
- * (sizes, NULL or aliased buffers), LPC_ERR_CUDA.
+ * LPC_ERR_INVALID.  Every call looks up that array's address
+ * (cudaGetSymbolAddress, a host-side lookup); the first call on a device also
+ * loads the library's device code there, so make a first call before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race
+ * and give wrong sums, so order them.  No MSD moments.  Errors:
+ * LPC_ERR_INVALID (sizes, NULL, aliased or misaligned buffers), LPC_ERR_CUDA.
  */
 lpc_status lpc_step_noalloc(int32_t nx, int32_t ny, int32_t nz, const int32_t* periodic,
                             const float* w, const float* R, const float* rho_in, const float* m_in,

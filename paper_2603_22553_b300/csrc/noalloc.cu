@@ -15,7 +15,7 @@
 // different streams, or from different threads without ordering) race on the
 // scratch and give wrong sums; order them.  The array is held by every GPU
 // that loads this library until the process exits.
-#include <mutex>
+#include <cstdint>
 
 #include "lpc_internal.cuh"
 
@@ -109,22 +109,17 @@ k_step_noalloc(int nx, int ny, int nz, int px, int py, int pz, const float* __re
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current.
-void* scratch_address(int dev, cudaError_t* err) {
-    static void* addr[64] = {nullptr};
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    *err = cudaSuccess;
-    if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
-    if (!addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) { *err = e; return nullptr; }
-        addr[dev] = p;
-    }
-    return addr[dev];
+// Device address of the scratch array on the current device.  Looked up on
+// every call (a host-side table lookup once the module is loaded), so the
+// address stays valid after a cudaDeviceReset reloads the module; the first
+// lookup on a device loads this library's device code there.
+void* scratch_address(cudaError_t* err) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    return *err == cudaSuccess ? p : nullptr;
 }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 }  // namespace
 }  // namespace lpc
@@ -160,10 +155,15 @@ extern "C" lpc_status lpc_step_noalloc(int32_t nx, int32_t ny, int32_t nz, const
         set_error("lpc_step_noalloc: input and output buffers must differ");
         return LPC_ERR_INVALID;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "lpc_step_noalloc: cudaGetDevice");
-    void* scratch = scratch_address(dev, &e);
+    // the kernel reads R and m as (re, im) float pairs and writes FP64 sums
+    if (!aligned(R, 8) || !aligned(m_in, 8) || !aligned(m_out, 8) || !aligned(sums, 8) || !aligned(w, 4) ||
+        !aligned(rho_in, 4) || !aligned(rho_out, 4)) {
+        set_error("lpc_step_noalloc: R, m_in, m_out and sums must be 8-byte aligned, w, rho_in and rho_out "
+                  "4-byte aligned");
+        return LPC_ERR_INVALID;
+    }
+    cudaError_t e = cudaSuccess;
+    void* scratch = scratch_address(&e);
     if (!scratch) return cuda_fail(e, "lpc_step_noalloc: cudaGetSymbolAddress");
     cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st);      // the completion counter

@@ -8,6 +8,7 @@ against it: at least one pin must fail.  The real oracle is untouched.
 import os
 import subprocess
 
+import numpy as np
 import pytest
 
 import oracle
@@ -107,4 +108,55 @@ def test_each_mutation_fails_a_pin(name, tmp_path, monkeypatch):
             fn()
         except (AssertionError, ValueError, FloatingPointError):
             failed.append(pin)
+    assert failed, "no pin caught the mutation: " + name
+
+
+# Planted mistakes in the oracle's plain-Python downstream estimators: each
+# replaces one function of the oracle module (for the duration of one test)
+# and the pins of that estimator must fail.
+def _region_diffusion_next_population(d, P, dt):
+    d = np.asarray(d, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    return d / (2.0 * dt * P[1:len(d) + 1])
+
+
+def _region_diffusion_initial_population(d, P, dt):
+    d = np.asarray(d, dtype=np.float64)
+    return d / (2.0 * dt * float(np.asarray(P)[0]))
+
+
+def _region_diffusion_total_population(d, P, dt):
+    d = np.asarray(d, dtype=np.float64)
+    return d / (2.0 * dt * np.asarray(P, dtype=np.float64)[:len(d)].sum() / len(d))
+
+
+PY_MUTATIONS = {
+    "region D divides by P_r(n + 1)": ("region_diffusion", _region_diffusion_next_population),
+    "region D divides by P_r(0)": ("region_diffusion", _region_diffusion_initial_population),
+    "region D divides by the mean of P_r": ("region_diffusion", _region_diffusion_total_population),
+}
+
+PY_PINS = {
+    "region_diffusion": [pins.test_kohn_and_region_diffusion_on_a_uniform_lattice,
+                         pins.test_region_diffusion_against_dense_moments_off_equilibrium],
+}
+
+
+def test_real_downstream_estimators_pass_their_pins():
+    for fns in PY_PINS.values():
+        for fn in fns:
+            fn()
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_each_downstream_mutation_fails_a_pin(name, monkeypatch):
+    attr, mutant = PY_MUTATIONS[name]
+    monkeypatch.setattr(oracle, attr, mutant)
+    failed = []
+    for fn in PY_PINS[attr]:
+        try:
+            fn()
+        except (AssertionError, ValueError, FloatingPointError, IndexError):
+            failed.append(fn.__name__)
     assert failed, "no pin caught the mutation: " + name

@@ -601,3 +601,43 @@ def test_kohn_and_region_diffusion_on_a_uniform_lattice():
         for g in range(3):
             Dr = oracle.region_diffusion(r.Dr[g, a], r.Pr[g], dt)
             assert np.allclose(Dr, alpha / (6 * dt), rtol=1e-12)
+
+
+def test_region_diffusion_against_dense_moments_off_equilibrium():
+    """D of the particles in a region at step n (Table 1's D per region):
+    dMSD_r(n) / (2 dt P_r(n)), both taken at step n.  A non-uniform lattice
+    (solids, random F, three regions) started far from equilibrium, so that
+    P_r(n) changes from step to step: the oracle's estimator must equal the
+    one built from dense powers of the transition operator, T^n rho0 for the
+    populations and the dense first moments for the MSD increments.  Reading
+    P_r at step n + 1 or at step 0 instead fails here (on a uniform lattice
+    started uniform both readings pass)."""
+    inp = lpc_inputs.random_case((5, 4, 3), 95, periodic=(1, 1, 0), solid_frac=0.2, F_sd=1.2,
+                                 alpha=0.8)
+    pk = oracle.pack_input(inp)
+    lab = lpc_inputs.random_regions(inp.F.shape, 96, 3)
+    N = inp.F.size
+    pore = inp.solid.reshape(-1) == 0
+    lf = lab.reshape(-1)
+    rho0 = np.zeros(N)
+    for g in range(3):                              # all particles start in two sites per region
+        rho0[np.flatnonzero(pore & (lf == g))[:2]] = 5.0 + g
+    steps, dt = 30, inp.dt
+    r = oracle.run(pk, rho0.reshape(inp.F.shape), steps, msd_axes=3, region=lab, n_regions=3)
+    T = bf.transition_matrix(inp.F, inp.solid, inp.periodic, inp.alpha)
+    for axis in (0, 1):
+        Dop = bf.displacement_operator(inp.F, inp.solid, inp.periodic, inp.alpha, axis)
+        u, q = Dop.sum(axis=0), np.abs(Dop).sum(axis=0)
+        rho, mu = rho0.copy(), np.zeros(N)
+        dense = np.zeros((3, steps))
+        for n in range(steps):
+            for g in range(3):
+                sel = lf == g
+                dense[g, n] = (2 * u[sel] @ mu[sel] + q[sel] @ rho[sel]) / (2.0 * dt * rho[sel].sum())
+            mu, rho = T @ mu + Dop @ rho, T @ rho
+        for g in range(3):
+            got = oracle.region_diffusion(r.Dr[g, axis], r.Pr[g], dt)
+            assert got.shape == (steps,) and np.all(np.isfinite(dense[g]))
+            assert np.allclose(got, dense[g], rtol=1e-10, atol=1e-12 * np.max(np.abs(dense[g])))
+    # the populations of the regions do change over the run, so the reading of n matters
+    assert np.max(np.abs(np.diff(r.Pr, axis=1))) > 1e-3 * r.P[0]
