@@ -58,6 +58,7 @@ typedef enum {
 enum { LPC_WEIGHTS_F32 = 0, LPC_WEIGHTS_BF16 = 1 };
 enum { LPC_INIT_UNIFORM = 0, LPC_INIT_BOLTZMANN = 1 };
 enum { LPC_KERNEL_AUTO = 0, LPC_KERNEL_STEP1 = 1, LPC_KERNEL_TB = 2 };
+enum { LPC_STATIC_AUTO = 0, LPC_STATIC_GATHER = 1, LPC_STATIC_LINK = 2 };
 
 /*
  * Device memory hooks.  alloc returns device memory of at least `bytes`
@@ -264,6 +265,31 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
  * k (1..min(4, ghost); k = 1 is the TMA-fed one-step kernel).
  * LPC_ERR_INVALID if the combination is impossible. */
 lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_steps);
+
+/*
+ * Form of the static data (hop weights and R) read by the TMA-fed one-step
+ * kernel (the automatic schedule of large lattices, or lattice_set_schedule
+ * (LPC_KERNEL_TB, 1)).  Both forms hold the weights packed from Eq. 1 and
+ * Eq. 7 exactly, so states are bit-identical in either; they differ in the
+ * bytes a site update reads:
+ *   LPC_STATIC_GATHER  per site the six in-weights w_k(y - e_k), the stay
+ *                      weight and R (gather form);
+ *   LPC_STATIC_LINK    one signed weight per link and axis, and R (link
+ *                      form): one hop of every open link is a downhill or
+ *                      level Metropolis move of weight alpha/6 (Eq. 1), so
+ *                      one number gives both; the kernel rebuilds in-, out-
+ *                      and stay weights from it.  Needs one jump factor (no
+ *                      per-link factors), no reservoir face and no regions;
+ *   LPC_STATIC_AUTO    the default: the link form for FP32 lattices of at
+ *                      least 3 * 2^24 sites that allow it, else the gather
+ *                      form.
+ * Static data made earlier in another form is released.  When the lattice's
+ * schedule is the TMA-fed one-step kernel the chosen form is made during this
+ * call (synchronously), else on that kernel's first launch.  Errors:
+ * LPC_ERR_INVALID (NULL handle, unknown form, LPC_STATIC_LINK for a lattice
+ * that does not allow it), LPC_ERR_OOM, LPC_ERR_CUDA.
+ */
+lpc_status lattice_set_static_form(lpc_lattice* h, int32_t form);
 
 /*
  * Autotune the step schedule of this lattice (kernel and time-block depth):

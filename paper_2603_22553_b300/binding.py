@@ -16,6 +16,7 @@ LPC_OK, LPC_ERR_INVALID, LPC_ERR_OOM, LPC_ERR_CUDA, LPC_ERR_TIMEOUT, LPC_ERR_STA
 LPC_WEIGHTS_F32, LPC_WEIGHTS_BF16 = 0, 1
 LPC_INIT_UNIFORM, LPC_INIT_BOLTZMANN = 0, 1
 LPC_KERNEL_AUTO, LPC_KERNEL_STEP1, LPC_KERNEL_TB = 0, 1, 2
+LPC_STATIC_AUTO, LPC_STATIC_GATHER, LPC_STATIC_LINK = 0, 1, 2
 
 STATUS_NAMES = {0: "LPC_OK", 1: "LPC_ERR_INVALID", 2: "LPC_ERR_OOM", 3: "LPC_ERR_CUDA",
                 4: "LPC_ERR_TIMEOUT", 5: "LPC_ERR_STATE"}
@@ -82,6 +83,7 @@ SIGNATURES = {
     "lattice_step_n": (ctypes.c_int, [_H, ctypes.c_int64]),
     "lattice_step_many": (ctypes.c_int, [ctypes.POINTER(_H), _I64P, ctypes.c_int32]),
     "lattice_set_schedule": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "lattice_set_static_form": (ctypes.c_int, [_H, ctypes.c_int32]),
     "lattice_sync": (ctypes.c_int, [_H]),
     "lattice_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32), _DP]),

@@ -102,6 +102,7 @@ struct lpc_lattice {
     int ny1 = 0;
     float link_a = 0.0f;
     bool links_given = false;           // created with per-link jump factors
+    int static_pref = LPC_STATIC_AUTO;  // lattice_set_static_form
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -262,16 +263,25 @@ bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h
 // 1.340e11 vs 1.326e11 on the 512^3 monolith, 1.126e11 vs 1.160e11 on the
 // 2048x256x256 slab with the x moment; the rule is kept as it is.
 constexpr long long kLinkFormSites = 3LL << 24;
+
+// The link form holds only lattices with one jump factor, no reservoir face
+// and no regions.
+bool link_form_possible(const lpc_lattice* h) { return !h->links_given && !h->rf.any() && h->nreg == 0; }
+
 lpc_status ensure_gather(lpc_lattice* h) {
     if (h->gwin || h->lnk) return LPC_OK;
     const int Xs = gather_pitch(h->p.nx);
     const long long Ns = (long long)Xs * h->p.ny * h->p.nz;
-    if (!h->links_given && !h->rf.any() && h->nreg == 0 && h->N >= kLinkFormSites &&
-        h->p.weight_dtype == LPC_WEIGHTS_F32) {
+    const bool want_link =
+        link_form_possible(h) &&
+        (h->static_pref == LPC_STATIC_LINK ||
+         (h->static_pref == LPC_STATIC_AUTO && h->N >= kLinkFormSites && h->p.weight_dtype == LPC_WEIGHTS_F32));
+    if (want_link) {
         const int ny1 = h->p.ny + 1;
         const size_t lb = (size_t)3 * h->p.nz * ny1 * Xs * wbytes(h);
         const size_t bytes = (lb + 255) / 256 * 256 + (size_t)Ns * 8;
         char* blk = (char*)dalloc(h, bytes);
+        if (!blk && h->static_pref == LPC_STATIC_LINK) { set_error("link-form allocation failed"); return LPC_ERR_OOM; }
         if (blk) {
             h->Xs = Xs;
             h->ny1 = ny1;
@@ -298,6 +308,10 @@ lpc_status ensure_gather(lpc_lattice* h) {
             }
             dfree(h, blk, bytes);     // a link outside the form: use the gather form
             h->ny1 = 0;
+            if (h->static_pref == LPC_STATIC_LINK) {
+                set_error("a link's weights do not fit the link form (one hop of every open link weighs alpha/6)");
+                return LPC_ERR_STATE;
+            }
         }
     }
     char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
@@ -444,6 +458,21 @@ bool all_of_parallel(long long n, Pred pred) {
 
 bool finite_all(const double* a, const uint8_t* solid, long long n, bool pore_only) {
     return all_of_parallel(n, [=](long long i) { return (pore_only && solid[i]) || std::isfinite(a[i]); });
+}
+
+// Release the static data of the one-step TMA kernel (either form); the next
+// launch of that kernel makes it again.  Tensor maps and graphs that name it
+// are dropped.
+void drop_static(lpc_lattice* h) {
+    if (!h->gwin && !h->lnk) return;
+    cudaStreamSynchronize(h->wstream);
+    drop_graphs(h);
+    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
+    if (h->lnk) dfree(h, h->lnk, h->lnk_bytes);
+    h->gwin = nullptr; h->gs = nullptr; h->gR = nullptr; h->gdm = nullptr;
+    h->lnk = nullptr; h->lnk_bytes = 0; h->ny1 = 0; h->link_a = 0.0f;
+    h->Xs = 0; h->Ns = 0;
+    h->maps_K = 0;          // re-encode the tensor maps on the next launch
 }
 
 void release_all(lpc_lattice* h) {
@@ -742,6 +771,29 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
     }
     set_error("lattice_set_schedule: unknown kernel");
     return LPC_ERR_INVALID;
+}
+
+lpc_status lattice_set_static_form(lpc_lattice* h, int32_t form) {
+    if (!h) { set_error("lattice_set_static_form: NULL handle"); return LPC_ERR_INVALID; }
+    if (form != LPC_STATIC_AUTO && form != LPC_STATIC_GATHER && form != LPC_STATIC_LINK) {
+        set_error("lattice_set_static_form: form must be LPC_STATIC_AUTO, _GATHER or _LINK");
+        return LPC_ERR_INVALID;
+    }
+    if (form == LPC_STATIC_LINK && !link_form_possible(h)) {
+        set_error("lattice_set_static_form: the link form needs one jump factor, no reservoir face and no regions");
+        return LPC_ERR_INVALID;
+    }
+    cudaSetDevice(h->device);
+    Entry en(h);
+    h->static_pref = form;
+    drop_static(h);
+    // made now when the one-step TMA kernel is the lattice's schedule (so a
+    // failure is reported here), else on that kernel's first launch
+    if (h->kernel == LPC_KERNEL_TB && h->kdepth == 1) {
+        const lpc_status st = ensure_maps(h);
+        if (st != LPC_OK) return st;
+    }
+    return LPC_OK;
 }
 
 lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {

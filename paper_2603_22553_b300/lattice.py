@@ -169,6 +169,11 @@ class Lattice:
     def set_schedule(self, kernel, block_steps=1):
         B.check(self.lib.lattice_set_schedule(self.h, int(kernel), int(block_steps)), self.lib)
 
+    def set_static_form(self, form):
+        """Static data form of the TMA-fed one-step kernel: B.LPC_STATIC_AUTO,
+        _GATHER or _LINK (``lattice_set_static_form``)."""
+        B.check(self.lib.lattice_set_static_form(self.h, int(form)), self.lib)
+
     def sync(self):
         B.check(self.lib.lattice_sync(self.h), self.lib)
 

@@ -109,6 +109,7 @@ def test_null_handle_calls(lib):
     out = np.zeros(2)
     assert lib.lattice_fid(None, 0, 1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == B.LPC_ERR_INVALID
     assert lib.lattice_step_many(None, None, -1) == B.LPC_ERR_INVALID
+    assert lib.lattice_set_static_form(None, B.LPC_STATIC_LINK) == B.LPC_ERR_INVALID
 
 
 @pytest.mark.parametrize("bad", [1.5, -0.1, float("nan")])
