@@ -220,6 +220,73 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* o, const do
                              const lpc_allocator* a, void* stream, lpc_lattice** out);
 
 /*
+ * Slab of a lattice decomposed along z (the slowest axis), for running one
+ * lattice on several GPUs (or as several handles on one): the paper runs
+ * large systems as domain-decomposed processes with ghost layers exchanged
+ * between neighbours (Sec. 3.2-3.3).  A slab holds its own nz planes plus
+ * one halo plane on each side: the plane just below its first plane and the
+ * plane just above its last, copies of the neighbouring slabs' boundary
+ * planes.  Its steps read the halos and never write them; they update and
+ * sum over the own planes only, so the slabs' M, P and dMSD histories add up
+ * to the whole lattice's.
+ *   p        the slab's parameters: nx, ny as the lattice, nz = the slab's
+ *            own planes; periodic[2] is ignored (the halo planes bound the
+ *            slab), periodic[0..1] as the lattice.
+ *   halo     halo planes per side; must be 1 (one step between exchanges).
+ *   F, omega, solid, rho0   [nz + 2][ny][nx]: plane 0 is the lower halo
+ *            (the lattice's plane below the slab; the last plane when z is
+ *            periodic and this is the first slab), planes 1..nz the slab's
+ *            own, plane nz + 1 the upper halo.  At a z wall of the lattice
+ *            the halo plane there is all solid (solid = 1), so no hop crosses
+ *            it and it never needs an exchange.  The hop weights between a
+ *            halo and the own planes are packed from these fields, exactly as
+ *            in the whole lattice.
+ *   o        options as lattice_create_ex; region labels are not accepted.
+ * A slab needs rho0 with LPC_INIT_BOLTZMANN (the normalisation of Eq. 2 is
+ * over the whole lattice).  Steps: lattice_step_n advances the own planes;
+ * between two steps the caller refreshes the halos from the neighbours
+ * (lattice_slab_planes gives the device addresses; a step's results are in
+ * place once lattice_step_n returns on the caller's stream), so a slab is
+ * advanced one step at a time.  Schedules: the one-step kernels (TB with
+ * block_steps > 1 is rejected); lattice_equilibrate is rejected
+ * (LPC_ERR_STATE: its convergence check needs every slab).  Queries
+ * (densities, weights, rotation, solid mask, lattice_info.n_sites) cover the
+ * own planes; checkpoints (lattice_get_state / lattice_set_state) hold every
+ * plane, halos included.  lattice_footprint of the parameters with nz + 2
+ * planes gives the slab's device bytes.  Errors as lattice_create_ex, and
+ * LPC_ERR_INVALID for halo != 1, region labels, or LPC_INIT_BOLTZMANN without
+ * rho0.
+ */
+lpc_status lattice_create_slab(const lpc_params* p, int32_t halo, const lpc_options* o, const double* F,
+                               const double* omega, const uint8_t* solid, const double* rho0,
+                               const lpc_allocator* a, void* stream, lpc_lattice** out);
+
+/* Planes of a slab, for the halo exchange. */
+enum { LPC_PLANE_FIRST = 0, LPC_PLANE_LAST = 1, LPC_PLANE_HALO_BELOW = 2, LPC_PLANE_HALO_ABOVE = 3 };
+
+/*
+ * Device addresses of one plane of the current state of a slab.  plane[q]
+ * and bytes[q] for q = rho (FP32), m (FP32 (re, im) pairs), mu_x, mu_y,
+ * mu_z (FP32; NULL and 0 when the moment is not enabled).  A plane is the
+ * whole ghost-padded plane (pitch_y rows of pitch_x sites, lattice_info), so
+ * a copy of it carries the x / y ghost images too.  The exchange after a step
+ * copies every slab's LPC_PLANE_FIRST plane into the LPC_PLANE_HALO_ABOVE
+ * plane of the slab below it and its LPC_PLANE_LAST plane into the
+ * LPC_PLANE_HALO_BELOW plane of the slab above it (byte copies; the slabs
+ * share nx, ny, the ghost width and the moments).  The addresses change with
+ * every step (the state is double-buffered): ask again after each step.
+ * Copies issued on the lattice's caller stream after lattice_step_n are
+ * ordered after that step, and the next step after them.  Errors:
+ * LPC_ERR_INVALID (NULL arguments, a lattice that is not a slab, which
+ * outside 0..3).
+ */
+typedef struct {
+    void* plane[5];
+    int64_t bytes[5];
+} lpc_plane_set;
+lpc_status lattice_slab_planes(lpc_lattice* h, int32_t which, lpc_plane_set* out);
+
+/*
  * Device bytes lattice_create would hold for these parameters, plus the
  * history of `steps` steps and the transient input copies of create (used to
  * admit requests by HBM footprint).  No device work.  LPC_ERR_INVALID on bad
@@ -348,6 +415,16 @@ lpc_status lattice_msd_region(lpc_lattice* h, int32_t region, int32_t axis, int6
  * LPC_ERR_INVALID if the axis is not in msd_axes or the range is invalid.
  */
 lpc_status lattice_msd(lpc_lattice* h, int32_t axis, int64_t first, int64_t count, double* out);
+
+/*
+ * The per-step MSD increments dMSD_a(n) = sum_x [2 (w_+a - w_-a) mu_a +
+ * (w_+a + w_-a) rho](x, n) of Eq. 5 (summed over the lattice's sites, or a
+ * slab's own planes) for n = first .. first+count-1 (0 .. steps_done - 1):
+ * the values lattice_msd accumulates, unnormalised, so that the increments
+ * of several slabs can be added before dividing by the whole lattice's P(0).
+ * LPC_ERR_INVALID if the axis is not in msd_axes or the range is invalid.
+ */
+lpc_status lattice_dmsd(lpc_lattice* h, int32_t axis, int64_t first, int64_t count, double* out);
 
 /*
  * Current site populations rho(x, n) (the densities of Sec. 3.2 item 5),

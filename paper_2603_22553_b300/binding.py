@@ -17,6 +17,7 @@ LPC_WEIGHTS_F32, LPC_WEIGHTS_BF16 = 0, 1
 LPC_INIT_UNIFORM, LPC_INIT_BOLTZMANN = 0, 1
 LPC_KERNEL_AUTO, LPC_KERNEL_STEP1, LPC_KERNEL_TB = 0, 1, 2
 LPC_STATIC_AUTO, LPC_STATIC_GATHER, LPC_STATIC_LINK = 0, 1, 2
+LPC_PLANE_FIRST, LPC_PLANE_LAST, LPC_PLANE_HALO_BELOW, LPC_PLANE_HALO_ABOVE = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "LPC_OK", 1: "LPC_ERR_INVALID", 2: "LPC_ERR_OOM", 3: "LPC_ERR_CUDA",
                 4: "LPC_ERR_TIMEOUT", 5: "LPC_ERR_STATE"}
@@ -52,6 +53,10 @@ class lpc_options(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class lpc_plane_set(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p * 5), ("bytes", ctypes.c_int64 * 5)]
+
+
 class lpc_info(ctypes.Structure):
     _fields_ = [("n_sites", ctypes.c_int64), ("n_padded", ctypes.c_int64),
                 ("ghost", ctypes.c_int32), ("pitch_x", ctypes.c_int32),
@@ -78,6 +83,10 @@ SIGNATURES = {
     "lattice_create_ex": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.POINTER(lpc_options), _DP, _DP,
                                          _U8P, _DP, ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
                                          ctypes.POINTER(_H)]),
+    "lattice_create_slab": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.c_int32, ctypes.POINTER(lpc_options),
+                                           _DP, _DP, _U8P, _DP, ctypes.POINTER(lpc_allocator), ctypes.c_void_p,
+                                           ctypes.POINTER(_H)]),
+    "lattice_slab_planes": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(lpc_plane_set)]),
     "lattice_destroy": (ctypes.c_int, [_H]),
     "lattice_footprint": (ctypes.c_int, [ctypes.POINTER(lpc_params), ctypes.c_int64, _I64P]),
     "lattice_step_n": (ctypes.c_int, [_H, ctypes.c_int64]),
@@ -92,6 +101,7 @@ SIGNATURES = {
     "lattice_fid": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_population": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_msd": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
+    "lattice_dmsd": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_fid_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_population_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP]),
     "lattice_msd_region": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,

@@ -215,8 +215,8 @@ __device__ __forceinline__ void step1_item(const LatticeView& v, int cz, int til
     if (c.load && c.lane == 0) c.halo = -1;
     if (c.site && c.lane == BX - 1) c.halo = 1;
     c.o = (c.y + v.G) * v.Xp + (c.x + v.G);
-    const int z0 = zc * cz;
-    const int z1 = min(z0 + cz, v.nz);
+    const int z0 = v.zlo + zc * cz;
+    const int z1 = min(z0 + cz, v.zhi);
 
     Pl<MSD> P0, P1, P2, P3;
     zero_pl(P0); zero_pl(P1); zero_pl(P2); zero_pl(P3);
@@ -299,14 +299,15 @@ Step1Shape step1_shape(const LatticeView& v, int wdtype) {
     const long long xy = (long long)s.tiles_x * s.tiles_y;
     const long long want = resident * 8;
     const long long nchunks = (want + xy - 1) / xy;
-    const long long nsites = (long long)v.nx * v.ny * v.nz;
+    const int nzu = v.zhi - v.zlo;              // planes updated
+    const long long nsites = (long long)v.nx * v.ny * nzu;
     const int czmin = nsites < (1LL << 17) ? 2 : (nsites < (1LL << 21) ? 4 : 8);
-    int cz = (int)((v.nz + nchunks - 1) / nchunks);
+    int cz = (int)((nzu + nchunks - 1) / nchunks);
     if (cz > 64) cz = 64;
     if (cz < czmin) cz = czmin;
-    if (cz > v.nz) cz = v.nz;
+    if (cz > nzu) cz = nzu;
     s.cz = cz;
-    const long long nzc = (v.nz + cz - 1) / cz;
+    const long long nzc = (nzu + cz - 1) / cz;
     s.n_items = (int)(xy * nzc);
     s.grid = (int)(resident < s.n_items ? resident : s.n_items);
     return s;

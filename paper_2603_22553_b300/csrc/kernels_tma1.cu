@@ -264,8 +264,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 const int item = (int)atomicAdd(g.work, 1u);
                 if (item >= g.n_items) break;
                 const int tile = item % g.tiles;
-                const int za = (item / g.tiles) * g.cz;
-                const int n = min(g.cz, nz - za);
+                const int za = v.zlo + (item / g.tiles) * g.cz;
+                const int n = min(g.cz, v.zhi - za);
                 const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
                 const int bx = tx * kTX;                 // padded column of the state box
                 const int by = ty * TY + G - 1;          // padded row of y0 - 1
@@ -688,7 +688,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 if (lane < KS) {
                     double sum = 0.0;
                     for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * KSP + lane];
-                    const int item = (h.za / g.cz) * g.tiles + h.tile;
+                    const int item = ((h.za - v.zlo) / g.cz) * g.tiles + h.tile;
                     v.partials[(long long)item * KS + lane] = sum;
                 }
                 __syncwarp();
@@ -952,13 +952,14 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.tiles_x = (v.nx + kTX - 1) / kTX;
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
-    long long cz = (long long)g.tiles * v.nz / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
+    const int nzu = v.zhi - v.zlo;              // planes updated
+    long long cz = (long long)g.tiles * nzu / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
     if (cz < 8) cz = 8;
-    if (cz > v.nz) cz = v.nz;
-    while ((long long)g.tiles * ((v.nz + cz - 1) / cz) > t1_max_items() && cz < v.nz) cz *= 2;
-    if (cz > v.nz) cz = v.nz;
+    if (cz > nzu) cz = nzu;
+    while ((long long)g.tiles * ((nzu + cz - 1) / cz) > t1_max_items() && cz < nzu) cz *= 2;
+    if (cz > nzu) cz = nzu;
     g.cz = (int)cz;
-    g.n_items = g.tiles * ((v.nz + g.cz - 1) / g.cz);
+    g.n_items = g.tiles * ((nzu + g.cz - 1) / g.cz);
     if (g.n_items > t1_max_items()) return cudaErrorInvalidConfiguration;
     g.err = err;
     g.work = err + 7;

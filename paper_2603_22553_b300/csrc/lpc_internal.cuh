@@ -31,6 +31,11 @@ constexpr int kMaxTB = 8;            // deepest temporal block
 // Everything a step kernel needs about one lattice, passed by value.
 struct LatticeView {
     int nx, ny, nz;
+    // planes a step updates and sums over: [zlo, zhi).  A whole lattice has
+    // zlo = 0, zhi = nz; a slab of a z-decomposed lattice holds one halo plane
+    // on each side (planes 0 and nz - 1, read but never written by its
+    // steps), so zlo = 1, zhi = nz - 1 and no plane index wraps.
+    int zlo, zhi;
     int G, Xp, Yp;
     int per_x, per_y, per_z;
     int msd_axes;

@@ -103,6 +103,11 @@ struct lpc_lattice {
     float link_a = 0.0f;
     bool links_given = false;           // created with per-link jump factors
     int static_pref = LPC_STATIC_AUTO;  // lattice_set_static_form
+    // slab of a z-decomposed lattice (lattice_create_slab): planes 0 and
+    // nz - 1 are halos, [zlo, zhi) the slab's own planes; a whole lattice has
+    // zlo = 0, zhi = nz
+    bool slab = false;
+    int zlo = 0, zhi = 0;
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -175,11 +180,12 @@ size_t history_bytes(long long cap, int sets) {
 // Steps of a TB launch that this lattice may use: reservoir ghosts must keep
 // their values and region sums are taken once per step, so lattices with
 // either run one step per launch.
-bool tb_depth_allowed(const lpc_lattice* h, int K) { return K == 1 || (!h->rf.any() && h->nreg == 0); }
+bool tb_depth_allowed(const lpc_lattice* h, int K) { return K == 1 || (!h->rf.any() && h->nreg == 0 && !h->slab); }
 
 LatticeView make_view(lpc_lattice* h, int in) {
     LatticeView v;
     v.nx = h->p.nx; v.ny = h->p.ny; v.nz = h->p.nz;
+    v.zlo = h->zlo; v.zhi = h->zhi;
     v.G = h->G; v.Xp = h->Xp; v.Yp = h->Yp;
     v.per_x = h->p.periodic[0]; v.per_y = h->p.periodic[1]; v.per_z = h->p.periodic[2];
     v.msd_axes = h->p.msd_axes;
@@ -193,6 +199,29 @@ LatticeView make_view(lpc_lattice* h, int in) {
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
     v.region = h->region; v.nreg = h->nreg; v.Xr = h->Xr;
+    return v;
+}
+
+// Sites a step updates (a slab's own planes, without its halos).
+long long n_updated(const lpc_lattice* h) { return (long long)h->p.nx * h->p.ny * (h->zhi - h->zlo); }
+
+// The view of the planes [zlo, zhi) alone, as a lattice of zhi - zlo planes
+// (per-plane pointers offset, plane strides unchanged): for the reductions
+// and read-backs that walk every plane of a view.
+LatticeView updated_view(lpc_lattice* h, int in) {
+    LatticeView v = make_view(h, in);
+    const long long off = (long long)h->zlo * h->Xp * h->Yp;
+    if (off == 0) return v;
+    v.nz = h->zhi - h->zlo;
+    v.zlo = 0;
+    v.zhi = v.nz;
+    v.rho_in += off; v.m_in += off; v.rho_out += off; v.m_out += off;
+    for (int a = 0; a < 3; ++a) {
+        if (v.mu_in[a]) v.mu_in[a] += off;
+        if (v.mu_out[a]) v.mu_out[a] += off;
+    }
+    v.w = static_cast<const char*>(v.w) + off * (long long)wbytes(h);
+    v.R += off;
     return v;
 }
 
@@ -275,7 +304,7 @@ lpc_status ensure_gather(lpc_lattice* h) {
     const bool want_link =
         link_form_possible(h) &&
         (h->static_pref == LPC_STATIC_LINK ||
-         (h->static_pref == LPC_STATIC_AUTO && h->N >= kLinkFormSites && h->p.weight_dtype == LPC_WEIGHTS_F32));
+         (h->static_pref == LPC_STATIC_AUTO && n_updated(h) >= kLinkFormSites && h->p.weight_dtype == LPC_WEIGHTS_F32));
     if (want_link) {
         const int ny1 = h->p.ny + 1;
         const size_t lb = (size_t)3 * h->p.nz * ny1 * Xs * wbytes(h);
@@ -420,7 +449,7 @@ lpc_status build_graph(lpc_lattice* h, int parity) {
 // Default schedule: the TMA-fed one-step kernel for lattices large enough to
 // fill its tiles, else the register-pipelined one-step kernel.
 void auto_schedule(lpc_lattice* h) {
-    const bool big = h->p.nx >= 64 && h->p.ny >= 16 && h->N >= (1LL << 20);
+    const bool big = h->p.nx >= 64 && h->p.ny >= 16 && n_updated(h) >= (1LL << 20);
     if (big && tb_supported(make_view(h, 0), h->p.weight_dtype, 1) &&
         tb_prepare(h->p.weight_dtype, 1, h->p.msd_axes) == cudaSuccess) {
         h->kernel = LPC_KERNEL_TB;
@@ -525,9 +554,15 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
     return lattice_create_ex(p, &o, F, omega, solid, rho0, a, stream, out);
 }
 
-lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const double* F,
-                             const double* omega, const uint8_t* solid, const double* rho0,
-                             const lpc_allocator* a, void* stream, lpc_lattice** out) {
+}  // extern "C"
+
+namespace {
+
+// lattice_create_ex, and lattice_create_slab with `slab` (p->nz then counts
+// the halo planes too).
+lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double* F, const double* omega,
+                       const uint8_t* solid, const double* rho0, const lpc_allocator* a, void* stream,
+                       lpc_lattice** out, bool slab) {
     Range nvtx("lattice_create");
     if (out) *out = nullptr;
     lpc_options o;
@@ -585,6 +620,14 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
         set_error("lattice_create_ex: n_regions must be 1..4 with region labels and 0 without");
         return LPC_ERR_INVALID;
     }
+    if (slab && o.region) {
+        set_error("lattice_create_slab: slabs take no region labels");
+        return LPC_ERR_INVALID;
+    }
+    if (slab && !rho0 && p->init == LPC_INIT_BOLTZMANN) {
+        set_error("lattice_create_slab: a Boltzmann start is normalised over the whole lattice: pass rho0");
+        return LPC_ERR_INVALID;
+    }
     if (o.region) {
         const uint8_t* reg = o.region;
         const int nr = o.n_regions;
@@ -598,6 +641,9 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
     h->p = *p;
     h->N = N;
+    h->slab = slab;
+    h->zlo = slab ? 1 : 0;
+    h->zhi = slab ? p->nz - 1 : p->nz;
     h->rf = rf;
     h->links_given = alpha_links != nullptr;
     h->nreg = o.n_regions;
@@ -686,7 +732,7 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
                 e = launch_init_state(v, dR0, p->init, dF, h->solid, p->kT, h->scratch, h->wstream);
             if (e == cudaSuccess) e = launch_reservoir_ghosts(v, rf, h->wstream);
             h->cur = 0;
-            if (e == cudaSuccess) e = launch_sum_state(make_view(h, 0), h->wstream);
+            if (e == cudaSuccess) e = launch_sum_state(updated_view(h, 0), h->wstream);
             if (e == cudaSuccess)
                 e = launch_region_sums(make_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
         }
@@ -702,6 +748,51 @@ lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const 
     h->steps = 0;
     auto_schedule(h);
     *out = h;
+    return LPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const double* F,
+                             const double* omega, const uint8_t* solid, const double* rho0,
+                             const lpc_allocator* a, void* stream, lpc_lattice** out) {
+    return create_impl(p, opt, F, omega, solid, rho0, a, stream, out, false);
+}
+
+lpc_status lattice_create_slab(const lpc_params* p, int32_t halo, const lpc_options* opt, const double* F,
+                               const double* omega, const uint8_t* solid, const double* rho0,
+                               const lpc_allocator* a, void* stream, lpc_lattice** out) {
+    if (out) *out = nullptr;
+    if (!p) { set_error("lattice_create_slab: NULL argument"); return LPC_ERR_INVALID; }
+    if (halo != 1) { set_error("lattice_create_slab: halo must be 1 (one plane on each side)"); return LPC_ERR_INVALID; }
+    if (p->nz < 1 || p->nz > 2147483647 - 2) { set_error("lattice_create_slab: edges must be >= 1"); return LPC_ERR_INVALID; }
+    lpc_params q = *p;
+    q.nz = p->nz + 2;          // the halo planes below and above the slab's own planes
+    q.periodic[2] = 0;         // the halos bound the slab: no plane index wraps
+    return create_impl(&q, opt, F, omega, solid, rho0, a, stream, out, true);
+}
+
+lpc_status lattice_slab_planes(lpc_lattice* h, int32_t which, lpc_plane_set* out) {
+    if (!h || !out) { set_error("lattice_slab_planes: NULL argument"); return LPC_ERR_INVALID; }
+    if (!h->slab) { set_error("lattice_slab_planes: not a slab (lattice_create_slab)"); return LPC_ERR_INVALID; }
+    if (which < 0 || which > 3) { set_error("lattice_slab_planes: which must be 0..3"); return LPC_ERR_INVALID; }
+    const int z = which == LPC_PLANE_FIRST ? h->zlo
+                : which == LPC_PLANE_LAST ? h->zhi - 1
+                : which == LPC_PLANE_HALO_BELOW ? h->zlo - 1 : h->zhi;
+    const long long plane = (long long)h->Xp * h->Yp;
+    const long long off = (long long)z * plane;
+    memset(out, 0, sizeof *out);
+    out->plane[0] = h->rho[h->cur] + off;
+    out->bytes[0] = plane * 4;
+    out->plane[1] = h->m[h->cur] + off;
+    out->bytes[1] = plane * 8;
+    for (int a = 0; a < 3; ++a)
+        if (h->mu[h->cur][a]) {
+            out->plane[2 + a] = h->mu[h->cur][a] + off;
+            out->bytes[2 + a] = plane * 4;
+        }
     return LPC_OK;
 }
 
@@ -859,7 +950,7 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
     for (int i = 0; i < count; ++i) {
         int tx, ty, cz;
         const int items = batch_items(make_view(hs[i], hs[i]->cur), &tx, &ty, &cz);
-        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0) alone.push_back(i);
+        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0 || hs[i]->slab) alone.push_back(i);
         else batched.push_back(i);
     }
     static thread_local BatchParams bp;
@@ -975,7 +1066,7 @@ lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* ker
         if (e != cudaSuccess) { st = cuda_fail(e, "lattice_autotune: trial"); break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double r = (double)h->N * K * trial_launches / (ms * 1e-3);
+        const double r = (double)n_updated(h) * K * trial_launches / (ms * 1e-3);
         if (r > best) { best = r; best_kernel = h->kernel; best_k = K; }
         // the device step counter advanced; put it back for the next trial
         const long long s0 = steps0;
@@ -1024,7 +1115,7 @@ lpc_status lattice_steps_done(lpc_lattice* h, int64_t* n) {
 
 lpc_status lattice_info(lpc_lattice* h, lpc_info* out) {
     if (!h || !out) { set_error("lattice_info: NULL argument"); return LPC_ERR_INVALID; }
-    out->n_sites = h->N;
+    out->n_sites = n_updated(h);
     out->n_padded = h->Np;
     out->ghost = h->G;
     out->pitch_x = h->Xp;
@@ -1089,6 +1180,19 @@ lpc_status lattice_msd(lpc_lattice* h, int32_t axis, int64_t first, int64_t coun
     return LPC_OK;
 }
 
+lpc_status lattice_dmsd(lpc_lattice* h, int32_t axis, int64_t first, int64_t count, double* out) {
+    if (!h || (!out && count > 0)) { set_error("lattice_dmsd: NULL argument"); return LPC_ERR_INVALID; }
+    if (first < 0 || count < 0 || first + count > h->steps) { set_error("lattice_dmsd: range outside 0..steps_done-1"); return LPC_ERR_INVALID; }
+    if (axis < 0 || axis > 2 || !(h->p.msd_axes >> axis & 1)) { set_error("lattice_dmsd: axis not enabled"); return LPC_ERR_INVALID; }
+    if (count == 0) return LPC_OK;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->wstream);
+    if (e == cudaSuccess) { lpc_status ds = check_device_error(h); if (ds != LPC_OK) return ds; }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, h->histD + axis * h->cap + first, sizeof(double) * count, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_dmsd");
+}
+
 static lpc_status region_check(lpc_lattice* h, int32_t region, const char* who) {
     if (!h) { set_error(std::string(who) + ": NULL handle"); return LPC_ERR_INVALID; }
     if (h->nreg == 0 || region < 0 || region >= h->nreg) {
@@ -1147,21 +1251,30 @@ lpc_status lattice_msd_region(lpc_lattice* h, int32_t region, int32_t axis, int6
     return LPC_OK;
 }
 
-static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* out, int32_t out_is_device, const char* who) {
+// Interior sites of a padded field into `out` (C order): a slab's own planes
+// (all_planes = false) or every plane, halos included (checkpoints).
+static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* out, int32_t out_is_device, const char* who,
+                             bool all_planes = false) {
     if (!h || !out) { set_error(std::string(who) + ": NULL argument"); return LPC_ERR_INVALID; }
     Entry en(h);
     LatticeView v = make_view(h, h->cur);
+    size_t n = (size_t)h->N;
+    if (!all_planes && h->slab) {
+        v.nz = h->zhi - h->zlo;
+        src = static_cast<const char*>(src) + (size_t)h->zlo * h->Xp * h->Yp * elem;
+        n = (size_t)n_updated(h);
+    }
     void* dst = out;
     void* tmp = nullptr;
     if (!out_is_device) {
-        tmp = dalloc(h, (size_t)h->N * elem);
+        tmp = dalloc(h, n * elem);
         if (!tmp) { set_error(std::string(who) + ": temporary allocation failed"); return LPC_ERR_OOM; }
         dst = tmp;
     }
     cudaError_t e = launch_unpad(src, elem, v, dst, h->wstream);
-    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, (size_t)h->N * elem, cudaMemcpyDeviceToHost, h->wstream);
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, n * elem, cudaMemcpyDeviceToHost, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
-    if (tmp) dfree(h, tmp, (size_t)h->N * elem);
+    if (tmp) dfree(h, tmp, n * elem);
     return e == cudaSuccess ? LPC_OK : cuda_fail(e, who);
 }
 
@@ -1185,12 +1298,13 @@ lpc_status lattice_moment(lpc_lattice* h, int32_t axis, float* out, int32_t out_
 lpc_status lattice_weights(lpc_lattice* h, float* out) {
     if (!h || !out) { set_error("lattice_weights: NULL argument"); return LPC_ERR_INVALID; }
     Entry en(h);
-    float* tmp = (float*)dalloc(h, (size_t)h->N * 6 * 4);
+    const size_t n = (size_t)n_updated(h);
+    float* tmp = (float*)dalloc(h, n * 6 * 4);
     if (!tmp) { set_error("lattice_weights: temporary allocation failed"); return LPC_ERR_OOM; }
-    cudaError_t e = launch_weights_f32(make_view(h, h->cur), h->p.weight_dtype, tmp, h->wstream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)h->N * 24, cudaMemcpyDeviceToHost, h->wstream);
+    cudaError_t e = launch_weights_f32(updated_view(h, h->cur), h->p.weight_dtype, tmp, h->wstream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * 24, cudaMemcpyDeviceToHost, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
-    dfree(h, tmp, (size_t)h->N * 24);
+    dfree(h, tmp, n * 24);
     return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_weights");
 }
 
@@ -1203,7 +1317,8 @@ lpc_status lattice_solid(lpc_lattice* h, uint8_t* out) {
     if (!h || !out) { set_error("lattice_solid: NULL argument"); return LPC_ERR_INVALID; }
     cudaSetDevice(h->device);
     cudaError_t e = cudaStreamSynchronize(h->wstream);
-    if (e == cudaSuccess) e = cudaMemcpy(out, h->solid, (size_t)h->N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, h->solid + (size_t)h->zlo * h->p.nx * h->p.ny, (size_t)n_updated(h), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? LPC_OK : cuda_fail(e, "lattice_solid");
 }
 
@@ -1247,15 +1362,15 @@ lpc_status lattice_get_state(lpc_lattice* h, void* buf, size_t bytes) {
     memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     const size_t N = (size_t)h->N;
-    lpc_status s = read_field(h, h->rho[h->cur], 4, p, 0, "lattice_get_state");
+    lpc_status s = read_field(h, h->rho[h->cur], 4, p, 0, "lattice_get_state", true);
     if (s != LPC_OK) return s;
     p += N * 4;
-    s = read_field(h, h->m[h->cur], 8, p, 0, "lattice_get_state");
+    s = read_field(h, h->m[h->cur], 8, p, 0, "lattice_get_state", true);
     if (s != LPC_OK) return s;
     p += N * 8;
     for (int a = 0; a < 3; ++a) {
         if (!(h->p.msd_axes >> a & 1)) continue;
-        s = read_field(h, h->mu[h->cur][a], 4, p, 0, "lattice_get_state");
+        s = read_field(h, h->mu[h->cur][a], 4, p, 0, "lattice_get_state", true);
         if (s != LPC_OK) return s;
         p += N * 4;
     }
@@ -1346,6 +1461,7 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
     if (!h) { set_error("lattice_equilibrate: NULL handle"); return LPC_ERR_INVALID; }
     if (!(threshold >= 0.0) || max_iter < 0 || check_every < 1) { set_error("lattice_equilibrate: bad arguments"); return LPC_ERR_INVALID; }
     if (h->steps != 0) { set_error("lattice_equilibrate: only before the propagation phase (steps_done must be 0)"); return LPC_ERR_STATE; }
+    if (h->slab) { set_error("lattice_equilibrate: the convergence check of a slab needs the whole lattice"); return LPC_ERR_STATE; }
     Entry en(h);
     lpc_status st = ensure_history(h, (long long)check_every + 2);
     if (st != LPC_OK) return st;

@@ -58,13 +58,18 @@ class Lattice:
     def __init__(self, nx, ny, nz, F, omega, solid, *, periodic=(1, 1, 1), alpha=0.005,
                  dt=5e-6, kT=1.0, rho0=None, weight_dtype=0, msd_axes=0, init=0, ghost=0,
                  stream=None, allocator="torch", alpha_links=None, reservoirs=None, region=None,
-                 n_regions=0):
+                 n_regions=0, slab=False):
         """reservoirs: None or 6 faces (f = 2 a + side), each None (wall) or
         (F_res, rho_res, m_res complex); region: None or per-site labels
-        < n_regions for region-resolved sums."""
+        < n_regions for region-resolved sums.  slab: a slab of a lattice
+        decomposed along z (``lattice_create_slab``): nz is the slab's own
+        planes and the fields hold nz + 2 planes (a halo plane on each side);
+        queries return the own planes."""
         self.lib = B.load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
+        self.slab = bool(slab)
+        nfield = nx * ny * (nz + 2) if slab else self.N
         self.msd_axes = msd_axes
         self.weight_dtype = int(weight_dtype)
         self.dt = dt
@@ -74,21 +79,21 @@ class Lattice:
         F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
         om = np.ascontiguousarray(omega, dtype=np.float64).reshape(-1)
         sol = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
-        if F.size != self.N or om.size != self.N or sol.size != self.N:
+        if F.size != nfield or om.size != nfield or sol.size != nfield:
             raise ValueError("field sizes do not match the lattice")
         r0 = None
         if rho0 is not None:
             r0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
-            if r0.size != self.N:
+            if r0.size != nfield:
                 raise ValueError("rho0 size does not match the lattice")
         links = None
         if alpha_links is not None:
             links = np.ascontiguousarray(alpha_links, dtype=np.float64).reshape(-1)
-            if links.size != 3 * self.N:
+            if links.size != 3 * nfield:
                 raise ValueError("alpha_links must hold 3 values per site")
         opts = None
         self.n_regions = 0
-        if reservoirs is not None or region is not None:
+        if reservoirs is not None or region is not None or (slab and links is not None):
             opts = B.lpc_options()
             if links is not None:
                 opts.alpha_links = links.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -116,7 +121,12 @@ class Lattice:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = ctypes.c_void_p()
-        if opts is not None:
+        if slab:
+            st = self.lib.lattice_create_slab(ctypes.byref(p), 1, ctypes.byref(opts) if opts is not None else None,
+                                              _dp(F), _dp(om), sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                              _dp(r0) if r0 is not None else None, aptr,
+                                              ctypes.c_void_p(self.stream), ctypes.byref(h))
+        elif opts is not None:
             st = self.lib.lattice_create_ex(ctypes.byref(p), ctypes.byref(opts), _dp(F), _dp(om),
                                             sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                             _dp(r0) if r0 is not None else None, aptr,
@@ -177,6 +187,14 @@ class Lattice:
     def sync(self):
         B.check(self.lib.lattice_sync(self.h), self.lib)
 
+    def slab_planes(self, which):
+        """Device addresses and sizes of one plane of a slab's current state
+        (``lattice_slab_planes``): a list of (address, bytes) for rho, m and
+        the enabled moments, in the order rho, m, mu_x, mu_y, mu_z."""
+        ps = B.lpc_plane_set()
+        B.check(self.lib.lattice_slab_planes(self.h, int(which), ctypes.byref(ps)), self.lib)
+        return [(ps.plane[q], ps.bytes[q]) for q in range(5) if ps.plane[q]]
+
     def autotune(self, trial_launches=6):
         """Time every schedule the ghost width allows and keep the fastest
         (``lattice_autotune``; the lattice's state is restored)."""
@@ -227,6 +245,14 @@ class Lattice:
             count = self.steps_done + 1 - first
         out = np.empty(count)
         B.check(self.lib.lattice_msd(self.h, int(axis), int(first), int(count), _dp(out)), self.lib)
+        return out
+
+    def dmsd(self, axis, first=0, count=None):
+        """Per-step MSD increments dMSD_axis(n), n in [first, first+count) (unnormalised)."""
+        if count is None:
+            count = self.steps_done - first
+        out = np.empty(count)
+        B.check(self.lib.lattice_dmsd(self.h, int(axis), int(first), int(count), _dp(out)), self.lib)
         return out
 
     def fid_region(self, region, first=0, count=None):
