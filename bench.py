@@ -57,6 +57,10 @@ WORKLOADS = {
         desc="2048x256x256 film-electrode slab (monodisperse porous particles of radius 9 taking 38% of each "
              "electrode, bulk electrolyte between them), BF16 weights, MSD along x, bulk reservoirs on both x "
              "faces, FID/population/MSD per region (electrode-, bulk, electrode+)", sub=64, regions=True),
+    "supercapacitor_1024x256x128": dict(
+        make=lambda: lpc_inputs.supercapacitor(nx=1024, ny=256, nz=128, electrode=448, bulk=128),
+        desc="1024x256x128 electrode/bulk/electrode slab (the supercapacitor recipe at a quarter of its sites, "
+             "for profiling), x walls, BF16 weights, MSD along x", sub=64),
     "supercapacitor_regions_1024x256x128": dict(
         make=lambda: _with_bulk_reservoirs(lpc_inputs.supercapacitor(nx=1024, ny=256, nz=128, electrode=448,
                                                                      bulk=128)),
@@ -91,6 +95,9 @@ def parse():
     ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS) + ["serving_stream"])
     ap.add_argument("--block", type=int, default=64, help="lattice steps per bench step")
     ap.add_argument("--schedule", default="auto", help="auto | step1 | tb:K")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slabs"],
+                    help="under torchrun: an independent lattice per rank (weak scaling) or one lattice cut "
+                         "into one z slab per rank with halo exchange (strong scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -456,6 +463,107 @@ def run_ours(args):
     return 0
 
 
+def run_slabs(args):
+    """One lattice cut along z into one slab per rank (strong scaling): every
+    lattice step is a step of each slab and the halo exchange (NCCL
+    point-to-point between ranks; a single rank is its own neighbour through
+    device copies).  ``value`` = the lattice's site updates per second of the
+    slowest rank; the FID is the slabs' histories added in rank order."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300 import slabs as S
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.load()
+    wl = WORKLOADS[args.workload]
+    if wl.get("regions"):
+        raise SystemExit("slabs take no region labels")
+    inp = wl["make"]()
+    N = inp.n_sites
+    plan = S.SlabPlan(inp.nz, ws, inp.periodic[2])
+    slab = S.Slab(inp, plan, rank)
+    kern = torch.tensor([slab.lattice.info()["kernel"]], dtype=torch.int32, device="cuda")
+    if ws > 1:
+        dist.all_reduce(kern, op=dist.ReduceOp.MIN)        # every slab on one kernel
+    slab.lattice.set_schedule(*S.common_schedule([int(kern.item())]))
+    transport = S.DistTransport() if ws > 1 else S.LocalTransport()
+    mine = {rank: slab} if ws > 1 else [slab]
+
+    def lattice_steps(n):
+        for _ in range(n):
+            slab.step()
+            transport.exchange(plan, mine)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        lattice_steps(args.block)
+    torch.cuda.synchronize()
+    info = slab.lattice.info()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lattice_steps(args.block)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, ws, "cuda")
+    lattice_steps_total = args.steps * args.block
+    value = N * lattice_steps_total / (ms / 1e3)
+    kernel_name = "k_step_tma1" if info["kernel"] == B.LPC_KERNEL_TB else "k_step1"
+    n_local = info["n_sites"]
+    launches = lattice_steps_total
+    bpu = info["bytes_per_site_update"]
+    achieved = bpu * n_local / (ms / launches / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    hist = slab.history()
+    M, P, _ = S.gather_histories(hist) if ws > 1 else S.reduce_histories([hist])
+    slab.close()
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32" if inp.weight_dtype == 0 else "f32/bf16-weights", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "sites": N,
+                       "lattice_steps_per_step": args.block, "kernel": kernel_name,
+                       "static_form": STATIC_FORMS.get(info["static_form"], "none"),
+                       "parallelism": "z slabs x%d (halo exchange %s)" % (ws, "NCCL" if ws > 1 else "self copy"),
+                       "slab_planes": [z1 - z0 for z0, z1 in plan.bounds],
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_site_update": bpu, "note": "one slab (the slowest rank), exchange included"},
+            "population_drift": float(np.max(np.abs(P / P[0] - 1.0))),
+            "fid_modulus_bounded": bool(np.all(np.abs(M) <= P[0] * (1 + 1e-6))),
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_serving(args):
     """Served stream: continuous batching vs one-at-a-time plain solves.
 
@@ -488,10 +596,16 @@ def run_serving(args):
         cache[w.rid] = w.lattice()
     Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(warm)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     recs = Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(reqs)
     torch.cuda.synchronize()
+    clk_served = clocks.stop()
     s_batch = summary(recs)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     seq = serve_sequential(eng, reqs)
+    clk_seq = clocks.stop()
     s_seq = summary(seq)
     same = all(np.allclose(a.fid, b.fid, rtol=1e-5, atol=1e-5 * abs(b.fid[0])) for a, b in zip(recs, seq))
     line = {"metric": "site-updates/s (served aggregate)", "value": s_batch["aggregate_site_updates_per_s"],
@@ -502,7 +616,8 @@ def run_serving(args):
                        "quantum": args.serve_quantum, "hbm_budget_gb": args.serve_budget_gb},
             "served": s_batch, "one_at_a_time": s_seq,
             "speedup_vs_one_at_a_time": s_batch["aggregate_site_updates_per_s"] / s_seq["aggregate_site_updates_per_s"],
-            "fid_same_as_one_at_a_time_1e-5": bool(same)}
+            "fid_same_as_one_at_a_time_1e-5": bool(same),
+            "clocks": {"served": clk_served, "one_at_a_time": clk_seq}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -513,6 +628,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving_stream":
         return run_serving(args)
+    if args.decomp == "slabs":
+        return run_slabs(args)
     return run_ours(args)
 
 

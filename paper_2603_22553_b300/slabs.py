@@ -144,13 +144,21 @@ class Slab:
         args.update(kw)
         self.lattice = Lattice(inp.nx, inp.ny, z1 - z0, f["F"], f["omega"], f["solid"], rho0=f.get("rho0"),
                                alpha_links=f.get("alpha_links"), slab=True, **args)
+        self._views = {}
 
     def step(self):
         self.lattice.step(1)
 
     def planes(self, which):
-        """Byte views (torch CUDA tensors) of the state planes named by ``which``."""
-        return [device_view(a, n) for a, n in self.lattice.slab_planes(which)]
+        """Byte views (torch CUDA tensors) of the state planes named by ``which``
+        (the views of the two state buffers are made once and kept)."""
+        out = []
+        for a, n in self.lattice.slab_planes(which):
+            t = self._views.get(a)
+            if t is None:
+                t = self._views[a] = device_view(a, n)
+            out.append(t)
+        return out
 
     def history(self):
         """(M complex, P, dMSD [3][steps]) of this slab's own planes."""
@@ -164,6 +172,7 @@ class Slab:
         return M, P, d
 
     def close(self):
+        self._views = {}
         self.lattice.close()
 
 
