@@ -186,11 +186,14 @@ typedef struct {
 /*
  * Options of lattice_create_ex (zero-initialise the struct for none).
  *   alpha_links  [3][N] per-link jump factors or NULL (as lattice_create_links).
- *   reservoir[f] face f = 2 a + side of axis a (0 = x, 1 = y; side 0 is the
- *                face below coordinate 0, side 1 the face above n_a - 1).
- *                A reservoir needs periodic[a] = 0 and is available on the x
- *                and y faces only (z has no ghost layer); reservoir[4] and
- *                reservoir[5] must be disabled.
+ *   reservoir[f] face f = 2 a + side of axis a (0 = x, 1 = y, 2 = z; side 0
+ *                is the face below coordinate 0, side 1 the face above
+ *                n_a - 1).  A reservoir needs periodic[a] = 0.  x and y
+ *                reservoirs live in the ghost bands of the padded planes; a
+ *                z reservoir is a halo plane of reservoir sites below or above
+ *                the lattice (the device arrays then hold nz + 2 planes, and
+ *                the other z face, without a reservoir, gets an all-solid
+ *                halo plane: a wall); queries still return the nz planes.
  *   region       [N] uint8 site labels, each < n_regions, or NULL: region-
  *                resolved FID, population and MSD sums (the spectra and
  *                diffusion of separate parts of a system, e.g. bulk and
@@ -209,11 +212,12 @@ typedef struct {
 /*
  * lattice_create with options (o may be NULL: then it is lattice_create).
  * Lattices with a reservoir face or with regions run the one-step kernels
- * (lattice_set_schedule rejects TB with block_steps > 1 for them).  Other
- * arguments, ownership and errors as lattice_create; LPC_ERR_INVALID also
- * for a reservoir on a periodic axis or on a z face, non-finite reservoir
- * values, region labels >= n_regions, or n_regions outside 1..4 with
- * region (0 without).
+ * (lattice_set_schedule rejects TB with block_steps > 1 for them).  A z
+ * reservoir copies the fields into nz + 2 planes on the host during create
+ * (transient).  Other arguments, ownership and errors as lattice_create;
+ * LPC_ERR_INVALID also for a reservoir on a periodic axis, non-finite
+ * reservoir values, region labels >= n_regions, or n_regions outside 1..4
+ * with region (0 without).
  */
 lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* o, const double* F,
                              const double* omega, const uint8_t* solid, const double* rho0,

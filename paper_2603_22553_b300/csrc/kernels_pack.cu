@@ -190,10 +190,16 @@ __global__ void k_reservoir_ghosts(LatticeView v, ResFaces rf) {
     const int px = (int)(pidx % v.Xp);
     const long long t = pidx / v.Xp;
     const int py = (int)(t % v.Yp);
+    const int z = (int)(t / v.Yp);
     const int x = unpad_coord(px, v.G, v.nx, v.per_x);
     const int y = unpad_coord(py, v.G, v.ny, v.per_y);
     int bx, by, k;
-    const int f = reservoir_ghost(v, rf, px, py, x, y, bx, by, k);
+    int f = reservoir_ghost(v, rf, px, py, x, y, bx, by, k);
+    // a z reservoir fills its whole halo plane (ghost bands included)
+    if (rf.any_z() && v.zlo > 0) {
+        if (z == v.zlo - 1) f = rf.on[4] ? 4 : -1;
+        else if (z == v.zhi) f = rf.on[5] ? 5 : -1;
+    }
     if (f < 0) return;
     v.rho_out[pidx] = rf.rho[f];
     v.m_out[pidx] = rf.m[f];
@@ -498,11 +504,14 @@ cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, floa
 cudaError_t launch_init_state(const LatticeView& v, const double* rho0_dev, int init_mode,
                               const double* F, const uint8_t* solid, double kT, double* scratch,
                               cudaStream_t st) {
-    const long long N = (long long)v.nx * v.ny * v.nz;
+    // the normalisation of Eq. 2 runs over the own planes [zlo, zhi) (halo
+    // planes of z reservoirs hold reservoir sites)
+    const long long plane = (long long)v.nx * v.ny;
+    const long long N = plane * (v.zhi - v.zlo);
     const double* zsum = nullptr;
     if (!rho0_dev && init_mode == LPC_INIT_BOLTZMANN) {
         const int nb = 256;
-        k_boltz_partial<<<nb, 256, 0, st>>>(F, solid, N, kT, scratch);
+        k_boltz_partial<<<nb, 256, 0, st>>>(F + v.zlo * plane, solid + v.zlo * plane, N, kT, scratch);
         k_boltz_final<<<1, 32, 0, st>>>(scratch, nb);
         zsum = scratch + 2 * nb;
     }

@@ -76,14 +76,18 @@ struct LatticeView {
     int Xr;
 };
 
-// Reservoir faces f = 2 a + side (a = x, y; side 0 below coordinate 0, side 1
-// above n_a - 1): the ghost sites just outside a face hold fixed values.
+// Reservoir faces f = 2 a + side (side 0 below coordinate 0, side 1 above
+// n_a - 1): the ghost sites just outside a face hold fixed values.  x and y
+// faces use the ghost bands of the padded planes; z faces use a halo plane
+// below or above the lattice's own planes (a lattice with a z reservoir holds
+// nz + 2 planes, with zlo = 1, and its steps never write the halos).
 struct ResFaces {
-    int on[4];
-    double F[4];
-    float rho[4];
-    float2 m[4];
-    __host__ __device__ bool any() const { return on[0] || on[1] || on[2] || on[3]; }
+    int on[6];
+    double F[6];
+    float rho[6];
+    float2 m[6];
+    __host__ __device__ bool any() const { return on[0] || on[1] || on[2] || on[3] || on[4] || on[5]; }
+    __host__ __device__ bool any_z() const { return on[4] || on[5]; }
 };
 
 // Deterministic sum helpers --------------------------------------------------

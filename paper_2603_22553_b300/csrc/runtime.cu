@@ -222,6 +222,7 @@ LatticeView updated_view(lpc_lattice* h, int in) {
     }
     v.w = static_cast<const char*>(v.w) + off * (long long)wbytes(h);
     v.R += off;
+    if (v.region) v.region += (long long)h->zlo * h->p.ny * h->Xr;
     return v;
 }
 
@@ -400,7 +401,7 @@ lpc_status launch_one(lpc_lattice* h, cudaStream_t st, bool tb = false) {
     // region sums: taken by the one-step TMA kernel itself where it can,
     // else by the separate pass over the new state
     if (h->nreg > 0 && !(tb && h->kdepth == 1 && t1_fused_regions(make_view(h, h->cur), h->p.weight_dtype))) {
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, st);
+        e = launch_region_sums(updated_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "region sums launch");
     }
     return LPC_OK;
@@ -558,11 +559,19 @@ lpc_status lattice_create_links(const lpc_params* p, const double* F, const doub
 
 namespace {
 
-// lattice_create_ex, and lattice_create_slab with `slab` (p->nz then counts
-// the halo planes too).
+enum CreateMode { kWhole = 0, kSlab = 1, kZHalos = 2 };
+
+lpc_status create_with_z_halos(const lpc_params* p, const lpc_options& o, const double* F, const double* omega,
+                               const uint8_t* solid, const double* rho0, const lpc_allocator* a, void* stream,
+                               lpc_lattice** out);
+
+// lattice_create_ex (kWhole), lattice_create_slab (kSlab: p->nz counts the
+// two halo planes too), and a whole lattice with a reservoir on a z face
+// (kZHalos: the reservoir sites are a halo plane, p->nz counts both halos).
 lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double* F, const double* omega,
                        const uint8_t* solid, const double* rho0, const lpc_allocator* a, void* stream,
-                       lpc_lattice** out, bool slab) {
+                       lpc_lattice** out, int mode) {
+    const bool slab = mode == kSlab;
     Range nvtx("lattice_create");
     if (out) *out = nullptr;
     lpc_options o;
@@ -605,7 +614,7 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
         const lpc_reservoir& r = o.reservoir[f];
         if (!r.enabled) continue;
         if (r.enabled != 1 || r.reserved != 0) { set_error("lattice_create_ex: reservoir.enabled must be 0 or 1 and reserved 0"); return LPC_ERR_INVALID; }
-        if (f >= 4) { set_error("lattice_create_ex: reservoirs are available on x and y faces only"); return LPC_ERR_INVALID; }
+        if (f >= 4 && slab) { set_error("lattice_create_slab: a slab's z faces are its halo planes, not reservoirs"); return LPC_ERR_INVALID; }
         if (p->periodic[f >> 1]) { set_error("lattice_create_ex: a reservoir needs a non-periodic axis"); return LPC_ERR_INVALID; }
         if (!std::isfinite(r.F) || !std::isfinite(r.rho) || !std::isfinite(r.m_re) || !std::isfinite(r.m_im)) {
             set_error("lattice_create_ex: non-finite reservoir values");
@@ -636,14 +645,15 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
             return LPC_ERR_INVALID;
         }
     }
+    if (mode == kWhole && rf.any_z()) return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
     h->p = *p;
     h->N = N;
     h->slab = slab;
-    h->zlo = slab ? 1 : 0;
-    h->zhi = slab ? p->nz - 1 : p->nz;
+    h->zlo = mode == kWhole ? 0 : 1;
+    h->zhi = mode == kWhole ? p->nz : p->nz - 1;
     h->rf = rf;
     h->links_given = alpha_links != nullptr;
     h->nreg = o.n_regions;
@@ -734,7 +744,7 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
             h->cur = 0;
             if (e == cudaSuccess) e = launch_sum_state(updated_view(h, 0), h->wstream);
             if (e == cudaSuccess)
-                e = launch_region_sums(make_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
+                e = launch_region_sums(updated_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     }
@@ -751,6 +761,60 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
     return LPC_OK;
 }
 
+// A whole lattice with a reservoir on a z face: the reservoir sites are a
+// halo plane below (face 4) or above (face 5) the own planes, with free
+// energy F_res and no solid; the hop weights between it and the boundary
+// plane are then packed by the same Metropolis rule as every other link,
+// which is the reservoir rule (reservoir links take the scalar alpha), and
+// its state is set to the reservoir's values after the start state.  A z
+// face without a reservoir gets an all-solid halo plane (a wall).  The
+// fields are extended on the host (transient copies); the caller's arrays
+// hold the nz own planes.
+lpc_status create_with_z_halos(const lpc_params* p, const lpc_options& o, const double* F, const double* omega,
+                               const uint8_t* solid, const double* rho0, const lpc_allocator* a, void* stream,
+                               lpc_lattice** out) {
+    const size_t plane = (size_t)p->nx * p->ny, N = plane * p->nz, N2 = plane * ((size_t)p->nz + 2);
+    std::vector<double> F2, O2, R2, A2;
+    std::vector<uint8_t> S2, L2;
+    try {
+        F2.assign(N2, 0.0);
+        O2.assign(N2, 0.0);
+        S2.assign(N2, 0);
+        if (rho0) R2.assign(N2, 0.0);
+        if (o.alpha_links) A2.assign(3 * N2, p->alpha);
+        if (o.region) L2.assign(N2, 0);
+    } catch (const std::bad_alloc&) {
+        set_error("lattice_create_ex: host allocation failed (z reservoir planes)");
+        return LPC_ERR_OOM;
+    }
+    memcpy(F2.data() + plane, F, N * 8);
+    memcpy(O2.data() + plane, omega, N * 8);
+    memcpy(S2.data() + plane, solid, N);
+    if (rho0) memcpy(R2.data() + plane, rho0, N * 8);
+    for (int ax = 0; ax < 3 && o.alpha_links; ++ax) memcpy(A2.data() + ax * N2 + plane, o.alpha_links + ax * N, N * 8);
+    // the +z links of the last own plane end in the upper halo: a reservoir
+    // link takes the scalar alpha (the caller's value there is unused)
+    if (o.alpha_links)
+        for (size_t i = 0; i < plane; ++i) A2[2 * N2 + plane * (size_t)p->nz + i] = p->alpha;
+    if (o.region) memcpy(L2.data() + plane, o.region, N);
+    for (int side = 0; side < 2; ++side) {
+        const lpc_reservoir& r = o.reservoir[4 + side];
+        const size_t z0 = side ? plane * ((size_t)p->nz + 1) : 0;
+        for (size_t i = 0; i < plane; ++i) {
+            F2[z0 + i] = r.enabled ? r.F : 0.0;
+            S2[z0 + i] = r.enabled ? 0 : 1;
+            if (rho0) R2[z0 + i] = r.enabled ? r.rho : 0.0;
+        }
+    }
+    lpc_params q = *p;
+    q.nz = p->nz + 2;
+    lpc_options o2 = o;
+    o2.alpha_links = o.alpha_links ? A2.data() : nullptr;
+    o2.region = o.region ? L2.data() : nullptr;
+    return create_impl(&q, &o2, F2.data(), O2.data(), S2.data(), rho0 ? R2.data() : nullptr, a, stream, out,
+                       kZHalos);
+}
+
 }  // namespace
 
 extern "C" {
@@ -758,7 +822,7 @@ extern "C" {
 lpc_status lattice_create_ex(const lpc_params* p, const lpc_options* opt, const double* F,
                              const double* omega, const uint8_t* solid, const double* rho0,
                              const lpc_allocator* a, void* stream, lpc_lattice** out) {
-    return create_impl(p, opt, F, omega, solid, rho0, a, stream, out, false);
+    return create_impl(p, opt, F, omega, solid, rho0, a, stream, out, kWhole);
 }
 
 lpc_status lattice_create_slab(const lpc_params* p, int32_t halo, const lpc_options* opt, const double* F,
@@ -771,7 +835,7 @@ lpc_status lattice_create_slab(const lpc_params* p, int32_t halo, const lpc_opti
     lpc_params q = *p;
     q.nz = p->nz + 2;          // the halo planes below and above the slab's own planes
     q.periodic[2] = 0;         // the halos bound the slab: no plane index wraps
-    return create_impl(&q, opt, F, omega, solid, rho0, a, stream, out, true);
+    return create_impl(&q, opt, F, omega, solid, rho0, a, stream, out, kSlab);
 }
 
 lpc_status lattice_slab_planes(lpc_lattice* h, int32_t which, lpc_plane_set* out) {
@@ -950,7 +1014,7 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
     for (int i = 0; i < count; ++i) {
         int tx, ty, cz;
         const int items = batch_items(make_view(hs[i], hs[i]->cur), &tx, &ty, &cz);
-        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0 || hs[i]->slab) alone.push_back(i);
+        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0 || hs[i]->zlo > 0) alone.push_back(i);
         else batched.push_back(i);
     }
     static thread_local BatchParams bp;
@@ -1259,7 +1323,7 @@ static lpc_status read_field(lpc_lattice* h, const void* src, int elem, void* ou
     Entry en(h);
     LatticeView v = make_view(h, h->cur);
     size_t n = (size_t)h->N;
-    if (!all_planes && h->slab) {
+    if (!all_planes && h->zlo > 0) {
         v.nz = h->zhi - h->zlo;
         src = static_cast<const char*>(src) + (size_t)h->zlo * h->Xp * h->Yp * elem;
         n = (size_t)n_updated(h);
@@ -1447,7 +1511,7 @@ lpc_status lattice_set_state(lpc_lattice* h, const void* buf, size_t bytes) {
     // the region pass takes dMSD_r of the current state ahead of its step (the
     // blob holds steps entries): recompute entry `steps` of dMSD_r only
     if (e == cudaSuccess)
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, true, h->wstream);
+        e = launch_region_sums(updated_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, true, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     dfree(h, tmp, N * 8);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_set_state");
@@ -1509,9 +1573,9 @@ lpc_status lattice_equilibrate(lpc_lattice* h, double threshold, int64_t max_ite
     e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
     if (e == cudaSuccess) e = launch_restart(make_view(h, h->cur), h->wstream);
     if (e == cudaSuccess) e = launch_reservoir_ghosts(make_view(h, h->cur), h->rf, h->wstream);
-    if (e == cudaSuccess) e = launch_sum_state(make_view(h, h->cur), h->wstream);
+    if (e == cudaSuccess) e = launch_sum_state(updated_view(h, h->cur), h->wstream);
     if (e == cudaSuccess)
-        e = launch_region_sums(make_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
+        e = launch_region_sums(updated_view(h, h->cur), h->p.weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "lattice_equilibrate");
     {

@@ -140,7 +140,7 @@ def _create_ex(lib, p, opts):
 
 @pytest.mark.parametrize("face,periodic,vals,msg", [
     (0, (1, 1, 1), (0.0, 1.0, 1.0), "non-periodic"),       # reservoir on a periodic axis
-    (4, (0, 0, 0), (0.0, 1.0, 1.0), "x and y faces"),      # z faces have no ghost layer
+    (4, (0, 0, 1), (0.0, 1.0, 1.0), "non-periodic"),       # a z reservoir on a periodic z
     (2, (1, 0, 1), (float("nan"), 1.0, 1.0), "non-finite"),
     (3, (1, 0, 1), (0.0, float("inf"), 1.0), "non-finite"),
 ])

@@ -363,3 +363,89 @@ def test_equilibration_then_region_sums(sched):
         assert H.rel_l2(lat.fid_region(r), o.Mr[r]) <= 1e-5
         assert H.rel_l2(lat.population_region(r), o.Pr[r]) <= 1e-5
     lat.close()
+
+
+# Reservoirs on z faces: the paper's supercapacitor is non-periodic in z
+# (Sec. 4).  The library keeps a z reservoir as a halo plane below or above
+# the own planes; results must equal the oracle's reservoir rule.
+RES_Z = (None, None, None, None, (-0.25, 1.5, 0.75 + 0.5j), (0.75, 0.5, 0.25 - 0.5j))
+
+
+@pytest.mark.parametrize("sched", ["auto", "step1", "tb1", "batch"])
+@pytest.mark.parametrize("faces", ["z", "z_low_only", "xz"])
+def test_z_face_reservoir_parity(sched, faces):
+    from paper_2603_22553_b300.lattice import Lattice
+    shape = (24, 30, 100)
+    per = {"z": (1, 1, 0), "z_low_only": (1, 0, 0), "xz": (0, 1, 0)}[faces]
+    inp = lpc_inputs.random_case(shape, 321, periodic=per, alpha=0.8, msd_axes=7)
+    res = list(RES_Z)
+    if faces == "z_low_only":
+        res[5] = None
+    if faces == "xz":
+        res[0], res[1] = RES[0], RES[1]
+    inp.reservoirs = tuple(res)
+    lat = _lattice(inp, sched)
+    info = lat.info()
+    assert info["n_sites"] == inp.n_sites
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    w = lat.weights().reshape(6, -1).T.astype(np.float64)
+    assert np.array_equal(w == 0, pk.w == 0), "link geometry differs"
+    assert _ulp_diff(w, pk.w, 24).max() <= 1.0
+    assert np.array_equal(lat.solid_mask(), inp.solid)
+    steps = 150
+    _advance(lat, sched, steps)
+    g = _read(lat, 7)
+    mus = [lat.moment(a).astype(np.float64) for a in range(3)]
+    o = oracle.run(pk, inp.uniform_rho0(), steps, msd_axes=7)
+    _compare_fid_pop(g, o, 1e-5)
+    for a in range(3):
+        sl = slice(10, None)
+        assert np.max(np.abs(g["msd%d" % a][sl] - o.msd(a)[sl]) / np.abs(o.msd(a)[sl])) <= 1e-5
+        assert H.rel_l2(mus[a], o.mu[a]) <= 1e-4
+    assert abs(g["P"][-1] / g["P"][0] - 1.0) > 1e-3      # population flows through the z faces
+    # a checkpoint taken now resumes bit for bit
+    blob = lat.get_state()
+    lat.step(7)
+    ref = lat.density()
+    lat.set_state(blob)
+    lat.step(7)
+    assert np.array_equal(lat.density(), ref)
+    lat.close()
+
+
+def test_z_face_reservoirs_grand_canonical_equilibrium():
+    """Reservoirs at one (F_res, rho_res) on both z faces: rho_res
+    exp(-(F - F_res)) is the fixed point, reached by the equilibration phase."""
+    shape = (32, 8, 16)
+    inp = lpc_inputs.random_case(shape, 322, periodic=(1, 1, 0), solid_frac=0.0, F_sd=0.7, alpha=1.0,
+                                 msd_axes=0)
+    F_res, rho_res = -0.5, 1.5
+    inp.reservoirs = (None, None, None, None, (F_res, rho_res, 0.0), (F_res, rho_res, 0.0))
+    lat = _lattice(inp, "auto")
+    it, diff = lat.equilibrate(0.0, 40000, check_every=2000)
+    assert it == 40000 and diff < 1e-5
+    rho_eq = rho_res * np.exp(-(inp.F - F_res))
+    assert H.rel_l2(lat.density().astype(np.float64), rho_eq) <= 1e-4
+    lat.close()
+
+
+def test_z_face_reservoir_with_regions_and_boltzmann_start():
+    """Region sums over the own planes only (the reservoir planes belong to
+    no region), and a Boltzmann start normalised over the own planes."""
+    from paper_2603_22553_b300.lattice import Lattice
+    shape = (16, 20, 70)
+    inp = lpc_inputs.random_case(shape, 323, periodic=(1, 1, 0), alpha=0.9, msd_axes=4)
+    inp.reservoirs = RES_Z
+    lab = lpc_inputs.random_regions(shape, 324, 3)
+    lat = Lattice.from_input(inp, region=lab, n_regions=3, init=1)
+    rho_b = oracle.boltzmann(inp.F, inp.solid)
+    assert H.rel_l2(lat.density().astype(np.float64), rho_b) <= 1e-6
+    steps = 60
+    lat.step(steps)
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    o = oracle.run(pk, rho_b, steps, msd_axes=4, region=lab, n_regions=3)
+    assert H.rel_l2(lat.fid(), o.M) <= 1e-5
+    for r in range(3):
+        assert H.rel_l2(lat.fid_region(r), o.Mr[r]) <= 1e-5
+        assert H.rel_l2(lat.population_region(r), o.Pr[r]) <= 1e-5
+    lat.close()
