@@ -119,6 +119,8 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the lattice */
     int64_t bytes_per_site_update; /* algorithmic HBM bytes of one site update (state
                                       read + write, hop weights, R, moments, region label) */
+    int32_t tile_rows;        /* TMA-fed one-step kernel: rows of a 64-site-wide tile */
+    int32_t items_per_cta;    /* TMA-fed one-step kernel: work items per CTA (sets the z chunk) */
 } lpc_info;
 
 /*
@@ -363,14 +365,27 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
 lpc_status lattice_set_static_form(lpc_lattice* h, int32_t form);
 
 /*
- * Autotune the step schedule of this lattice (kernel and time-block depth):
- * times `trial_launches` launches
- * of every schedule its ghost width allows (one-step kernel; TB with depth
- * 1..min(4, ghost)) with CUDA events, keeps the fastest and restores the
- * lattice's state, step counter and history afterwards (results are as if
- * no trial had run).  kernel / block_steps / rate (nullable) receive the
- * choice and its site updates per second.  Errors: LPC_ERR_INVALID,
- * LPC_ERR_OOM (state snapshot), LPC_ERR_CUDA.
+ * Tiling of the TMA-fed one-step kernel: tile_rows (8, 12 or 16: a tile is
+ * 64 x tile_rows sites, one consumer warp per row) and items_per_cta (work
+ * items per CTA of the persistent grid, which sets the z-chunk length of an
+ * item: chunks of at least 8 planes).  0 keeps the heuristic (the tallest
+ * tile whose shared-memory rings keep 3 planes in flight; 40 items per CTA).
+ * A tile height whose rings do not fit falls back to the heuristic
+ * (lattice_info reports the one used).  States do not depend on the tiling;
+ * sums agree to FP32 summation order.  Errors: LPC_ERR_INVALID.
+ */
+lpc_status lattice_set_tiling(lpc_lattice* h, int32_t tile_rows, int32_t items_per_cta);
+
+/*
+ * Autotune the step schedule of this lattice: times `trial_launches`
+ * launches of every candidate with CUDA events (the register-pipelined
+ * one-step kernel; the TMA-fed one-step kernel at tile rows 16, 12, 8 and
+ * 20, 40, 80 work items per CTA; TB with depth 2..min(4, ghost)), keeps the
+ * fastest and restores the lattice's state, step counter and history
+ * afterwards (results are as if no trial had run).  kernel / block_steps /
+ * rate (nullable) receive the choice and its site updates per second; the
+ * tiling is in lattice_info.  Errors: LPC_ERR_INVALID, LPC_ERR_OOM (state
+ * snapshot), LPC_ERR_CUDA.
  */
 lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* kernel,
                             int32_t* block_steps, double* rate);

@@ -1,11 +1,13 @@
 """Schedule autotuning with a persistent JSON cache.
 
-``choose(lattice)`` returns the fastest step schedule (one-step kernel, or the
-temporally blocked kernel with depth K) for the lattice's shape, boundary,
+``choose(lattice)`` returns the fastest step schedule (the register-pipelined
+one-step kernel; the TMA-fed one-step kernel with its tile rows and work
+items per CTA; or the temporally blocked kernel with depth K) for the
+lattice's shape, boundary,
 weight type, MSD mask, ghost width and GPU.  A cache miss runs
 ``lattice_autotune`` (which times every candidate on the lattice itself and
 restores its state); a hit applies the cached choice with
-``lattice_set_schedule``.  The cache file is ``$LPC3D_AUTOTUNE_CACHE`` or
+``lattice_set_schedule`` and ``lattice_set_tiling``.  The cache file is ``$LPC3D_AUTOTUNE_CACHE`` or
 ``~/.cache/lpc3d_autotune.json``.
 """
 from __future__ import annotations
@@ -54,8 +56,11 @@ def choose(lat, trial_launches=6, path=None, refresh=False):
     if not refresh and k in table:
         c = table[k]
         lat.set_schedule(c["kernel"], c["block_steps"])
+        lat.set_tiling(c.get("tile_rows", 0), c.get("items_per_cta", 0))
         return dict(c, cached=True)
     c = lat.autotune(trial_launches)
+    info = lat.info()
+    c.update(tile_rows=info["tile_rows"], items_per_cta=info["items_per_cta"])
     with _LOCK:
         table = _load(path)
         table[k] = c

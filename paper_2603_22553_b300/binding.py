@@ -62,7 +62,8 @@ class lpc_info(ctypes.Structure):
                 ("ghost", ctypes.c_int32), ("pitch_x", ctypes.c_int32),
                 ("pitch_y", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("block_steps", ctypes.c_int32), ("static_form", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64), ("bytes_per_site_update", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("bytes_per_site_update", ctypes.c_int64),
+                ("tile_rows", ctypes.c_int32), ("items_per_cta", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -93,6 +94,7 @@ SIGNATURES = {
     "lattice_step_many": (ctypes.c_int, [ctypes.POINTER(_H), _I64P, ctypes.c_int32]),
     "lattice_set_schedule": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
     "lattice_set_static_form": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "lattice_set_tiling": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
     "lattice_sync": (ctypes.c_int, [_H]),
     "lattice_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32), _DP]),

@@ -787,7 +787,12 @@ T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool
     const int ndm = (!lnk && v.gdm) ? nmsd : 0;  // pairs staged where the lattice keeps them
     T1Choice c{};
     c.W = t1_box_width(v.G);
-    for (int i = 0; i < 3; ++i) {
+    bool chosen = false;
+    if (v.t1_ty == 8 || v.t1_ty == 12 || v.t1_ty == 16) {       // set by the caller or the autotuner
+        t1_rings(c, v.t1_ty, nmsd, wb, false, false, ndm, lnk);
+        chosen = c.depth >= 1;
+    }
+    for (int i = 0; i < 3 && !chosen; ++i) {
         t1_rings(c, kShapes[i], nmsd, wb, false, false, ndm, lnk);
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
@@ -853,6 +858,10 @@ bool t1_fused_regions(const LatticeView& v, int wdtype) {
     const long long rings = (long long)c.S1 * c.L.bytes1 + (long long)c.S2 * c.L.bytes2;
     return c.depth >= 1 && scratch <= rings && v.Xr == v.Xs;
 }
+
+int t1_tile_rows(const LatticeView& v, int wdtype) { return t1_choose(v, wdtype).TY; }
+
+int t1_default_items_per_cta() { return LPC_T1_ITEMS_PER_CTA; }
 
 bool t1_supported(const LatticeView& v, int wdtype) {
     const T1Choice c = t1_choose(v, wdtype);
@@ -953,7 +962,8 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
     const int sms = device_props().sm_count;
     const int nzu = v.zhi - v.zlo;              // planes updated
-    long long cz = (long long)g.tiles * nzu / ((long long)LPC_T1_ITEMS_PER_CTA * sms);
+    const long long ipc = v.t1_ipc > 0 ? v.t1_ipc : LPC_T1_ITEMS_PER_CTA;
+    long long cz = (long long)g.tiles * nzu / (ipc * sms);
     if (cz < 8) cz = 8;
     if (cz > nzu) cz = nzu;
     while ((long long)g.tiles * ((nzu + cz - 1) / cz) > t1_max_items() && cz < nzu) cz *= 2;

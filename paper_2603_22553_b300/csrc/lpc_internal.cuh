@@ -74,6 +74,9 @@ struct LatticeView {
     const uint8_t* region;
     int nreg;
     int Xr;
+    // tiling of the TMA-fed one-step kernel (0 = its heuristic): tile rows
+    // (8, 12 or 16) and work items per CTA, which sets the z-chunk length
+    int t1_ty, t1_ipc;
 };
 
 // Reservoir faces f = 2 a + side (side 0 below coordinate 0, side 1 above
@@ -522,6 +525,11 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
 bool t1_fused_regions(const LatticeView& v, int wdtype);
 cudaError_t t1_prepare(int wdtype, int msd);
 bool t1_supported(const LatticeView& v, int wdtype);
+// Tile rows the TMA-fed one-step kernel uses for this lattice (the caller's
+// choice in v.t1_ty if its rings fit, else the heuristic's), and the default
+// work items per CTA.
+int t1_tile_rows(const LatticeView& v, int wdtype);
+int t1_default_items_per_cta();
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
 int gather_pitch(int nx);
 cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,

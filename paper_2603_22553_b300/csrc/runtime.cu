@@ -108,6 +108,8 @@ struct lpc_lattice {
     // zlo = 0, zhi = nz
     bool slab = false;
     int zlo = 0, zhi = 0;
+    // tiling of the TMA-fed one-step kernel (lattice_set_tiling, autotuner): 0 = heuristic
+    int t1_ty = 0, t1_ipc = 0;
 
     // captured step sequences: [parity] -> graph of graph_len steps
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -199,6 +201,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
     v.region = h->region; v.nreg = h->nreg; v.Xr = h->Xr;
+    v.t1_ty = h->t1_ty; v.t1_ipc = h->t1_ipc;
     return v;
 }
 
@@ -951,6 +954,25 @@ lpc_status lattice_set_static_form(lpc_lattice* h, int32_t form) {
     return LPC_OK;
 }
 
+lpc_status lattice_set_tiling(lpc_lattice* h, int32_t tile_rows, int32_t items_per_cta) {
+    if (!h) { set_error("lattice_set_tiling: NULL handle"); return LPC_ERR_INVALID; }
+    if (tile_rows != 0 && tile_rows != 8 && tile_rows != 12 && tile_rows != 16) {
+        set_error("lattice_set_tiling: tile_rows must be 0 (heuristic), 8, 12 or 16");
+        return LPC_ERR_INVALID;
+    }
+    if (items_per_cta != 0 && (items_per_cta < 1 || items_per_cta > 1024)) {
+        set_error("lattice_set_tiling: items_per_cta must be 0 (heuristic) or 1..1024");
+        return LPC_ERR_INVALID;
+    }
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->wstream);
+    h->t1_ty = tile_rows;
+    h->t1_ipc = items_per_cta;
+    h->maps_K = 0;
+    drop_graphs(h);
+    return LPC_OK;
+}
+
 lpc_status lattice_step_n(lpc_lattice* h, int64_t n) {
     Range nvtx("lattice_step_n");
     if (!h) { set_error("lattice_step_n: NULL handle"); return LPC_ERR_INVALID; }
@@ -1108,16 +1130,34 @@ lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* ker
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best_kernel = LPC_KERNEL_STEP1, best_k = 1;
+    // candidates: the register-pipelined kernel; the TMA-fed one-step kernel
+    // at every tile height and three work-item sizes; TB at depth 2..maxk
+    struct Cand { int kernel, K, ty, ipc; };
+    std::vector<Cand> cands{{LPC_KERNEL_STEP1, 1, 0, 0}};
+    for (int ty : {16, 12, 8})
+        for (int ipc : {20, 40, 80}) cands.push_back({LPC_KERNEL_TB, 1, ty, ipc});
+    for (int K = 2; K <= maxk; ++K) cands.push_back({LPC_KERNEL_TB, K, 0, 0});
+    const int ty0 = h->t1_ty, ipc0 = h->t1_ipc;
+    Cand best_c{LPC_KERNEL_STEP1, 1, 0, 0};
     double best = -1.0;
-    for (int cand = 0; cand <= maxk && st == LPC_OK; ++cand) {
-        const bool tb = cand > 0;
-        const int K = tb ? cand : 1;
+    for (const Cand& c : cands) {
+        if (st != LPC_OK) break;
+        const bool tb = c.kernel == LPC_KERNEL_TB;
+        const int K = c.K;
         if (tb && (!tb_supported(make_view(h, 0), h->p.weight_dtype, K) || !tb_depth_allowed(h, K))) continue;
         if (tb) {
             h->kernel = LPC_KERNEL_TB;
             h->kdepth = K;
+            h->t1_ty = c.ty;
+            h->t1_ipc = c.ipc;
+            h->maps_K = 0;                 // re-encode the tensor maps for this tiling
             if (tb_prepare(h->p.weight_dtype, K, h->p.msd_axes) != cudaSuccess) continue;
+            if (K == 1) {
+                st = ensure_maps(h);          // static data and tensor maps for this tiling
+                if (st != LPC_OK) break;
+                // a tile height the rings cannot hold falls back to the heuristic: skip it
+                if (t1_tile_rows(make_view(h, 0), h->p.weight_dtype) != c.ty) continue;
+            }
         } else {
             h->kernel = LPC_KERNEL_STEP1;
             h->kdepth = 1;
@@ -1131,7 +1171,7 @@ lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* ker
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         const double r = (double)n_updated(h) * K * trial_launches / (ms * 1e-3);
-        if (r > best) { best = r; best_kernel = h->kernel; best_k = K; }
+        if (r > best) { best = r; best_c = c; }
         // the device step counter advanced; put it back for the next trial
         const long long s0 = steps0;
         cudaMemcpyAsync(h->dstep, &s0, 8, cudaMemcpyHostToDevice, h->wstream);
@@ -1151,13 +1191,20 @@ lpc_status lattice_autotune(lpc_lattice* h, int32_t trial_launches, int32_t* ker
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
     dfree(h, snap, snap_bytes);
     h->steps = steps0;
-    if (st != LPC_OK) { h->kernel = kernel0; h->kdepth = k0; drop_graphs(h); return st; }
+    if (st != LPC_OK) {
+        h->kernel = kernel0; h->kdepth = k0; h->t1_ty = ty0; h->t1_ipc = ipc0; h->maps_K = 0;
+        drop_graphs(h);
+        return st;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "lattice_autotune: restore");
-    h->kernel = best_kernel;
-    h->kdepth = best_k;
+    h->kernel = best_c.kernel;
+    h->kdepth = best_c.K;
+    h->t1_ty = best_c.ty;
+    h->t1_ipc = best_c.ipc;
+    h->maps_K = 0;
     drop_graphs(h);
-    if (kernel) *kernel = best_kernel;
-    if (block_steps) *block_steps = best_k;
+    if (kernel) *kernel = best_c.kernel;
+    if (block_steps) *block_steps = best_c.K;
     if (rate) *rate = best;
     return LPC_OK;
 }
@@ -1187,6 +1234,8 @@ lpc_status lattice_info(lpc_lattice* h, lpc_info* out) {
     out->kernel = h->kernel;
     out->block_steps = h->kdepth;
     out->static_form = h->lnk ? 2 : (h->gwin ? 1 : 0);
+    out->tile_rows = t1_tile_rows(make_view(h, h->cur), h->p.weight_dtype);
+    out->items_per_cta = h->t1_ipc > 0 ? h->t1_ipc : t1_default_items_per_cta();
     out->device_bytes = h->device_bytes;
     long long b = 24 + 6 * (long long)wbytes(h) + 8;
     for (int a = 0; a < 3; ++a) if (h->p.msd_axes >> a & 1) b += 8;

@@ -179,6 +179,11 @@ class Lattice:
     def set_schedule(self, kernel, block_steps=1):
         B.check(self.lib.lattice_set_schedule(self.h, int(kernel), int(block_steps)), self.lib)
 
+    def set_tiling(self, tile_rows=0, items_per_cta=0):
+        """Tile rows (8, 12, 16) and work items per CTA of the TMA-fed one-step
+        kernel; 0 = its heuristic (``lattice_set_tiling``)."""
+        B.check(self.lib.lattice_set_tiling(self.h, int(tile_rows), int(items_per_cta)), self.lib)
+
     def set_static_form(self, form):
         """Static data form of the TMA-fed one-step kernel: B.LPC_STATIC_AUTO,
         _GATHER or _LINK (``lattice_set_static_form``)."""

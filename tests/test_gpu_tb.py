@@ -132,8 +132,39 @@ def test_autotune_restores_state_and_caches(tmp_path):
     other = Lattice.from_input(inp, ghost=4)
     c2 = autotune.choose(other, path=path)
     assert c2["cached"] and c2["kernel"] == c1["kernel"] and c2["block_steps"] == c1["block_steps"]
+    assert c2["tile_rows"] == c1["tile_rows"] and c2["items_per_cta"] == c1["items_per_cta"]
+    info = other.info()
+    if c1["kernel"] == B.LPC_KERNEL_TB and c1["block_steps"] == 1:
+        assert (info["tile_rows"], info["items_per_cta"]) == (c1["tile_rows"], c1["items_per_cta"])
     for l in (ref, lat, other):
         l.close()
+
+
+@pytest.mark.parametrize("tiling", [(16, 0), (12, 5), (8, 200), (16, 1024)])
+def test_tma_tiling_keeps_states_bit_identical(tiling):
+    """Tile rows and work items per CTA of the TMA-fed one-step kernel (the
+    autotuner's knobs) change the work split, not the states; sums agree to
+    FP32 summation order."""
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case((48, 70, 150), 331, periodic=(1, 0, 1), alpha=0.6, msd_axes=3)
+    out = []
+    for t in ((0, 0), tiling):
+        lat = Lattice.from_input(inp)
+        lat.set_schedule(B.LPC_KERNEL_TB, 1)
+        lat.set_tiling(*t)
+        lat.step(25)
+        info = lat.info()
+        if t[0]:
+            assert info["tile_rows"] == t[0]
+        if t[1]:
+            assert info["items_per_cta"] == t[1]
+        out.append((lat.density(), lat.magnetization(), lat.moment(0), lat.fid(), lat.msd(1)))
+        lat.close()
+    a, b = out
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    assert np.allclose(a[3], b[3], rtol=1e-6, atol=1e-6 * abs(a[3][0]))
+    assert np.allclose(a[4][1:], b[4][1:], rtol=1e-5)
 
 
 def test_one_step_tma_sums_bit_reproducible():
