@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=48)
     ap.add_argument("--serve-quantum", type=int, default=250)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
+                    help="admission order of the served pass (the comparator runs in arrival order)")
     return ap.parse_args()
 
 
@@ -594,11 +596,12 @@ def run_serving(args):
     warm = [lpc_inputs.Request(10 ** 6 + i, 0.0, 24, 20, 7) for i in range(2)]
     for w in warm:
         cache[w.rid] = w.lattice()
-    Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(warm)
+    Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum, policy=args.serve_policy).run(warm)
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    recs = Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum).run(reqs)
+    recs = Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum,
+                  policy=args.serve_policy).run(reqs)
     torch.cuda.synchronize()
     clk_served = clocks.stop()
     s_batch = summary(recs)
@@ -613,7 +616,8 @@ def run_serving(args):
             "dtype": "f32",
             "config": {"workload": "serving_stream", "requests": len(reqs),
                        "step_scale": args.serve_step_scale, "slots": args.serve_slots,
-                       "quantum": args.serve_quantum, "hbm_budget_gb": args.serve_budget_gb},
+                       "quantum": args.serve_quantum, "hbm_budget_gb": args.serve_budget_gb,
+                       "policy": args.serve_policy},
             "served": s_batch, "one_at_a_time": s_seq,
             "speedup_vs_one_at_a_time": s_batch["aggregate_site_updates_per_s"] / s_seq["aggregate_site_updates_per_s"],
             "fid_same_as_one_at_a_time_1e-5": bool(same),

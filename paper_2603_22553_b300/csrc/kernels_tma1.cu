@@ -722,6 +722,337 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
         items_finish<NC + 1>(v, g.n_items, reinterpret_cast<double*>(ring1));
 }
 
+// ---------------------------------------------------------------------------
+// Many lattices in one launch (serving): the work queue holds the items of
+// every lattice of the launch, each lattice with its own tensor maps, view
+// and item split (the split of its own launch), so a lattice's states and
+// per-item sums are those of its own launch of k_step_tma1, and its final
+// fixed-order reduction (items_reduce, by the last CTA, lattice by lattice)
+// gives its sums bit for bit.  Lattices of one launch share the weight type,
+// the tile height and the ghost width; the full step without moments, in
+// the gather form (the form of the mid-size lattices that serving holds).
+
+struct alignas(64) T1Lat {
+    CUtensorMap rho, m, gwin, gs, gR;   // the lattice's current input buffer, gather form
+    LatticeView v;
+    int tiles_x, tiles, cz, n_items, item0;
+};
+
+struct T1MultiParams {
+    T1Lat lat[kMaxMulti];
+    int count, total_items;
+    int W, S1, S2, slot1, slot2, tx1, tx2;
+    unsigned int* work;                 // launch work queue (zeroed before the launch)
+    unsigned int* done;                 // CTAs finished (zeroed by the last one)
+};
+static_assert(sizeof(T1MultiParams) <= 32000, "kernel parameter space");
+
+template <typename WT, int NC>
+__global__ void __launch_bounds__((NC + 1) * 32, 1)
+k_step_tma1_multi(const __grid_constant__ T1MultiParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
+    constexpr int TY = NC;
+    constexpr int KSP = 8;
+    const int W = P.W, S1 = P.S1, S2 = P.S2;
+    const T1Slots SL = t1_slots(W, TY, 0, (int)sizeof(WT), false, false, 0, false);
+    unsigned char* ring1 = smem;
+    unsigned char* ring2 = smem + (size_t)S1 * P.slot1;
+    uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * P.slot2);
+    uint64_t* empty1 = full1 + S1;
+    uint64_t* full2 = empty1 + S1;
+    uint64_t* empty2 = full2 + S2;
+    uint64_t* ifree = empty2 + S2;
+    unsigned int* icount = reinterpret_cast<unsigned int*>(ifree + 2);
+    SlotHdr* hdr = reinterpret_cast<SlotHdr*>(ifree + 3);
+    double* ired = reinterpret_cast<double*>(hdr + S1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(ired + 2 * NC * KSP);
+    volatile unsigned int* issued1 = reinterpret_cast<volatile unsigned int*>(abort_flag + 1);
+    volatile unsigned int* issued2 = issued1 + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < S1; ++s) {
+            mbar_init(&full1[s], 1);
+            mbar_init(&empty1[s], NC);
+        }
+        for (int s = 0; s < S2; ++s) {
+            mbar_init(&full2[s], 1);
+            mbar_init(&empty2[s], NC);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ifree[b], 1);
+            icount[b] = 0u;
+        }
+        *abort_flag = 0;
+        *issued1 = 0;
+        *issued2 = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == NC) {
+        // ---------------- producer: one elected lane takes items of any lattice
+        if (lane == 0) {
+            bool ok = true;
+            Cursor c1{0, 0u}, c2{0, 0u};
+            unsigned int n1 = 0, n2 = 0;
+            auto state_load = [&](const T1Lat& T, int z, const SlotHdr& h, int bx, int by) -> bool {
+                if (n1 >= (unsigned)S1 && !mbar_wait_bounded(&empty1[c1.slot], c1.ph ^ 1u)) return false;
+                if (*abort_flag) return false;
+                hdr[c1.slot] = h;
+                unsigned char* st = ring1 + (size_t)c1.slot * P.slot1;
+                uint64_t* fb = &full1[c1.slot];
+                fence_proxy_async();
+                if (h.tile < 0) {
+                    mbar_arrive(fb);
+                } else {
+                    mbar_expect_tx(fb, (uint32_t)P.tx1);
+                    tma3(st, &T.rho, fb, bx, by, z);
+                    tma3(st + SL.m, &T.m, fb, 2 * bx, by, z);
+                }
+                *issued1 = ++n1;
+                c1.next(S1);
+                return true;
+            };
+            for (;;) {
+                const int item = (int)atomicAdd(P.work, 1u);
+                if (item >= P.total_items) break;
+                int L = 0;
+                while (L + 1 < P.count && item >= P.lat[L + 1].item0) ++L;
+                const T1Lat& T = P.lat[L];
+                const int local = item - T.item0;
+                const int nz = T.v.nz;
+                const int tile = local % T.tiles;
+                const int za = T.v.zlo + (local / T.tiles) * T.cz;
+                const int n = min(T.cz, T.v.zhi - za);
+                const int tx = tile % T.tiles_x, ty = tile / T.tiles_x;
+                const int bx = tx * kTX;
+                const int by = ty * TY + T.v.G - 1;
+                const int sx = tx * kTX, sy = ty * TY;
+                const SlotHdr h{tile, za, n, L};
+                ok = state_load(T, za == 0 ? nz - 1 : za - 1, h, bx, by) && state_load(T, za, h, bx, by);
+                for (int q = 0; q < n && ok; ++q) {
+                    if (n2 >= (unsigned)S2) ok = mbar_wait_bounded(&empty2[c2.slot], c2.ph ^ 1u);
+                    if (!ok || *abort_flag) { ok = false; break; }
+                    {
+                        unsigned char* st = ring2 + (size_t)c2.slot * P.slot2;
+                        uint64_t* fb = &full2[c2.slot];
+                        const int z = za + q;
+                        fence_proxy_async();
+                        mbar_expect_tx(fb, (uint32_t)P.tx2);
+                        tma4(st, &T.gwin, fb, sx, sy, z, 0);
+                        tma3(st + SL.s, &T.gs, fb, sx, sy, z);
+                        tma3(st + SL.R, &T.gR, fb, 2 * sx, sy, z);
+                        *issued2 = ++n2;
+                        c2.next(S2);
+                    }
+                    const int za1 = za + q + 1;
+                    ok = state_load(T, za1 == nz ? 0 : za1, h, bx, by);
+                }
+                if (!ok) break;
+            }
+            if (ok) ok = state_load(P.lat[0], 0, SlotHdr{-1, 0, 0, 0}, 0, 0);
+            if (!ok) *abort_flag = 1;
+        }
+    } else {
+        // ---------------- consumer warps: core row `warp`, sites x0 + 2 lane + {0, 1}
+        float part[3] = {0.f, 0.f, 0.f};
+        bool ok = true;
+        Cursor w1{0, 0u}, w2{0, 0u};
+        unsigned int kitem = 0;
+        const int o = (warp + 1) * W + P.lat[0].v.G + 2 * lane;   // one ghost width for the launch
+        const int os = warp * kTX + 2 * lane;
+        const int C = TY * kTX;
+        for (;;) {
+            ok = mbar_wait_bounded(&full1[w1.slot], w1.ph);
+            if (!ok) break;
+            const SlotHdr h = hdr[w1.slot];
+            if (h.tile < 0) break;
+            const T1Lat& T = P.lat[h.pad];
+            const LatticeView& v = T.v;
+            const int G = v.G;
+            const int tx = h.tile % T.tiles_x, ty = h.tile / T.tiles_x;
+            const int x = tx * kTX + 2 * lane;
+            const int y = ty * TY + warp;
+            const bool ok_y = y < v.ny;
+            const bool site0 = ok_y && x < v.nx;
+            const bool site1 = ok_y && x + 1 < v.nx;
+            const bool images = (v.per_x && (x < G || x + 1 >= v.nx - G)) || (v.per_y && (y < G || y >= v.ny - G));
+            const long long col = (long long)(y + G) * v.Xp + (x + G);
+            const long long zplane = (long long)v.Xp * v.Yp;
+            float* rho_out = v.rho_out;
+            float2* m_out = v.m_out;
+            float2 br;
+            float4 bm;
+            {
+                const unsigned char* s0 = ring1 + (size_t)w1.slot * P.slot1;
+                br = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(s0) + o);
+                bm = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(s0 + SL.m) + o);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty1[w1.slot]);
+                w1.next(S1);
+            }
+            ok = mbar_wait_bounded(&full1[w1.slot], w1.ph);
+            int center = w1.slot;
+            w1.next(S1);
+            for (int q = 0; q < h.n && ok; ++q) {
+                const int z = h.za + q;
+                const int sslot = w2.slot;
+                ok = mbar_wait_bounded(&full2[sslot], w2.ph);
+                w2.next(S2);
+                const int above = w1.slot;
+                ok = ok && mbar_wait_bounded(&full1[above], w1.ph);
+                w1.next(S1);
+                if (!ok || *abort_flag) { ok = false; break; }
+                const unsigned char* sc = ring1 + (size_t)center * P.slot1;
+                const unsigned char* sv = ring1 + (size_t)above * P.slot1;
+                const unsigned char* ss = ring2 + (size_t)sslot * P.slot2;
+                const float* rc = reinterpret_cast<const float*>(sc);
+                const float2 r_c = *reinterpret_cast<const float2*>(rc + o);
+                const float r_l = rc[o - 1], r_r = rc[o + 2];
+                const float2 r_u = *reinterpret_cast<const float2*>(rc + o - W);
+                const float2 r_d = *reinterpret_cast<const float2*>(rc + o + W);
+                const float2 r_a = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sv) + o);
+                const WT* win = reinterpret_cast<const WT*>(ss);
+                const float2 sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
+                float2 win2[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) win2[k] = lds_w2<WT>(win + k * C + os);
+                SiteIn q0, q1;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    q0.win[k] = win2[k].x;
+                    q1.win[k] = win2[k].y;
+                }
+                const float2 rn2[6] = {make_float2(r_l, r_c.x), make_float2(r_c.y, r_r), r_u, r_d, br, r_a};
+                const float2 ro = pair_rho(win2, rn2, r_c, sp);
+                const float2* mc = reinterpret_cast<const float2*>(sc + SL.m);
+                const float4 m_c = *reinterpret_cast<const float4*>(mc + o);
+                const float2 m_l = mc[o - 1], m_r = mc[o + 2];
+                const float4 m_u = *reinterpret_cast<const float4*>(mc + o - W);
+                const float4 m_d = *reinterpret_cast<const float4*>(mc + o + W);
+                const float4 m_a = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(sv + SL.m) + o);
+                const float4 Rp = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(ss + SL.R) + os);
+                q0.m[0] = m_l;                         q1.m[0] = make_float2(m_c.x, m_c.y);
+                q0.m[1] = make_float2(m_c.z, m_c.w);   q1.m[1] = m_r;
+                q0.m[2] = make_float2(m_u.x, m_u.y);   q1.m[2] = make_float2(m_u.z, m_u.w);
+                q0.m[3] = make_float2(m_d.x, m_d.y);   q1.m[3] = make_float2(m_d.z, m_d.w);
+                q0.m[4] = make_float2(bm.x, bm.y);     q1.m[4] = make_float2(bm.z, bm.w);
+                q0.m[5] = make_float2(m_a.x, m_a.y);   q1.m[5] = make_float2(m_a.z, m_a.w);
+                q0.mc = make_float2(m_c.x, m_c.y); q0.R = make_float2(Rp.x, Rp.y);
+                q1.mc = make_float2(m_c.z, m_c.w); q1.R = make_float2(Rp.z, Rp.w);
+                float2 mo0, mo1;
+                site_m(q0, sp.x, mo0);
+                site_m(q1, sp.y, mo1);
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&empty1[center]);
+                    mbar_arrive(&empty2[sslot]);
+                }
+                {
+                    const long long p = col + (long long)z * zplane;
+                    if (site0 && site1) {
+                        *reinterpret_cast<float2*>(rho_out + p) = ro;
+                        *reinterpret_cast<float4*>(m_out + p) = make_float4(mo0.x, mo0.y, mo1.x, mo1.y);
+                    } else if (site0) {
+                        rho_out[p] = ro.x;
+                        m_out[p] = mo0;
+                    }
+                }
+                if (images) {
+                    const long long zoff = (long long)z * zplane;
+                    if (site0) {
+                        store_ghost_images(rho_out, v, x, y, zoff, ro.x);
+                        store_ghost_images(m_out, v, x, y, zoff, mo0);
+                    }
+                    if (site1) {
+                        store_ghost_images(rho_out, v, x + 1, y, zoff, ro.y);
+                        store_ghost_images(m_out, v, x + 1, y, zoff, mo1);
+                    }
+                }
+                if (site0) { part[0] += mo0.x; part[1] += mo0.y; part[2] += ro.x; }
+                if (site1) { part[0] += mo1.x; part[1] += mo1.y; part[2] += ro.y; }
+                br = r_c;
+                bm = m_c;
+                center = above;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty1[center]);
+            const int b = kitem & 1;
+            const unsigned int use = kitem >> 1;
+            if (use > 0) ok = mbar_wait_bounded(&ifree[b], (use - 1) & 1u);
+            if (!ok) break;
+            // the item's sums, as in k_step_tma1: a butterfly per warp, the
+            // last warp of the item adds the warps in order
+#pragma unroll
+            for (int qq = 0; qq < kNumSums; ++qq) {
+                const float t = warp_sum_f32(qq < 3 ? part[qq] : 0.f);
+                if (lane == 0) ired[(b * NC + warp) * KSP + qq] = (double)t;
+                if (qq < 3) part[qq] = 0.f;
+            }
+            __syncwarp();
+            unsigned int last = 0u;
+            if (lane == 0) {
+                __threadfence_block();
+                last = atomicAdd(&icount[b], 1u) == (unsigned)NC - 1u;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                if (lane < kNumSums) {
+                    double sum = 0.0;
+                    for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * KSP + lane];
+                    const int item = ((h.za - v.zlo) / T.cz) * T.tiles + h.tile;
+                    v.partials[(long long)item * kNumSums + lane] = sum;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    icount[b] = 0u;
+                    mbar_arrive(&ifree[b]);
+                }
+            }
+            ++kitem;
+        }
+        if (!ok) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        if (tid == 0) {
+            for (int L = 0; L < P.count; ++L) atomicExch(P.lat[L].v.counter + 1, (unsigned int)LPC_ERR_TIMEOUT);
+            const unsigned int m1 = *issued1, m2 = *issued2;
+            for (unsigned int l = m1 > (unsigned)S1 ? m1 - S1 : 0; l < m1; ++l)
+                mbar_wait_bounded(&full1[l % S1], (l / S1) & 1u);
+            for (unsigned int l = m2 > (unsigned)S2 ? m2 - S2 : 0; l < m2; ++l)
+                mbar_wait_bounded(&full2[l % S2], (l / S2) & 1u);
+        }
+        __syncthreads();
+        return;
+    }
+    // the last CTA reduces every lattice's items in a fixed order, in the
+    // idle ring memory
+    __threadfence();
+    __shared__ unsigned int is_last;
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(P.done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int L = 0; L < P.count; ++L) items_reduce<NC + 1>(P.lat[L].v, P.lat[L].n_items, reinterpret_cast<double*>(ring1));
+    if (tid == 0) *P.done = 0u;
+}
+
+template <typename WT, int NC>
+void* t1_multi_fn() { return reinterpret_cast<void*>(&k_step_tma1_multi<WT, NC>); }
+
+void* t1_multi_kernel(int TY, int wdtype) {
+    const bool bf = wdtype == LPC_WEIGHTS_BF16;
+    if (TY == 16) return bf ? t1_multi_fn<__nv_bfloat16, 16>() : t1_multi_fn<float, 16>();
+    if (TY == 12) return bf ? t1_multi_fn<__nv_bfloat16, 12>() : t1_multi_fn<float, 12>();
+    return bf ? t1_multi_fn<__nv_bfloat16, 8>() : t1_multi_fn<float, 8>();
+}
+
 template <typename WT, int MSD, int NC, bool REG, bool LNK>
 void* t1_fn() { return reinterpret_cast<void*>(&k_step_tma1<WT, MSD, NC, false, REG, LNK>); }
 
@@ -863,6 +1194,26 @@ int t1_tile_rows(const LatticeView& v, int wdtype) { return t1_choose(v, wdtype)
 
 int t1_default_items_per_cta() { return LPC_T1_ITEMS_PER_CTA; }
 
+// Work items of one lattice at tile height TY: tiles of 64 x TY sites, the
+// tile index fastest, over z-chunks of cz planes of [zlo, zhi); about
+// items_per_cta items per CTA of a one-CTA-per-SM grid, chunks of at least 8
+// planes (the multi-lattice launch uses the same split, so a lattice's
+// per-item sums are the same in either launch).
+void t1_items(const LatticeView& v, int TY, int* tiles_x, int* tiles, int* cz_out, int* n_items) {
+    *tiles_x = (v.nx + kTX - 1) / kTX;
+    *tiles = *tiles_x * ((v.ny + TY - 1) / TY);
+    const int sms = device_props().sm_count;
+    const int nzu = v.zhi - v.zlo;              // planes updated
+    const long long ipc = v.t1_ipc > 0 ? v.t1_ipc : LPC_T1_ITEMS_PER_CTA;
+    long long cz = (long long)*tiles * nzu / (ipc * sms);
+    if (cz < 8) cz = 8;
+    if (cz > nzu) cz = nzu;
+    while ((long long)*tiles * ((nzu + cz - 1) / cz) > t1_max_items() && cz < nzu) cz *= 2;
+    if (cz > nzu) cz = nzu;
+    *cz_out = (int)cz;
+    *n_items = *tiles * ((nzu + *cz_out - 1) / *cz_out);
+}
+
 bool t1_supported(const LatticeView& v, int wdtype) {
     const T1Choice c = t1_choose(v, wdtype);
     const long long tiles = (long long)((v.nx + kTX - 1) / kTX) * ((v.ny + c.TY - 1) / c.TY);
@@ -935,6 +1286,71 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
     return ok;
 }
 
+// A lattice joins a multi-lattice launch when it runs the TMA-fed one-step
+// kernel from the gather form, without moments, regions or halo planes.
+bool t1_multi_member(const LatticeView& v, int wdtype) {
+    return v.gwin && !v.lnk && !v.gdm && v.msd_axes == 0 && v.nreg == 0 && v.zlo == 0 && v.zhi == v.nz &&
+           t1_supported(v, wdtype);
+}
+
+int t1_multi_group(const LatticeView& v, int wdtype) {
+    return (t1_choose(v, wdtype).TY * 16 + v.G) * 2 + (wdtype == LPC_WEIGHTS_BF16 ? 1 : 0);
+}
+
+cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* maps, int count, int wdtype,
+                              unsigned int* words, cudaStream_t st) {
+    if (count < 1 || count > kMaxMulti) return cudaErrorInvalidValue;
+    static thread_local T1MultiParams P;
+    const T1Choice c = t1_choose(views[0], wdtype);
+    const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    P.W = c.W;
+    P.S1 = c.S1;
+    P.S2 = c.S2;
+    P.slot1 = c.L.bytes1;
+    P.slot2 = c.L.bytes2;
+    P.tx1 = (c.TY + 2) * c.W * 12;
+    P.tx2 = c.TY * kTX * (6 * wb + 4 + 8);
+    int total = 0;
+    for (int i = 0; i < count; ++i) {
+        const LatticeView& v = views[i];
+        if (!t1_multi_member(v, wdtype) || t1_multi_group(v, wdtype) != t1_multi_group(views[0], wdtype))
+            return cudaErrorInvalidValue;
+        T1Lat& T = P.lat[i];
+        T.rho = maps[i]->rho;
+        T.m = maps[i]->m;
+        T.gwin = maps[i]->gwin;
+        T.gs = maps[i]->gs;
+        T.gR = maps[i]->gR;
+        T.v = v;
+        t1_items(v, c.TY, &T.tiles_x, &T.tiles, &T.cz, &T.n_items);
+        if (T.n_items > t1_max_items()) return cudaErrorInvalidConfiguration;
+        T.item0 = total;
+        total += T.n_items;
+    }
+    P.count = count;
+    P.total_items = total;
+    P.work = words;
+    P.done = words + 1;
+    static bool attr_done[2][3] = {};
+    bool& ad = attr_done[wb == 2][c.TY == 16 ? 0 : (c.TY == 12 ? 1 : 2)];
+    void* fn = t1_multi_kernel(c.TY, wdtype);
+    if (!ad) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 device_props().max_smem_optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+        ad = true;
+    }
+    cudaError_t e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int grid = device_props().sm_count;
+    if (grid > total) grid = total;
+    void* args[] = {&P};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((c.TY + 1) * 32), args, (size_t)c.smem, st);
+}
+
 cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, unsigned int* err,
                         cudaStream_t st, bool rho_only) {
     if (!v.gwin && !v.lnk) return cudaErrorInvalidValue;
@@ -958,18 +1374,8 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
         g.tx2 = c.TY * kTX * (3 * wb + (rho_only ? 0 : 8)) + kTX * wb;
     else
         g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
-    g.tiles_x = (v.nx + kTX - 1) / kTX;
-    g.tiles = g.tiles_x * ((v.ny + c.TY - 1) / c.TY);
+    t1_items(v, c.TY, &g.tiles_x, &g.tiles, &g.cz, &g.n_items);
     const int sms = device_props().sm_count;
-    const int nzu = v.zhi - v.zlo;              // planes updated
-    const long long ipc = v.t1_ipc > 0 ? v.t1_ipc : LPC_T1_ITEMS_PER_CTA;
-    long long cz = (long long)g.tiles * nzu / (ipc * sms);
-    if (cz < 8) cz = 8;
-    if (cz > nzu) cz = nzu;
-    while ((long long)g.tiles * ((nzu + cz - 1) / cz) > t1_max_items() && cz < nzu) cz *= 2;
-    if (cz > nzu) cz = nzu;
-    g.cz = (int)cz;
-    g.n_items = g.tiles * ((nzu + g.cz - 1) / g.cz);
     if (g.n_items > t1_max_items()) return cudaErrorInvalidConfiguration;
     g.err = err;
     g.work = err + 7;

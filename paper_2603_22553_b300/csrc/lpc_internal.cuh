@@ -330,19 +330,16 @@ __device__ void block_finish_smem(const LatticeView& v, int levels, double* smem
 // butterfly), so the result does not depend on which block took which item,
 // and writes the history entries of one step at *v.step.  `scratch` is
 // shared memory for kNumSums * blockDim doubles (free at this point).
+// The fixed-order reduction of items_finish, run by every thread of one
+// block: the items' FP64 partials into the history entries of one step at
+// *v.step (thread t adds items t, t + T, ... in order into scratch[q][t];
+// warp q adds the T values lane-strided and by an FP64 butterfly), then
+// *v.step advances.  The result depends on the items' partials only.
 template <int NW>
-__device__ void items_finish(const LatticeView& v, int n_items, double* scratch) {
+__device__ void items_reduce(const LatticeView& v, int n_items, double* scratch) {
     const int T = NW * 32;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    __threadfence();
-    __shared__ unsigned int is_last;
-    __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(v.counter, 1u) == (unsigned)nblk - 1u);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
     double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
     for (int b = tid; b < n_items; b += T) {
@@ -366,10 +363,27 @@ __device__ void items_finish(const LatticeView& v, int n_items, double* scratch)
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        *v.step = n + 1;
-        *v.counter = 0u;
-    }
+    if (tid == 0) *v.step = n + 1;
+}
+
+// Final reduction of per-item FP64 sums v.partials[item * kNumSums + q]
+// written by the blocks of a work-queue kernel: the last block to finish
+// runs items_reduce, so the result does not depend on which block took which
+// item.  `scratch` is shared memory for kNumSums * blockDim doubles (free at
+// this point).
+template <int NW>
+__device__ void items_finish(const LatticeView& v, int n_items, double* scratch) {
+    const int tid = threadIdx.x;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    __shared__ unsigned int is_last;
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(v.counter, 1u) == (unsigned)nblk - 1u);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    items_reduce<NW>(v, n_items, scratch);
+    if (tid == 0) *v.counter = 0u;
 }
 
 // items_finish for items that also carry region sums: per item KS values,
@@ -530,6 +544,16 @@ bool t1_supported(const LatticeView& v, int wdtype);
 // work items per CTA.
 int t1_tile_rows(const LatticeView& v, int wdtype);
 int t1_default_items_per_cta();
+// Multi-lattice launches of the TMA-fed one-step kernel (serving): up to
+// kMaxMulti lattices of one group (weight type, tile height, ghost width)
+// step once in one launch, each with the states and sums of its own launch.
+constexpr int kMaxMulti = 24;
+bool t1_multi_member(const LatticeView& v, int wdtype);
+int t1_multi_group(const LatticeView& v, int wdtype);
+// maps[i]: the tensor maps of lattice i's current input buffer; words: two
+// device words (work queue, CTAs done), zeroed here before the launch.
+cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* maps, int count, int wdtype,
+                              unsigned int* words, cudaStream_t st);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
 int gather_pitch(int nx);
 cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,

@@ -1030,17 +1030,69 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
         cudaEventRecord(hs[i]->ev_in, hs[i]->wstream);
         cudaStreamWaitEvent(bs, hs[i]->ev_in, 0);
     }
-    // lattices whose item partials do not fit their buffer step alone
+    // lattices on the TMA-fed one-step kernel share multi-lattice launches
+    // (per group of weight type, tile height and ghost width); the others
+    // are batched with the register-pipelined kernel, or step alone where
+    // their item partials do not fit their buffer
     std::vector<int> alone;
     std::vector<int> batched;
-    for (int i = 0; i < count; ++i) {
+    std::vector<int> multi;
+    lpc_status status = LPC_OK;
+    for (int i = 0; i < count && status == LPC_OK; ++i) {
+        lpc_lattice* h = hs[i];
+        if (n[i] > 0 && h->kernel == LPC_KERNEL_TB && h->kdepth == 1) {
+            status = ensure_maps(h);        // static data and tensor maps, outside the launches
+            if (status == LPC_OK && t1_multi_member(make_view(h, h->cur), h->p.weight_dtype)) {
+                multi.push_back(i);
+                continue;
+            }
+        }
         int tx, ty, cz;
-        const int items = batch_items(make_view(hs[i], hs[i]->cur), &tx, &ty, &cz);
-        if ((size_t)items * kNumSums > hs[i]->partials_doubles || hs[i]->nreg > 0 || hs[i]->zlo > 0) alone.push_back(i);
+        const int items = batch_items(make_view(h, h->cur), &tx, &ty, &cz);
+        if ((size_t)items * kNumSums > h->partials_doubles || h->nreg > 0 || h->zlo > 0) alone.push_back(i);
         else batched.push_back(i);
     }
+    if (status != LPC_OK) return status;
     static thread_local BatchParams bp;
-    lpc_status status = LPC_OK;
+    // multi-lattice TMA launches: one per step and group chunk, over the
+    // lattices with steps left (sorted by step count, so they form a prefix)
+    {
+        std::vector<int> order = multi;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const int ga = t1_multi_group(make_view(hs[a], hs[a]->cur), hs[a]->p.weight_dtype);
+            const int gb = t1_multi_group(make_view(hs[b], hs[b]->cur), hs[b]->p.weight_dtype);
+            return ga != gb ? ga < gb : n[a] > n[b];
+        });
+        static thread_local std::vector<LatticeView> views;
+        static thread_local std::vector<const TBMaps*> mps;
+        for (size_t g0 = 0; g0 < order.size() && status == LPC_OK;) {
+            const int grp = t1_multi_group(make_view(hs[order[g0]], hs[order[g0]]->cur), hs[order[g0]]->p.weight_dtype);
+            size_t g1 = g0;
+            while (g1 < order.size() &&
+                   t1_multi_group(make_view(hs[order[g1]], hs[order[g1]]->cur), hs[order[g1]]->p.weight_dtype) == grp)
+                ++g1;
+            const int wd = hs[order[g0]]->p.weight_dtype;
+            for (size_t c0 = g0; c0 < g1 && status == LPC_OK; c0 += kMaxMulti) {
+                const size_t c1 = std::min(g1, c0 + (size_t)kMaxMulti);
+                const long long steps_c = n[order[c0]];
+                for (long long s = 0; s < steps_c && status == LPC_OK; ++s) {
+                    views.clear();
+                    mps.clear();
+                    for (size_t j = c0; j < c1; ++j) {
+                        lpc_lattice* h = hs[order[j]];
+                        if (n[order[j]] <= s) break;          // sorted: the rest are done too
+                        views.push_back(make_view(h, h->cur));
+                        mps.push_back(h->maps[h->cur]);
+                    }
+                    const cudaError_t e = launch_tma1_multi(views.data(), mps.data(), (int)views.size(), wd,
+                                                            h0->counter + 20, bs);
+                    if (e != cudaSuccess) { status = cuda_fail(e, "multi-lattice step launch"); break; }
+                    for (size_t j = 0; j < views.size(); ++j) hs[order[c0 + j]]->cur ^= 1;
+                }
+            }
+            g0 = g1;
+        }
+    }
     // per (weight type, MSD mask) group, chunks of kMaxBatch lattices sorted
     // by step count: one persistent launch runs every step of a chunk; where
     // a cooperative launch is not possible, one launch per step
@@ -1092,7 +1144,8 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
             }
         }
     for (int i : alone)
-        for (long long s = 0; s < n[i] && status == LPC_OK; ++s) status = launch_one(hs[i], bs, false);
+        for (long long s = 0; s < n[i] && status == LPC_OK; ++s)
+            status = launch_one(hs[i], bs, hs[i]->kernel == LPC_KERNEL_TB && hs[i]->kdepth == 1);
     for (int i = 0; i < count; ++i) hs[i]->steps += n[i];
     // every lattice's private stream continues after the batch (queries and
     // later calls synchronise on it); callers' streams are left free so that

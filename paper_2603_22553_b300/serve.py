@@ -8,11 +8,16 @@ Continuous batching on one GPU:
   thread builds its fields and creates the lattice (its state then stays
   resident on the device until it finishes);
 * every round advances all resident lattices together by up to ``quantum``
-  steps: the small ones with ``lattice_step_many`` (one persistent launch
-  covers the work items of every small resident lattice), the large ones
-  with ``lattice_step_n`` on their own streams (the one-step TMA kernel in
-  captured graphs), each on its own stream, so work of requests that
-  arrived at different times overlaps on the device;
+  steps with one ``lattice_step_many`` call: the mid-size and large ones
+  (the TMA-fed one-step kernel) share one multi-lattice launch per step
+  whose work queue holds the tiles of every such lattice, the small ones
+  share one persistent launch of the batched register-pipelined kernel, so
+  work of requests that arrived at different times runs in the same
+  launches;
+* admission order: ``policy="fifo"`` (arrival order, no overtaking) or
+  ``"sjf"`` (the pending request with the least work, sites x steps, first:
+  short requests are not held behind long ones; ``max_wait_s`` lets a
+  request that has waited that long go first, so none starves);
 * a lattice that has done its steps has its FID read back and is destroyed,
   which frees its slot and memory for the next admission.
 
@@ -104,28 +109,11 @@ class GpuEngine:
         return lat
 
     def step_many(self, lats, steps):
-        """Lattices that the one-step TMA kernel serves (large enough to fill
-        its tiles) advance with lattice_step_n on their own streams (captured
-        graphs); the others share batched launches.  Both kinds are queued
-        before any waits, so their work overlaps on the device."""
-        own, batch = [], []
-        for lat, n in zip(lats, steps):
-            if self._tma(lat):
-                own.append((lat, n))
-            else:
-                batch.append((lat, n))
-        for lat, n in own:
-            lat.step(n)
-        if batch:
-            self.L.step_many([b[0] for b in batch], [b[1] for b in batch])
-
-    def _tma(self, lat):
-        k = getattr(lat, "_serve_tma", None)
-        if k is None:
-            info = lat.info()
-            k = info["kernel"] == B.LPC_KERNEL_TB and info["block_steps"] == 1
-            lat._serve_tma = k
-        return k
+        """Every resident lattice in one lattice_step_many call: the library
+        puts the lattices of the TMA-fed one-step kernel into multi-lattice
+        launches and the small ones into batched launches."""
+        if lats:
+            self.L.step_many(list(lats), list(steps))
 
     def finish(self, lat):
         fid = lat.fid() if self.keep_fid else None
@@ -145,12 +133,27 @@ class GpuEngine:
 class Server:
     """Continuous-batching server over an engine (GPU or a test fake)."""
 
-    def __init__(self, engine, hbm_budget, max_active=48, quantum=250, prefetch=4):
+    def __init__(self, engine, hbm_budget, max_active=48, quantum=250, prefetch=4, policy="fifo",
+                 max_wait_s=None):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
         self.engine = engine
         self.budget = int(hbm_budget)
         self.max_active = int(max_active)
         self.quantum = int(quantum)
         self.prefetch = int(prefetch)
+        self.policy = policy
+        self.max_wait_s = max_wait_s
+
+    def _next(self, pending, t):
+        """Index of the pending request to admit next."""
+        if self.policy == "fifo":
+            return 0
+        if self.max_wait_s is not None:
+            for i, r in enumerate(pending):       # pending is in arrival order
+                if t - r.arrival_s >= self.max_wait_s:
+                    return i
+        return min(range(len(pending)), key=lambda i: (pending[i].edge ** 3 * pending[i].steps, i))
 
     def run(self, requests, realtime=True):
         """Serve ``requests`` (sorted by arrival); returns the list of Records."""
@@ -194,10 +197,14 @@ class Server:
                 t = now()
                 while arrivals and arrivals[0].arrival_s <= t:
                     pending.append(arrivals.popleft())
-                # admission by footprint and free slots (FIFO: no overtaking)
-                while (pending and len(active) + preparing < self.max_active
-                       and used + fp[pending[0].rid] <= self.budget):
-                    req = pending.popleft()
+                # admission by footprint and free slots, in the policy's order
+                # (the chosen request waits for memory; nothing overtakes it)
+                while pending and len(active) + preparing < self.max_active:
+                    k = self._next(pending, t)
+                    if used + fp[pending[k].rid] > self.budget:
+                        break
+                    req = pending[k]
+                    del pending[k]
                     used += fp[req.rid]
                     preparing += 1
                     recs[req.rid].admit = now()

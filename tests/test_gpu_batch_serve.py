@@ -119,3 +119,50 @@ def test_served_tma_lattices_equal_alone():
         alone = Server(eng, 16 << 30, max_active=1, quantum=32, prefetch=1).run([r], realtime=False)[0]
         assert np.array_equal(alone.fid, rec.fid), r.rid
     torch.cuda.synchronize()
+
+
+def test_step_many_multi_lattice_tma_launch_equals_own_launches():
+    """Lattices on the TMA-fed one-step kernel (mid-size, gather form) advance
+    together in one multi-lattice launch per step: each lattice's states and
+    FID / population histories are bit-identical to its own lattice_step_n
+    run (the same work items and the same fixed-order reductions), whatever
+    lattices share the launch; and they match the FP64 oracle."""
+    from paper_2603_22553_b300 import binding as B
+    shapes = [((64, 96, 110), (1, 1, 1), 0), ((70, 70, 128), (1, 0, 1), 0), ((40, 100, 96), (0, 1, 0), 0),
+              ((30, 64, 200), (1, 1, 1), 1), ((36, 70, 130), (1, 1, 0), 1)]
+    cases = [lpc_inputs.random_case(sh, 610 + i, periodic=per, alpha=0.6, msd_axes=0, weight_dtype=wd)
+             for i, (sh, per, wd) in enumerate(shapes)]
+    steps = [23, 40, 17, 40, 9]
+
+    def make(c):
+        lat = Lattice.from_input(c)
+        lat.set_schedule(B.LPC_KERNEL_TB, 1)
+        lat.set_static_form(B.LPC_STATIC_GATHER)
+        return lat
+
+    mixed = [make(c) for c in cases]
+    step_many(mixed, steps)
+    res_mixed = [_read(l, 0) for l in mixed]
+    for l in mixed:
+        l.close()
+    # two other mixes: every lattice with one other, and in reverse order
+    for i, c in enumerate(cases):
+        ref = make(c)
+        ref.step(steps[i])
+        rr = _read(ref, 0)
+        ref.close()
+        for k in rr:
+            assert np.array_equal(rr[k], res_mixed[i][k]), (i, k)
+        j = (i + 1) % len(cases)
+        pair = [make(cases[j]), make(c)]
+        step_many(pair, [steps[j], steps[i]])
+        rp = _read(pair[1], 0)
+        for l in pair:
+            l.close()
+        for k in rr:
+            assert np.array_equal(rr[k], rp[k]), (i, k)
+        if i < 2:
+            o = H.oracle_run(c, steps[i], H.MODE_OF_DTYPE[c.weight_dtype], msd_axes=0)
+            g = dict(rr)
+            g["rho"] = rr["rho"].astype(np.float64)
+            H.compare(g, o, 0, tol=1e-5)

@@ -1,6 +1,6 @@
 """Host logic of the serving loop on the CPU (a fake engine, virtual clock):
-admission by footprint within the HBM budget, FIFO order, slot limit,
-every request finishes with the steps it asked for."""
+admission by footprint within the HBM budget, FIFO or least-work-first
+order, slot limit, every request finishes with the steps it asked for."""
 import numpy as np
 import pytest
 
@@ -137,3 +137,25 @@ def test_failed_creation_releases_every_lattice(prefetch):
         Server(eng, 10 ** 12, max_active=8, quantum=50, prefetch=prefetch).run(reqs, realtime=False)
     # resident lattices and those created after the failure were destroyed
     assert eng.order and not eng.live and eng.bytes == 0
+
+
+def test_sjf_admits_the_least_work_first_and_ages():
+    """policy="sjf": among the requests waiting at an admission, the one with
+    the least work (sites x steps) goes first; with max_wait_s a request that
+    waited that long goes before shorter ones.  Every request still runs its
+    steps, and the slot limit holds."""
+    reqs = [lpc_inputs.Request(i, 0.0, e, s, 100 + i) for i, (e, s) in
+            enumerate([(30, 900), (8, 20), (20, 100), (9, 10), (40, 500), (10, 30)])]
+    eng = FakeEngine()
+    recs = Server(eng, 1 << 40, max_active=1, quantum=50, prefetch=1, policy="sjf").run(reqs, realtime=False)
+    work = {r.rid: r.edge ** 3 * r.steps for r in reqs}
+    assert eng.order == sorted(work, key=lambda k: (work[k], k))
+    assert all(r.finish >= r.arrival for r in recs)
+    # aging: with a virtual clock advancing by the work done, the longest
+    # request (arrived first) passes the queue once it has waited max_wait_s
+    eng2 = FakeEngine()
+    Server(eng2, 1 << 40, max_active=1, quantum=50, prefetch=1, policy="sjf", max_wait_s=1e-8).run(
+        reqs, realtime=False)
+    assert eng2.order[0] == 3 and eng2.order[1] == 0     # at t = 0 nobody has waited; then rid 0 has
+    with pytest.raises(ValueError):
+        Server(eng, 1 << 40, policy="lifo")
