@@ -418,20 +418,32 @@ template <typename WT> __device__ __forceinline__ float wt_to_float(WT w);
 template <> __device__ __forceinline__ float wt_to_float<float>(float w) { return w; }
 template <> __device__ __forceinline__ float wt_to_float<__nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
 
-// Link form of the static data of a plain lattice (one jump factor, no
-// reservoir face): for every site y and axis a the link to y + e_a as one
-// signed value L (0: closed; L > 0: the hop y -> y + e_a weighs L and the hop
-// back A; L < 0: the hop y -> y + e_a weighs A and the hop back -L), A =
-// alpha/6 rounded like the hop weights (the weight of a downhill or level
-// Metropolis move, Eq. 1).  Read from the padded out-weights (ghost images and
-// walls included), so the weights the kernel rebuilds are the stored ones.
-// Rows of pitch Xs, ny + 1 rows per plane (row 0: the image of row ny - 1 on
-// a periodic y axis, else closed).  R is copied to rows of pitch Xs.  `bad`
-// is set when a link does not fit the form (an open link whose small hop
-// rounded to zero, or no hop equal to A); `a_out` receives A as a float.
+// Link form of the static data of a lattice with one jump factor: for every
+// site y and axis a the link to y + e_a as one signed value L (0: closed;
+// L > 0: the hop y -> y + e_a weighs L and the hop back A; L < 0: the hop
+// y -> y + e_a weighs A and the hop back -L), A = alpha/6 rounded like the
+// hop weights (the weight of a downhill or level Metropolis move, Eq. 1;
+// reservoir links follow the same rule).  Read from the padded out-weights
+// (ghost images, walls and reservoir ghosts included), so the weights the
+// kernel rebuilds are the stored ones.  Rows of pitch Xs, ny + 1 rows per
+// plane: row 0 holds the link that enters row 0 from below (from the image
+// of row ny - 1 on a periodic y axis, from the ghost row otherwise: a
+// reservoir's link, or closed at a wall).  X0 [nz][ny] holds the link that
+// enters column 0 from the left in the same way.  R is copied to rows of
+// pitch Xs.  `bad` is set when a link does not fit the form (an open link
+// whose small hop rounded to zero, or no hop equal to A); `a_out` receives A
+// as a float.
+__device__ __forceinline__ float link_value(float wf, float wb, float A, unsigned int* bad) {
+    if (wf == 0.0f && wb == 0.0f) return 0.0f;
+    if (wb == A && wf > 0.0f) return wf;
+    if (wf == A && wb > 0.0f) return -wb;
+    atomicOr(bad, 1u);
+    return 0.0f;
+}
+
 template <typename WT>
-__global__ void k_link_pack(LatticeView v, WT* __restrict__ L, float2* __restrict__ Rl, double alpha,
-                            unsigned int* __restrict__ bad, float* __restrict__ a_out) {
+__global__ void k_link_pack(LatticeView v, WT* __restrict__ L, WT* __restrict__ X0, float2* __restrict__ Rl,
+                            double alpha, unsigned int* __restrict__ bad, float* __restrict__ a_out) {
     const WT* W = static_cast<const WT*>(v.w);
     const float A = wt_to_float<WT>(round_weight<WT>(alpha / 6.0 * 1.0));
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -447,21 +459,31 @@ __global__ void k_link_pack(LatticeView v, WT* __restrict__ L, float2* __restric
         const int z = (int)(t2 % v.nz);
         const int a = (int)(t2 / v.nz);
         int y = row - 1;
-        if (row == 0) y = v.per_y ? v.ny - 1 : -1;
+        if (row == 0 && v.per_y) y = v.ny - 1;
         float val = 0.0f;
-        if (x < v.nx && y >= 0) {
+        // y = -1: the ghost row below row 0 (its weights: 0 at a wall, a
+        // reservoir's at a reservoir face); only y links start there
+        if (x < v.nx && (y >= 0 || a == 1)) {
             const long long p = z * zp + (long long)(y + v.G) * v.Xp + (x + v.G);
             const long long pn = a == 0 ? p + 1
                                  : a == 1 ? p + v.Xp
                                           : (long long)(z + 1 == v.nz ? 0 : z + 1) * zp + (p - z * zp);
             const float wf = ldw<WT>(W + (long long)(2 * a) * v.Np + p);
             const float wb = ldw<WT>(W + (long long)(2 * a + 1) * v.Np + pn);
-            if (wf == 0.0f && wb == 0.0f) val = 0.0f;
-            else if (wb == A && wf > 0.0f) val = wf;
-            else if (wf == A && wb > 0.0f) val = -wb;
-            else atomicOr(bad, 1u);
+            val = link_value(wf, wb, A, bad);
         }
         L[g] = round_weight<WT>((double)val);
+    }
+    // links entering column 0 from the left: from the ghost column (the image
+    // of column nx - 1 on a periodic x axis, a reservoir ghost, or a wall)
+    const long long nx0 = (long long)v.nz * v.ny;
+    for (long long g = gid; g < nx0; g += stride) {
+        const int y = (int)(g % v.ny);
+        const int z = (int)(g / v.ny);
+        const long long p = z * zp + (long long)(y + v.G) * v.Xp + (v.G - 1);
+        const float wf = ldw<WT>(W + p);
+        const float wb = ldw<WT>(W + v.Np + p + 1);
+        X0[g] = round_weight<WT>((double)link_value(wf, wb, A, bad));
     }
     const long long nr = (long long)v.nz * v.ny * v.Xs;
     for (long long g = gid; g < nr; g += stride) {
@@ -475,14 +497,16 @@ __global__ void k_link_pack(LatticeView v, WT* __restrict__ L, float2* __restric
 
 }  // namespace
 
-cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, float2* Rl, double alpha,
+cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, void* X0, float2* Rl, double alpha,
                              unsigned int* bad, float* a_out, cudaStream_t st) {
     const long long total = 3LL * v.nz * v.ny1 * v.Xs;
     const int g = grid_for(total, 256);
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_link_pack<__nv_bfloat16><<<g, 256, 0, st>>>(v, static_cast<__nv_bfloat16*>(L), Rl, alpha, bad, a_out);
+        k_link_pack<__nv_bfloat16><<<g, 256, 0, st>>>(v, static_cast<__nv_bfloat16*>(L),
+                                                      static_cast<__nv_bfloat16*>(X0), Rl, alpha, bad, a_out);
     else
-        k_link_pack<float><<<g, 256, 0, st>>>(v, static_cast<float*>(L), Rl, alpha, bad, a_out);
+        k_link_pack<float><<<g, 256, 0, st>>>(v, static_cast<float*>(L), static_cast<float*>(X0), Rl, alpha, bad,
+                                              a_out);
     return cudaGetLastError();
 }
 

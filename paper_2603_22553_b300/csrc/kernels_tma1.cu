@@ -127,8 +127,10 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
         off += up128(C * wb);
         L.R = off;
         if (!rho_only) off += up128(C * 8);
-        L.s = L.lab = off;
+        L.s = off;
         for (int n = 0; n < 3; ++n) L.dm[n] = off;
+        L.lab = off;
+        if (reg) off += up128(C);
         L.bytes2 = off;
         return L;
     }
@@ -175,7 +177,6 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     static_assert(!RHO || MSD == 0, "the rho-only step carries no moments");
     static_assert(!RHO || !REG, "the rho-only step takes no sums");
-    static_assert(!REG || !LNK, "lattices with regions keep the gather form");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (sa(smem_raw) & 127u)) & 127u);
     constexpr int NMSD = popc(MSD);
@@ -368,7 +369,13 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
             float lxe = 0.f, lxe1 = 0.f;                           // lane 0: this plane's and the next
             const WT* lnk = static_cast<const WT*>(v.lnk);
             const long long lplane = (long long)v.ny1 * v.Xs;     // one axis, one plane
-            const int xe = (x == 0 ? v.nx : x) - 1;                // lane 0: the column left of the tile
+            // lane 0: the +x link that ends in site 0, from the column left of
+            // the tile (at x = 0 the links that enter column 0 from the left)
+            const WT* lx0 = static_cast<const WT*>(v.lnk_x0);
+            auto left_link = [&](int zz) -> float {
+                return x == 0 ? ldw<WT>(lx0 + (long long)zz * v.ny + y)
+                              : ldw<WT>(lnk + (long long)zz * lplane + (long long)(y + 1) * v.Xs + x - 1);
+            };
             if (LNK) {
                 const int zb = h.za == 0 ? nz - 1 : h.za - 1;
                 const long long lb = (2LL * nz + zb) * lplane + (long long)(y + 1) * v.Xs + x;
@@ -377,8 +384,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                 zin = make_float2(link_fwd(lzb0, g.abig), link_fwd(lzb1, g.abig));
                 zout = make_float2(link_bwd(lzb0, g.abig), link_bwd(lzb1, g.abig));
                 if (lane == 0 && ok_y) {
-                    lxe = ldw<WT>(lnk + (long long)h.za * lplane + (long long)(y + 1) * v.Xs + xe);
-                    if (h.n > 1) lxe1 = ldw<WT>(lnk + (long long)(h.za + 1) * lplane + (long long)(y + 1) * v.Xs + xe);
+                    lxe = left_link(h.za);
+                    if (h.n > 1) lxe1 = left_link(h.za + 1);
                 }
             }
             // plane za-1: keep this lane's two columns as "below"
@@ -465,7 +472,7 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     zout = zb;
                     lxe = lxe1;
                     if (lane == 0 && ok_y && q + 2 < h.n)
-                        lxe1 = ldw<WT>(lnk + (long long)(z + 2) * lplane + (long long)(y + 1) * v.Xs + xe);
+                        lxe1 = left_link(z + 2);
                 } else {
                     const WT* win = reinterpret_cast<const WT*>(ss);
                     sp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(ss + SL.s) + os);
@@ -1128,7 +1135,7 @@ T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
     if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0, lnk);
-    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, nmsd, false);
+    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, lnk ? 0 : nmsd, lnk);
     return c;
 }
 
@@ -1138,6 +1145,11 @@ void* t1_kernel(int TY, int wdtype, int msd, bool rho_only = false, bool reg = f
                                  : (TY == 12 ? t1_rho_kernel<12, true>(wdtype) : t1_rho_kernel<8, true>(wdtype));
         return TY == 16 ? t1_rho_kernel<16, false>(wdtype)
                         : (TY == 12 ? t1_rho_kernel<12, false>(wdtype) : t1_rho_kernel<8, false>(wdtype));
+    }
+    if (reg && lnk) {
+        if (TY == 16) return t1_kernel_shape<16, true, true>(wdtype, msd);
+        if (TY == 12) return t1_kernel_shape<12, true, true>(wdtype, msd);
+        return t1_kernel_shape<8, true, true>(wdtype, msd);
     }
     if (reg) {
         if (TY == 16) return t1_kernel_shape<16, true, false>(wdtype, msd);
@@ -1160,10 +1172,11 @@ cudaError_t t1_prepare(int wdtype, int msd) {
     static bool done[2][8] = {};
     bool& d = done[wdtype == LPC_WEIGHTS_BF16][msd & 7];
     if (d) return cudaSuccess;
-    // per tile height: full step, rho-only step, with regions, link form, link-form rho-only step
-    for (int i = 0; i < 15; ++i) {
+    // per tile height: full step, rho-only step, with regions, link form, link-form rho-only step,
+    // link form with regions
+    for (int i = 0; i < 18; ++i) {
         const int mode = i / 3;
-        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, mode == 1 || mode == 4, mode == 2, mode >= 3);
+        void* fn = t1_kernel(kShapes[i % 3], wdtype, msd, mode == 1 || mode == 4, mode == 2 || mode == 5, mode >= 3);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, fn);
         if (e != cudaSuccess) return e;
@@ -1355,7 +1368,7 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
                         cudaStream_t st, bool rho_only) {
     if (!v.gwin && !v.lnk) return cudaErrorInvalidValue;
     const bool lnk = v.lnk != nullptr;
-    const bool reg = !rho_only && !lnk && t1_fused_regions(v, wdtype);
+    const bool reg = !rho_only && t1_fused_regions(v, wdtype);
     const T1Choice c = t1_choose(v, wdtype, rho_only, reg);
     const int nmsd = rho_only ? 0 : popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
@@ -1370,8 +1383,8 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.dm_src = (!rho_only && !lnk && v.gdm) ? 1 : 0;
     const int ndm = (reg || g.dm_src) ? nmsd : 0;
     g.abig = v.link_a;
-    if (lnk)   // three link boxes (one with the row above) and R
-        g.tx2 = c.TY * kTX * (3 * wb + (rho_only ? 0 : 8)) + kTX * wb;
+    if (lnk)   // three link boxes (one with the row above), R and the labels
+        g.tx2 = c.TY * kTX * (3 * wb + (rho_only ? 0 : 8) + (reg ? 1 : 0)) + kTX * wb;
     else
         g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
     t1_items(v, c.TY, &g.tiles_x, &g.tiles, &g.cz, &g.n_items);

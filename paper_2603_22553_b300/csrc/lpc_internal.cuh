@@ -60,6 +60,7 @@ struct LatticeView {
     // unless used: [3][nz][ny1][Xs] signed link weights (ny1 = ny + 1 rows,
     // row 0 the image of row ny - 1), R in gR; link_a: alpha/6 as stored
     const void* lnk;
+    const void* lnk_x0;              // [nz][ny] links entering column 0 from the left
     int ny1;
     float link_a;
     // reductions: per-block partials, completion counter, history
@@ -560,7 +561,7 @@ cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, floa
                                cudaStream_t st);
 // Link form of a plain lattice's static data (v.Xs, v.ny1 set); bad / a_out:
 // device words (a link that does not fit the form; alpha/6 as stored).
-cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, float2* Rl, double alpha,
+cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, void* X0, float2* Rl, double alpha,
                              unsigned int* bad, float* a_out, cudaStream_t st);
 cudaError_t launch_tb(const LatticeView& v, int wdtype, int K, const TBMaps& maps, unsigned int* err,
                       cudaStream_t st);

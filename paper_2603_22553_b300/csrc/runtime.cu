@@ -98,6 +98,7 @@ struct lpc_lattice {
     long long Ns = 0;
     // link form of the static data (plain lattices), instead of the gather form
     void* lnk = nullptr;
+    void* lnk_x0 = nullptr;             // inside the lnk block
     size_t lnk_bytes = 0;
     int ny1 = 0;
     float link_a = 0.0f;
@@ -197,7 +198,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     for (int a = 0; a < 3; ++a) { v.mu_in[a] = h->mu[in][a]; v.mu_out[a] = h->mu[in ^ 1][a]; }
     v.w = h->w; v.R = h->R;
     v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.Xs = h->Xs; v.Ns = h->Ns;
-    v.lnk = h->lnk; v.ny1 = h->ny1; v.link_a = h->link_a;
+    v.lnk = h->lnk; v.lnk_x0 = h->lnk_x0; v.ny1 = h->ny1; v.link_a = h->link_a;
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
     v.region = h->region; v.nreg = h->nreg; v.Xr = h->Xr;
@@ -297,9 +298,10 @@ bool gather_dm(const lpc_lattice* h) { return h->p.msd_axes && (h->nreg > 0 || h
 // 2048x256x256 slab with the x moment; the rule is kept as it is.
 constexpr long long kLinkFormSites = 3LL << 24;
 
-// The link form holds only lattices with one jump factor, no reservoir face
-// and no regions.
-bool link_form_possible(const lpc_lattice* h) { return !h->links_given && !h->rf.any() && h->nreg == 0; }
+// The link form holds the lattices with one jump factor (reservoir links take
+// it too); per-link factors break its rule that one hop of every open link
+// weighs alpha/6.
+bool link_form_possible(const lpc_lattice* h) { return !h->links_given; }
 
 lpc_status ensure_gather(lpc_lattice* h) {
     if (h->gwin || h->lnk) return LPC_OK;
@@ -311,8 +313,9 @@ lpc_status ensure_gather(lpc_lattice* h) {
          (h->static_pref == LPC_STATIC_AUTO && n_updated(h) >= kLinkFormSites && h->p.weight_dtype == LPC_WEIGHTS_F32));
     if (want_link) {
         const int ny1 = h->p.ny + 1;
-        const size_t lb = (size_t)3 * h->p.nz * ny1 * Xs * wbytes(h);
-        const size_t bytes = (lb + 255) / 256 * 256 + (size_t)Ns * 8;
+        const size_t lb = ((size_t)3 * h->p.nz * ny1 * Xs * wbytes(h) + 255) / 256 * 256;
+        const size_t x0b = ((size_t)h->p.nz * h->p.ny * wbytes(h) + 255) / 256 * 256;
+        const size_t bytes = lb + x0b + (size_t)Ns * 8;
         char* blk = (char*)dalloc(h, bytes);
         if (!blk && h->static_pref == LPC_STATIC_LINK) { set_error("link-form allocation failed"); return LPC_ERR_OOM; }
         if (blk) {
@@ -321,18 +324,20 @@ lpc_status ensure_gather(lpc_lattice* h) {
             LatticeView v = make_view(h, h->cur);
             v.Xs = Xs;
             v.ny1 = ny1;
-            float2* Rl = reinterpret_cast<float2*>(blk + (lb + 255) / 256 * 256);
+            void* X0 = blk + lb;
+            float2* Rl = reinterpret_cast<float2*>(blk + lb + x0b);
             unsigned int* bad = reinterpret_cast<unsigned int*>(h->scratch);
             float* a_out = reinterpret_cast<float*>(h->scratch) + 1;
             cudaError_t e = cudaMemsetAsync(bad, 0, 4, h->wstream);
             if (e == cudaSuccess)
-                e = launch_link_pack(v, h->p.weight_dtype, blk, Rl, h->p.alpha, bad, a_out, h->wstream);
+                e = launch_link_pack(v, h->p.weight_dtype, blk, X0, Rl, h->p.alpha, bad, a_out, h->wstream);
             unsigned int hb[2] = {1u, 0u};
             if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, h->wstream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
             if (e != cudaSuccess) { dfree(h, blk, bytes); return cuda_fail(e, "link pack"); }
             if (hb[0] == 0u) {
                 h->lnk = blk;
+                h->lnk_x0 = X0;
                 h->lnk_bytes = bytes;
                 h->gR = Rl;
                 h->Ns = Ns;
@@ -503,7 +508,7 @@ void drop_static(lpc_lattice* h) {
     if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
     if (h->lnk) dfree(h, h->lnk, h->lnk_bytes);
     h->gwin = nullptr; h->gs = nullptr; h->gR = nullptr; h->gdm = nullptr;
-    h->lnk = nullptr; h->lnk_bytes = 0; h->ny1 = 0; h->link_a = 0.0f;
+    h->lnk = nullptr; h->lnk_x0 = nullptr; h->lnk_bytes = 0; h->ny1 = 0; h->link_a = 0.0f;
     h->Xs = 0; h->Ns = 0;
     h->maps_K = 0;          // re-encode the tensor maps on the next launch
 }

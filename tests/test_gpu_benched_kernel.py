@@ -115,15 +115,81 @@ def test_static_form_switch_mid_run_keeps_the_trajectory():
 
 
 def test_link_form_rejected_where_it_cannot_hold_the_weights():
+    """Per-link jump factors break the form's rule (one hop of every open link
+    weighs alpha/6): the link form is refused, the gather form allowed."""
     from paper_2603_22553_b300.lattice import Lattice
     inp = lpc_inputs.random_case((8, 8, 70), 308, periodic=(0, 1, 1), alpha=0.6, msd_axes=0)
-    lab = lpc_inputs.random_regions(inp.F.shape, 309, 2)
-    lat = Lattice.from_input(inp, region=lab, n_regions=2)
+    links = np.random.default_rng(309).uniform(0.2, 1.0, (3,) + inp.F.shape)
+    lat = Lattice.from_input(inp, alpha_links=links)
     with pytest.raises(B.LPCError) as ei:
         lat.set_static_form(B.LPC_STATIC_LINK)
     assert ei.value.status == B.LPC_ERR_INVALID
     lat.set_static_form(B.LPC_STATIC_GATHER)      # allowed
     lat.close()
+
+
+RES_ALL = ((-0.75, 1.25, 0.5 - 0.25j), (0.5, 0.625, 1.0 + 0.0j), (0.25, 0.75, 0.0j), (-1.5, 2.0, 0.0j),
+           (-0.25, 1.5, 0.75 + 0.5j), (0.75, 0.5, 0.25 - 0.5j))
+
+
+# (nz, ny, nx), periodic (x, y, z), reservoir faces, regions, MSD axes, weight type
+RES_REG_CASES = [
+    ((20, 36, 130), (0, 0, 1), (0, 1, 3), 3, 5, 0),        # x and y reservoirs, regions, MSD x and z
+    ((24, 40, 128), (0, 1, 0), (0, 1, 4, 5), 3, 1, 1),     # x and z reservoirs, BF16, MSD x
+    ((16, 48, 96), (1, 0, 1), (2,), 0, 2, 0),              # a lower y reservoir only, no regions
+    ((18, 33, 70), (0, 1, 1), (1,), 2, 1, 0),              # an upper x reservoir only (lower x face a wall)
+]
+
+
+@pytest.mark.parametrize("shape,periodic,faces,nreg,msd,wdt", RES_REG_CASES)
+def test_link_form_with_reservoirs_and_regions(shape, periodic, faces, nreg, msd, wdt):
+    """Reservoir links follow the Metropolis rule too (one hop weighs alpha/6),
+    so the link form holds lattices with reservoir faces; the links entering
+    column 0 and row 0 come from the ghost sites.  Regions stage their labels
+    beside the links.  States bit-identical to the gather form, sums to FP32
+    summation order (the link form attributes MSD increments to the source
+    site, as the region and reservoir sums need), and against the oracle."""
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case(shape, 340 + len(faces), periodic=periodic, alpha=0.8, msd_axes=msd,
+                                 weight_dtype=wdt)
+    inp.reservoirs = tuple(RES_ALL[f] if f in faces else None for f in range(6))
+    kw = {}
+    lab = None
+    if nreg:
+        lab = lpc_inputs.random_regions(shape, 350, nreg)
+        kw = dict(region=lab, n_regions=nreg)
+    steps = 120
+    out = {}
+    for form in (B.LPC_STATIC_LINK, B.LPC_STATIC_GATHER):
+        lat = Lattice.from_input(inp, **kw)
+        lat.set_schedule(B.LPC_KERNEL_TB, 1)
+        lat.set_static_form(form)
+        assert lat.info()["static_form"] == FORM_CODE[form]
+        lat.step(steps)
+        r = dict(rho=lat.density(), m=lat.magnetization(), M=lat.fid(), P=lat.population())
+        for a in range(3):
+            if msd >> a & 1:
+                r["mu%d" % a] = lat.moment(a)
+                r["msd%d" % a] = lat.msd(a)
+        for g in range(nreg):
+            r["Mr%d" % g] = lat.fid_region(g)
+            r["Pr%d" % g] = lat.population_region(g)
+        out[form] = r
+        lat.close()
+    a, b = out[B.LPC_STATIC_LINK], out[B.LPC_STATIC_GATHER]
+    for k in a:
+        if k in ("rho", "m") or k.startswith("mu"):
+            assert np.array_equal(a[k], b[k]), k
+        else:
+            assert np.allclose(a[k], b[k], rtol=1e-5, atol=1e-6 * abs(b["P"][0])), k
+    pk = oracle.pack_input(inp, H.MODE_OF_DTYPE[wdt])
+    o = oracle.run(pk, inp.uniform_rho0(), steps, msd_axes=msd, region=lab, n_regions=nreg)
+    g = dict(a)
+    g["rho"] = a["rho"].astype(np.float64)
+    H.compare(g, o, msd, tol=1e-5)
+    for r in range(nreg):
+        assert H.rel_l2(a["Mr%d" % r], o.Mr[r]) <= 1e-5
+        assert H.rel_l2(a["Pr%d" % r], o.Pr[r]) <= 1e-5
 
 
 def test_monolith_384_link_form_whole_lattice_against_the_oracle():
