@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS) + ["serving_stream"])
     ap.add_argument("--block", type=int, default=64, help="lattice steps per bench step")
     ap.add_argument("--schedule", default="auto", help="auto | step1 | tb:K")
+    ap.add_argument("--static-form", default="auto", choices=["auto", "gather", "link"],
+                    help="static data of the TMA-fed one-step kernel")
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slabs"],
                     help="under torchrun: an independent lattice per rank (weak scaling) or one lattice cut "
                          "into one z slab per rank with halo exchange (strong scaling)")
@@ -329,9 +331,12 @@ def run_ours(args):
     ghost = (sched[1] + 1) // 2 * 2 if sched and sched[0] == B.LPC_KERNEL_TB else 0
 
     rkw = region_kwargs(wl, inp)
+    form = {"auto": B.LPC_STATIC_AUTO, "gather": B.LPC_STATIC_GATHER, "link": B.LPC_STATIC_LINK}[args.static_form]
     lat = Lattice.from_input(inp, ghost=ghost, **rkw)
     if sched:
         lat.set_schedule(*sched)
+    if form != B.LPC_STATIC_AUTO:
+        lat.set_static_form(form)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         lat.step(args.block)
@@ -425,6 +430,8 @@ def run_ours(args):
                       reservoirs=inp.reservoirs, **rkw)
         if sched:
             lat.set_schedule(*sched)
+        if form != B.LPC_STATIC_AUTO:
+            lat.set_static_form(form)
         for _ in range(args.steps):
             lat.step(args.block)
         M = lat.fid()

@@ -352,7 +352,8 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
  *                      level Metropolis move of weight alpha/6 (Eq. 1), so
  *                      one number gives both; the kernel rebuilds in-, out-
  *                      and stay weights from it.  Needs one jump factor (no
- *                      per-link factors), no reservoir face and no regions;
+ *                      per-link factors); reservoir links follow the same
+ *                      rule, and region labels are read beside the links;
  *   LPC_STATIC_AUTO    the default: the link form for FP32 lattices of at
  *                      least 3 * 2^24 sites that allow it, else the gather
  *                      form.
@@ -360,7 +361,7 @@ lpc_status lattice_set_schedule(lpc_lattice* h, int32_t kernel, int32_t block_st
  * schedule is the TMA-fed one-step kernel the chosen form is made during this
  * call (synchronously), else on that kernel's first launch.  Errors:
  * LPC_ERR_INVALID (NULL handle, unknown form, LPC_STATIC_LINK for a lattice
- * that does not allow it), LPC_ERR_OOM, LPC_ERR_CUDA.
+ * with per-link jump factors), LPC_ERR_OOM, LPC_ERR_CUDA.
  */
 lpc_status lattice_set_static_form(lpc_lattice* h, int32_t form);
 

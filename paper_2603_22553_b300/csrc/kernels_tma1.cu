@@ -733,9 +733,12 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
 // Many lattices in one launch (serving): the work queue holds the items of
 // every lattice of the launch, each lattice with its own tensor maps, view
 // and item split (the split of its own launch), so a lattice's states and
-// per-item sums are those of its own launch of k_step_tma1, and its final
-// fixed-order reduction (items_reduce, by the last CTA, lattice by lattice)
-// gives its sums bit for bit.  Lattices of one launch share the weight type,
+// per-item sums are those of its own launch of k_step_tma1.  The warp that
+// stores a lattice's last item (counted in the lattice's completion word)
+// reduces that lattice's items with the arithmetic of its own launch's final
+// reduction (items_reduce_warp), so its sums are bit for bit those of its own
+// launch, and the reductions of different lattices overlap the remaining
+// items instead of waiting for the end of the launch.  Lattices of one launch share the weight type,
 // the tile height and the ghost width; the full step without moments, in
 // the gather form (the form of the mid-size lattices that serving holds).
 
@@ -750,7 +753,6 @@ struct T1MultiParams {
     int count, total_items;
     int W, S1, S2, slot1, slot2, tx1, tx2;
     unsigned int* work;                 // launch work queue (zeroed before the launch)
-    unsigned int* done;                 // CTAs finished (zeroed by the last one)
 };
 static_assert(sizeof(T1MultiParams) <= 32000, "kernel parameter space");
 
@@ -1013,11 +1015,22 @@ k_step_tma1_multi(const __grid_constant__ T1MultiParams P) {
                     for (int w = 0; w < NC; ++w) sum += ired[(b * NC + w) * KSP + lane];
                     const int item = ((h.za - v.zlo) / T.cz) * T.tiles + h.tile;
                     v.partials[(long long)item * kNumSums + lane] = sum;
+                    __threadfence();
                 }
                 __syncwarp();
+                unsigned int done_items = 0u;
                 if (lane == 0) {
                     icount[b] = 0u;
                     mbar_arrive(&ifree[b]);
+                    done_items = atomicAdd(v.counter, 1u);     // the lattice's items stored so far
+                }
+                done_items = __shfl_sync(0xffffffffu, done_items, 0);
+                if (done_items == (unsigned)T.n_items - 1u) {
+                    // the lattice's last item: this warp reduces its items, in
+                    // the fixed order of the lattice's own launch
+                    __threadfence();
+                    items_reduce_warp<NC + 1>(v, T.n_items);
+                    if (lane == 0) *v.counter = 0u;
                 }
             }
             ++kitem;
@@ -1037,17 +1050,6 @@ k_step_tma1_multi(const __grid_constant__ T1MultiParams P) {
         __syncthreads();
         return;
     }
-    // the last CTA reduces every lattice's items in a fixed order, in the
-    // idle ring memory
-    __threadfence();
-    __shared__ unsigned int is_last;
-    __syncthreads();
-    if (tid == 0) is_last = (atomicAdd(P.done, 1u) == gridDim.x - 1u);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int L = 0; L < P.count; ++L) items_reduce<NC + 1>(P.lat[L].v, P.lat[L].n_items, reinterpret_cast<double*>(ring1));
-    if (tid == 0) *P.done = 0u;
 }
 
 template <typename WT, int NC>
@@ -1343,7 +1345,6 @@ cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* map
     P.count = count;
     P.total_items = total;
     P.work = words;
-    P.done = words + 1;
     static bool attr_done[2][3] = {};
     bool& ad = attr_done[wb == 2][c.TY == 16 ? 0 : (c.TY == 12 ? 1 : 2)];
     void* fn = t1_multi_kernel(c.TY, wdtype);
@@ -1356,7 +1357,7 @@ cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* map
         if (e != cudaSuccess) return e;
         ad = true;
     }
-    cudaError_t e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     int grid = device_props().sm_count;
     if (grid > total) grid = total;

@@ -324,13 +324,6 @@ __device__ void block_finish_smem(const LatticeView& v, int levels, double* smem
     }
 }
 
-// Final reduction of per-item FP64 sums v.partials[item * kNumSums + q]
-// written by the blocks of a work-queue kernel: the last block to finish sums
-// the items in a fixed order (thread t adds items t, t + T, ... in order into
-// scratch[q][t], then warp q adds the T values lane-strided and by an FP64
-// butterfly), so the result does not depend on which block took which item,
-// and writes the history entries of one step at *v.step.  `scratch` is
-// shared memory for kNumSums * blockDim doubles (free at this point).
 // The fixed-order reduction of items_finish, run by every thread of one
 // block: the items' FP64 partials into the history entries of one step at
 // *v.step (thread t adds items t, t + T, ... in order into scratch[q][t];
@@ -365,6 +358,40 @@ __device__ void items_reduce(const LatticeView& v, int n_items, double* scratch)
     }
     __syncthreads();
     if (tid == 0) *v.step = n + 1;
+}
+
+// The arithmetic of items_reduce<NW> carried out by one warp, without a
+// block-wide barrier: lane l plays the threads t = l, l + 32, ... of a block
+// of T = NW * 32 threads (each adds its items t, t + T, ... in order), adds
+// their sums in increasing t (the lane-strided second stage of
+// items_reduce), and the warp ends with the same FP64 butterfly.  The same
+// additions in the same order give the same history entries.
+template <int NW>
+__device__ void items_reduce_warp(const LatticeView& v, int n_items) {
+    const int T = NW * 32;
+    const int lane = threadIdx.x & 31;
+    double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int t = lane; t < T; t += 32) {
+        double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int b = t; b < n_items; b += T) {
+            const double* p = v.partials + (long long)b * kNumSums;
+#pragma unroll
+            for (int q = 0; q < kNumSums; ++q) acc[q] += __ldcg(p + q);
+        }
+#pragma unroll
+        for (int q = 0; q < kNumSums; ++q) s[q] += acc[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kNumSums; ++q) s[q] = warp_sum_f64(s[q]);
+    if (lane == 0) {
+        const long long n = *v.step;
+        v.histM[n + 1].x = s[0];
+        v.histM[n + 1].y = s[1];
+        v.histP[n + 1] = s[2];
+        for (int q = 3; q < kNumSums; ++q)
+            if (n >= 0 && (v.msd_axes >> (q - 3) & 1)) v.histD[(long long)(q - 3) * v.cap + n] = s[q];
+        *v.step = n + 1;
+    }
 }
 
 // Final reduction of per-item FP64 sums v.partials[item * kNumSums + q]
