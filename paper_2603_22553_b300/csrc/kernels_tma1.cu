@@ -803,6 +803,13 @@ k_step_tma1_multi(const __grid_constant__ T1MultiParams P) {
     if (warp == NC) {
         // ---------------- producer: one elected lane takes items of any lattice
         if (lane == 0) {
+            for (int L = 0; L < P.count; ++L) {          // every lattice's descriptors
+                prefetch_tmap(&P.lat[L].rho);
+                prefetch_tmap(&P.lat[L].m);
+                prefetch_tmap(&P.lat[L].gwin);
+                prefetch_tmap(&P.lat[L].gs);
+                prefetch_tmap(&P.lat[L].gR);
+            }
             bool ok = true;
             Cursor c1{0, 0u}, c2{0, 0u};
             unsigned int n1 = 0, n2 = 0;

@@ -81,6 +81,12 @@ __device__ __forceinline__ void tma4(void* dst, const CUtensorMap* map, uint64_t
         : "memory");
 }
 
+// Warm the tensor-map cache with a descriptor (a hint; kernel-parameter or
+// constant memory, generic address).
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 template <typename WT> __device__ __forceinline__ float lds_w(const WT* p);
 template <> __device__ __forceinline__ float lds_w<float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float lds_w<__nv_bfloat16>(const __nv_bfloat16* p) {
