@@ -110,6 +110,8 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
                     help="admission order of the served pass (the comparator runs in arrival order)")
+    ap.add_argument("--serve-mode", default="streams", choices=["streams", "batched"],
+                    help="served lattices on their own streams, or in multi-lattice / batched launches")
     return ap.parse_args()
 
 
@@ -582,6 +584,9 @@ def run_serving(args):
     ``--serve-step-scale`` so that both passes fit in a few minutes.  Fields
     are generated before the timed passes.
     """
+    # more hardware work queues than the default 8, so that the streams of
+    # the resident lattices do not alias (read when CUDA initialises)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     from paper_2603_22553_b300 import binding as B
@@ -598,7 +603,7 @@ def run_serving(args):
         def lattice_input(self, req):
             return cache[req.rid]
 
-    eng = CachedEngine(keep_fid=True)
+    eng = CachedEngine(keep_fid=True, mode=args.serve_mode)
     budget = int(args.serve_budget_gb * (1 << 30))
     warm = [lpc_inputs.Request(10 ** 6 + i, 0.0, 24, 20, 7) for i in range(2)]
     for w in warm:
@@ -624,7 +629,8 @@ def run_serving(args):
             "config": {"workload": "serving_stream", "requests": len(reqs),
                        "step_scale": args.serve_step_scale, "slots": args.serve_slots,
                        "quantum": args.serve_quantum, "hbm_budget_gb": args.serve_budget_gb,
-                       "policy": args.serve_policy},
+                       "policy": args.serve_policy, "mode": args.serve_mode,
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")},
             "served": s_batch, "one_at_a_time": s_seq,
             "speedup_vs_one_at_a_time": s_batch["aggregate_site_updates_per_s"] / s_seq["aggregate_site_updates_per_s"],
             "fid_same_as_one_at_a_time_1e-5": bool(same),

@@ -104,16 +104,17 @@ def test_served_results_equal_alone_and_oracle():
     torch.cuda.synchronize()
 
 
-def test_served_tma_lattices_equal_alone():
+@pytest.mark.parametrize("mode", ["streams", "batched"])
+def test_served_tma_lattices_equal_alone(mode):
     """Requests large enough for the one-step TMA kernel are served side by
-    side, each on its own stream; every FID is bit-identical to the request
-    served alone."""
+    side, each on its own stream or together in multi-lattice launches; every
+    FID is bit-identical to the request served alone."""
     import torch
     from paper_2603_22553_b300.serve import GpuEngine, Server
 
     reqs = lpc_inputs.request_stream(n=6, seed=45, edge_lo=102, edge_hi=124, steps_lo=40,
                                      steps_hi=150, rate_per_s=1000.0)
-    eng = GpuEngine()
+    eng = GpuEngine(mode=mode)
     recs = Server(eng, 16 << 30, max_active=4, quantum=32, prefetch=2).run(reqs, realtime=True)
     for r, rec in zip(sorted(reqs, key=lambda q: q.arrival_s), recs):
         alone = Server(eng, 16 << 30, max_active=1, quantum=32, prefetch=1).run([r], realtime=False)[0]
