@@ -92,7 +92,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="monolith_512", choices=sorted(WORKLOADS) + ["serving_stream"])
+    ap.add_argument("--workload", default="monolith_512",
+                    choices=sorted(WORKLOADS) + ["serving_stream", "serving_mix_mid", "serving_mix_small"])
     ap.add_argument("--block", type=int, default=64, help="lattice steps per bench step")
     ap.add_argument("--schedule", default="auto", help="auto | step1 | tb:K")
     ap.add_argument("--static-form", default="auto", choices=["auto", "gather", "link"],
@@ -265,6 +266,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-lattice workloads; "
+                          "%s is a serving workload" % args.workload}), flush=True)
+        return 0
     wl = WORKLOADS[args.workload]
     inp = wl["make"]()
     sub = sub_lattice(inp, wl["sub"])
@@ -575,6 +580,68 @@ def run_slabs(args):
     return 0
 
 
+MIXES = {"serving_mix_mid": [104, 112, 120, 128, 136, 144, 152, 160, 168, 176, 184, 192],
+         "serving_mix_small": list(range(24, 101, 4))}
+
+
+def run_mix(args):
+    """Resident particle lattices of the serving recipe (edges of the mix,
+    FP32), advanced ``--block`` steps per bench step either on their own
+    streams (``--serve-mode streams``: graphs of one-step launches, queued
+    before any wait) or together (``batched``: lattice_step_many, the
+    multi-lattice TMA launch for the mid-size ones, the batched
+    register-pipelined kernel for the small ones)."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+
+    from paper_2603_22553_b300 import binding as B
+    from paper_2603_22553_b300.lattice import Lattice, step_many
+
+    torch.cuda.set_device(0)
+    B.load()
+    edges = MIXES[args.workload]
+    lats = []
+    for i, e in enumerate(edges):
+        inp = lpc_inputs.Request(7000 + i, 0.0, e, args.block, 7000 + i).lattice()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            lat = Lattice.from_input(inp, stream=s.cuda_stream)
+        lat._stream = s
+        lats.append(lat)
+    sites = sum(e ** 3 for e in edges)
+
+    def one():
+        if args.serve_mode == "batched":
+            step_many(lats, [args.block] * len(lats))
+        else:
+            for lat in lats:
+                lat.step(args.block)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    clk = clocks.stop()
+    for lat in lats:
+        lat.close()
+    line = {"metric": "site-updates/s", "value": sites * args.block * args.steps / t, "unit": "site-updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "edges": edges, "sites": sites,
+                       "lattice_steps_per_step": args.block, "mode": args.serve_mode,
+                       "timing": "host clock around the device work, synchronised on both sides"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Served stream: continuous batching vs one-at-a-time plain solves.
 
@@ -645,6 +712,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving_stream":
         return run_serving(args)
+    if args.workload in MIXES:
+        return run_mix(args)
     if args.decomp == "slabs":
         return run_slabs(args)
     return run_ours(args)
