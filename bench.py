@@ -40,6 +40,10 @@ WORKLOADS = {
     "monolith_384": dict(make=lambda: lpc_inputs.monolith(edge=384, msd_axes=0),
                          desc="384^3 porous monolith (the 512^3 recipe at 0.42 of the sites, for "
                               "profiling), FP32 state and hop weights", sub=64),
+    "monolith_320": dict(make=lambda: lpc_inputs.monolith(edge=320, msd_axes=0),
+                         desc="320^3 porous monolith (the 512^3 recipe at a quarter of the sites, 4 GB on the "
+                              "device with the link form: the small case of the full ncu captures), FP32",
+                         sub=64),
     "monolith_512_bf16": dict(make=lambda: lpc_inputs.monolith(edge=512, msd_axes=0, weight_dtype=1),
                               desc="512^3 porous monolith, FP32 state, BF16 hop weights", sub=64),
     "particle_in_bath_256": dict(make=lambda: lpc_inputs.particle_in_bath(),
