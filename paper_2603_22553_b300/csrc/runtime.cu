@@ -609,13 +609,16 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
     for (int i = 0; i < 3; ++i)
         if (p->periodic[i] != 0 && p->periodic[i] != 1) { set_error("lattice_create: periodic flags must be 0 or 1"); return LPC_ERR_INVALID; }
     if (a && (!a->alloc || !a->free)) { set_error("lattice_create: allocator needs alloc and free"); return LPC_ERR_INVALID; }
-    if (!finite_all(F, solid, N, true)) { set_error("lattice_create: non-finite F on a pore site"); return LPC_ERR_INVALID; }
-    if (!finite_all(omega, solid, N, false)) { set_error("lattice_create: non-finite omega"); return LPC_ERR_INVALID; }
-    if (rho0 && !finite_all(rho0, solid, N, true)) { set_error("lattice_create: non-finite rho0 on a pore site"); return LPC_ERR_INVALID; }
-    if (alpha_links && !all_of_parallel(3 * N, [=](long long i) { return alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0; })) {
-        set_error("lattice_create_links: link factors must be in [0, 1]");
-        return LPC_ERR_INVALID;
-    }
+    // the checks that read every input value: finite F and rho0 on pore
+    // sites, finite omega, link factors in [0, 1]
+    auto check_values = [=]() -> const char* {
+        if (!finite_all(F, solid, N, true)) return "lattice_create: non-finite F on a pore site";
+        if (!finite_all(omega, solid, N, false)) return "lattice_create: non-finite omega";
+        if (rho0 && !finite_all(rho0, solid, N, true)) return "lattice_create: non-finite rho0 on a pore site";
+        if (alpha_links && !all_of_parallel(3 * N, [=](long long i) { return alpha_links[i] >= 0.0 && alpha_links[i] <= 1.0; }))
+            return "lattice_create_links: link factors must be in [0, 1]";
+        return nullptr;
+    };
     if (o.reserved != 0) { set_error("lattice_create_ex: reserved option fields must be 0"); return LPC_ERR_INVALID; }
     ResFaces rf{};
     for (int f = 0; f < 6; ++f) {
@@ -653,7 +656,29 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
             return LPC_ERR_INVALID;
         }
     }
-    if (mode == kWhole && rf.any_z()) return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
+    if (mode == kWhole && rf.any_z()) {
+        // the extended fields are checked by the call that takes them
+        const char* bad = check_values();
+        if (bad) { set_error(bad); return LPC_ERR_INVALID; }
+        return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
+    }
+    // Small lattices are checked before any device work.  A large lattice's
+    // values are checked on host threads while its inputs upload and pack
+    // (the scan reads gigabytes and costs as much as the upload and the pack
+    // together); a failure then releases everything made so far and returns
+    // LPC_ERR_INVALID, as an early check would.
+    struct Checker {
+        std::thread th;
+        const char* bad = nullptr;
+        ~Checker() { if (th.joinable()) th.join(); }
+        const char* result() { if (th.joinable()) th.join(); return bad; }
+    } checker;
+    if (N < (1LL << 22)) {
+        checker.bad = check_values();
+        if (checker.bad) { set_error(checker.bad); return LPC_ERR_INVALID; }
+    } else {
+        checker.th = std::thread([&checker, check_values] { checker.bad = check_values(); });
+    }
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
     if (!h) { set_error("lattice_create: host allocation failed"); return LPC_ERR_OOM; }
@@ -758,6 +783,11 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
     }
     dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
     dfree(h, dA, (size_t)N * 24);
+    if (const char* bad = checker.result()) {
+        release_all(h); delete h;
+        set_error(bad);
+        return LPC_ERR_INVALID;
+    }
     if (e != cudaSuccess || st != LPC_OK) {
         if (st == LPC_OK) st = cuda_fail(e, "lattice_create");
         release_all(h); delete h;

@@ -129,3 +129,40 @@ def test_bounded_wait_that_runs_out_reports_timeout(mode, expect):
     assert lib.lpc_wait_selftest(3, 100, stream) == B.LPC_ERR_INVALID
     assert lib.lpc_wait_selftest(0, 0, stream) == B.LPC_ERR_INVALID
     assert lib.lpc_wait_selftest(0, 5_000_000_000, stream) == B.LPC_ERR_INVALID
+
+
+@pytest.mark.parametrize("field", ["F", "omega", "rho0", "links"])
+def test_large_lattice_input_checks_run_beside_the_upload(field):
+    """Lattices of 2^22 sites or more check their values on host threads while
+    the inputs upload and pack: a bad value still returns LPC_ERR_INVALID,
+    no handle, and the device memory taken meanwhile is given back."""
+    import torch
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case((64, 256, 260), 61, periodic=(1, 1, 1), alpha=0.6, msd_axes=0)
+    assert inp.n_sites >= 1 << 22
+    kw = {}
+    pore = np.flatnonzero(inp.solid.reshape(-1) == 0)
+    F, om = inp.F.copy(), inp.omega.copy()
+    if field == "F":
+        F.reshape(-1)[pore[-3]] = np.nan
+    elif field == "omega":
+        om.reshape(-1)[7] = np.inf
+    elif field == "rho0":
+        r0 = np.ones(inp.n_sites)
+        r0[pore[1000]] = np.nan
+        kw["rho0"] = r0
+    else:
+        links = np.full((3,) + inp.F.shape, 0.5)
+        links.reshape(-1)[12345] = 1.5
+        kw["alpha_links"] = links
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    with pytest.raises(B.LPCError) as ei:
+        Lattice(inp.nx, inp.ny, inp.nz, F, om, inp.solid, periodic=inp.periodic, alpha=inp.alpha, **kw)
+    assert ei.value.status == B.LPC_ERR_INVALID
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    ok = Lattice.from_input(inp)
+    ok.step(3)
+    assert ok.steps_done == 3
+    ok.close()
