@@ -6,7 +6,7 @@ every step compared, not sampled sites).
   Parseval its relative error equals the FID's) and the final densities,
   against the FP64 oracle on the same FP32 weights.
 * Supercapacitor slab, 2048 x 256 x 256 (BF16 weights, first moment along
-  x, walls in x): the first 120 of its 5000 steps in the oracle's matched
+  x, walls in x): the first 100 of its 5000 steps in the oracle's matched
   BF16 mode: the density profile along x (sum over y and z), MSD_x, the FID
   and the whole density field.  The oracle's 6.7e10 site updates of the
   first 500 steps take about ten minutes on the host, longer than the whole
@@ -60,7 +60,7 @@ def test_particle_in_bath_256_first_1000_steps_whole_lattice():
 def test_supercapacitor_2048x256x256_whole_lattice_matched_bf16():
     from paper_2603_22553_b300.lattice import Lattice
     inp = lpc_inputs.supercapacitor()
-    steps = 500 if os.environ.get("LPC_FULL_PARITY") == "1" else 120
+    steps = 500 if os.environ.get("LPC_FULL_PARITY") == "1" else 100
     lat = Lattice.from_input(inp)
     lat.step(steps)
     M, P = lat.fid(), lat.population()
