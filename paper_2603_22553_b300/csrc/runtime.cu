@@ -1093,19 +1093,15 @@ lpc_status lattice_step_many(lpc_lattice* const* hs, const int64_t* n, int32_t c
     // lattices with steps left (sorted by step count, so they form a prefix)
     {
         std::vector<int> order = multi;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            const int ga = t1_multi_group(make_view(hs[a], hs[a]->cur), hs[a]->p.weight_dtype);
-            const int gb = t1_multi_group(make_view(hs[b], hs[b]->cur), hs[b]->p.weight_dtype);
-            return ga != gb ? ga < gb : n[a] > n[b];
-        });
+        std::vector<int> key(count, 0);
+        for (int i : multi) key[i] = t1_multi_group(make_view(hs[i], hs[i]->cur), hs[i]->p.weight_dtype);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return key[a] != key[b] ? key[a] < key[b] : n[a] > n[b]; });
         static thread_local std::vector<LatticeView> views;
         static thread_local std::vector<const TBMaps*> mps;
         for (size_t g0 = 0; g0 < order.size() && status == LPC_OK;) {
-            const int grp = t1_multi_group(make_view(hs[order[g0]], hs[order[g0]]->cur), hs[order[g0]]->p.weight_dtype);
             size_t g1 = g0;
-            while (g1 < order.size() &&
-                   t1_multi_group(make_view(hs[order[g1]], hs[order[g1]]->cur), hs[order[g1]]->p.weight_dtype) == grp)
-                ++g1;
+            while (g1 < order.size() && key[order[g1]] == key[order[g0]]) ++g1;
             const int wd = hs[order[g0]]->p.weight_dtype;
             for (size_t c0 = g0; c0 < g1 && status == LPC_OK; c0 += kMaxMulti) {
                 const size_t c1 = std::min(g1, c0 + (size_t)kMaxMulti);
