@@ -83,6 +83,10 @@ __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double
     const int y = unpad_coord(py, v.G, v.ny, v.per_y);
     double w[6] = {0, 0, 0, 0, 0, 0};
     float2 rot = make_float2(1.0f, 0.0f);
+    // FP64 divisions are slow on this part: alpha / 6 once per thread, and no
+    // division by kT = 1 (both give the same values as dividing every time)
+    const double a6 = alpha / 6.0;
+    const bool unit_kT = kT == 1.0;
     if (x >= 0 && y >= 0) {
         const long long i = ((long long)z * v.ny + y) * v.nx + x;
         if (!solid[i]) {
@@ -92,13 +96,16 @@ __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double
                 if (j < 0) {
                     // out through a face: +a hops leave by side 1, -a hops by side 0
                     const int f = 2 * (k >> 1) + ((k & 1) ? 0 : 1);
-                    if (k < 4 && rf.on[f]) w[k] = alpha / 6.0 * metropolis((rf.F[f] - F[i]) / kT);
+                    if (k < 4 && rf.on[f]) {
+                        const double d = rf.F[f] - F[i];
+                        w[k] = a6 * metropolis(unit_kT ? d : d / kT);
+                    }
                     continue;
                 }
                 if (solid[j]) continue;
-                const double dE = (F[j] - F[i]) / kT;
-                const double a_link = links ? links[(long long)(k >> 1) * N + ((k & 1) ? j : i)] : alpha;
-                w[k] = a_link / 6.0 * metropolis(dE);
+                const double d = F[j] - F[i];
+                const double dE = unit_kT ? d : d / kT;
+                w[k] = (links ? links[(long long)(k >> 1) * N + ((k & 1) ? j : i)] / 6.0 : a6) * metropolis(dE);
             }
         }
         double s, c;
@@ -109,7 +116,8 @@ __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double
         const int f = reservoir_ghost(v, rf, px, py, x, y, bx, by, k);
         if (f >= 0) {
             const long long i = ((long long)z * v.ny + by) * v.nx + bx;
-            if (!solid[i]) w[k] = alpha / 6.0 * metropolis((F[i] - rf.F[f]) / kT);
+            const double d = F[i] - rf.F[f];
+            if (!solid[i]) w[k] = a6 * metropolis(unit_kT ? d : d / kT);
         }
     }
 #pragma unroll
