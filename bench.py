@@ -154,6 +154,14 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def physical_gpu(dev):
+    """nvidia-smi index of torch device ``dev`` (CUDA_VISIBLE_DEVICES maps them)."""
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if dev < len(vis) and vis[dev].strip().isdigit():
+        return int(vis[dev])
+    return dev
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -355,8 +363,7 @@ def run_ours(args):
     info = lat.info()          # after the first launches: the static form is made by then
     if ws > 1:
         dist.barrier()
-    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(dev)).split(",")[0])
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else dev)
+    clocks = ClockSampler(physical_gpu(dev))
     clocks.start()
     time.sleep(0.3)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -529,7 +536,7 @@ def run_slabs(args):
     info = slab.lattice.info()
     if ws > 1:
         dist.barrier()
-    clocks = ClockSampler(dev)
+    clocks = ClockSampler(physical_gpu(dev))
     clocks.start()
     time.sleep(0.3)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -624,7 +631,7 @@ def run_mix(args):
     for _ in range(args.warmup):
         one()
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(physical_gpu(torch.cuda.current_device()))
     clocks.start()
     time.sleep(0.3)
     t0 = time.perf_counter()
@@ -681,14 +688,14 @@ def run_serving(args):
         cache[w.rid] = w.lattice()
     Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum, policy=args.serve_policy).run(warm)
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(physical_gpu(torch.cuda.current_device()))
     clocks.start()
     recs = Server(eng, budget, max_active=args.serve_slots, quantum=args.serve_quantum,
                   policy=args.serve_policy).run(reqs)
     torch.cuda.synchronize()
     clk_served = clocks.stop()
     s_batch = summary(recs)
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(physical_gpu(torch.cuda.current_device()))
     clocks.start()
     seq = serve_sequential(eng, reqs)
     clk_seq = clocks.stop()
