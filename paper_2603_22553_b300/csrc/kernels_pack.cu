@@ -330,6 +330,40 @@ cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const
     return cudaGetLastError();
 }
 
+namespace {
+
+// The value checks of create on the device copies (bit 0: F not finite on a
+// pore site, 1: omega not finite, 2: rho0 not finite on a pore site, 3: a
+// link factor outside [0, 1]), or-ed into *bits.
+__global__ void k_check_inputs(const double* __restrict__ F, const double* __restrict__ omega,
+                               const uint8_t* __restrict__ solid, const double* __restrict__ rho0,
+                               const double* __restrict__ links, long long N, unsigned int* bits) {
+    unsigned int b = 0u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const bool pore = solid[i] == 0;
+        if (pore && !isfinite(F[i])) b |= 1u;
+        if (!isfinite(omega[i])) b |= 2u;
+        if (rho0 && pore && !isfinite(rho0[i])) b |= 4u;
+        if (links)
+            for (int a = 0; a < 3; ++a) {
+                const double l = links[a * N + i];
+                if (!(l >= 0.0 && l <= 1.0)) b |= 8u;
+            }
+    }
+    b = __reduce_or_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && b) atomicOr(bits, b);
+}
+
+}  // namespace
+
+cudaError_t launch_check_inputs(const double* F, const double* omega, const uint8_t* solid, const double* rho0,
+                                const double* links, long long N, unsigned int* bits, cudaStream_t st) {
+    const int B = 256;
+    k_check_inputs<<<grid_for(N, B), B, 0, st>>>(F, omega, solid, rho0, links, N, bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reservoir_ghosts(const LatticeView& v, const ResFaces& rf, cudaStream_t st) {
     if (!rf.any()) return cudaSuccess;
     const int B = 256;

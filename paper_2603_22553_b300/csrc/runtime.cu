@@ -51,6 +51,13 @@ namespace lpc {
 // Both state buffers from the current rho: rho copied, m = rho, mu = 0
 // (v: input = the current buffer); in kernels_pack.cu.
 cudaError_t launch_restart(const LatticeView& v, cudaStream_t st);
+// The value checks of create on the uploaded copies (F and rho0 finite on
+// pore sites, omega finite, link factors in [0, 1]), or-ed as bits 0..3 into
+// *bits (zeroed before); in kernels_pack.cu.
+cudaError_t launch_check_inputs(const double* F, const double* omega, const uint8_t* solid, const double* rho0,
+                                const double* links, long long N, unsigned int* bits, cudaStream_t st);
+// Counter-block word of the input checks.
+constexpr int kInputCheckWord = 30;
 }  // namespace lpc
 
 using namespace lpc;
@@ -662,22 +669,15 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
         if (bad) { set_error(bad); return LPC_ERR_INVALID; }
         return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
     }
-    // Small lattices are checked before any device work.  A large lattice's
-    // values are checked on host threads while its inputs upload and pack
-    // (the scan reads gigabytes and costs as much as the upload and the pack
-    // together); a failure then releases everything made so far and returns
-    // LPC_ERR_INVALID, as an early check would.
-    struct Checker {
-        std::thread th;
-        const char* bad = nullptr;
-        ~Checker() { if (th.joinable()) th.join(); }
-        const char* result() { if (th.joinable()) th.join(); return bad; }
-    } checker;
-    if (N < (1LL << 22)) {
-        checker.bad = check_values();
-        if (checker.bad) { set_error(checker.bad); return LPC_ERR_INVALID; }
-    } else {
-        checker.th = std::thread([&checker, check_values] { checker.bad = check_values(); });
+    // Small lattices are checked on the host before any device work.  A large
+    // lattice's values are checked on the device, in its uploaded copies (a
+    // host scan of gigabytes cost as much as the upload and the pack
+    // together); a failure releases everything made so far and returns
+    // LPC_ERR_INVALID, as the host check does.
+    const bool device_check = N >= (1LL << 22);
+    if (!device_check) {
+        const char* bad = check_values();
+        if (bad) { set_error(bad); return LPC_ERR_INVALID; }
     }
 
     lpc_lattice* h = new (std::nothrow) lpc_lattice();
@@ -767,6 +767,8 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
                                       (size_t)p->ny * p->nz, cudaMemcpyHostToDevice, h->wstream);
         }
         // the byte mask is stored as given; solid means nonzero
+        if (e == cudaSuccess && device_check)
+            e = launch_check_inputs(dF, dO, h->solid, dR0, dA, N, h->counter + kInputCheckWord, h->wstream);
         if (e == cudaSuccess) st = ensure_history(h, 1024);
         if (e == cudaSuccess && st == LPC_OK) {
             LatticeView v = make_view(h, 1);   // writes go to buffer 0
@@ -783,10 +785,18 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
     }
     dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
     dfree(h, dA, (size_t)N * 24);
-    if (const char* bad = checker.result()) {
-        release_all(h); delete h;
-        set_error(bad);
-        return LPC_ERR_INVALID;
+    if (e == cudaSuccess && st == LPC_OK && device_check) {
+        unsigned int bits = 0;
+        e = cudaMemcpy(&bits, h->counter + kInputCheckWord, 4, cudaMemcpyDeviceToHost);
+        const char* bad = (bits & 1u) ? "lattice_create: non-finite F on a pore site"
+                        : (bits & 2u) ? "lattice_create: non-finite omega"
+                        : (bits & 4u) ? "lattice_create: non-finite rho0 on a pore site"
+                        : (bits & 8u) ? "lattice_create_links: link factors must be in [0, 1]" : nullptr;
+        if (e == cudaSuccess && bad) {
+            release_all(h); delete h;
+            set_error(bad);
+            return LPC_ERR_INVALID;
+        }
     }
     if (e != cudaSuccess || st != LPC_OK) {
         if (st == LPC_OK) st = cuda_fail(e, "lattice_create");

@@ -132,10 +132,11 @@ def test_bounded_wait_that_runs_out_reports_timeout(mode, expect):
 
 
 @pytest.mark.parametrize("field", ["F", "omega", "rho0", "links"])
-def test_large_lattice_input_checks_run_beside_the_upload(field):
-    """Lattices of 2^22 sites or more check their values on host threads while
-    the inputs upload and pack: a bad value still returns LPC_ERR_INVALID,
-    no handle, and the device memory taken meanwhile is given back."""
+def test_large_lattice_input_checks_on_the_device(field):
+    """Lattices of 2^22 sites or more check their values on the device, in the
+    uploaded copies (a host scan of gigabytes costs as much as the upload): a
+    bad value still returns LPC_ERR_INVALID, no handle, and the device memory
+    taken meanwhile is given back."""
     import torch
     from paper_2603_22553_b300.lattice import Lattice
     inp = lpc_inputs.random_case((64, 256, 260), 61, periodic=(1, 1, 1), alpha=0.6, msd_axes=0)
