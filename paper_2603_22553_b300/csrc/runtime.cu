@@ -663,12 +663,8 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
             return LPC_ERR_INVALID;
         }
     }
-    if (mode == kWhole && rf.any_z()) {
-        // the extended fields are checked by the call that takes them
-        const char* bad = check_values();
-        if (bad) { set_error(bad); return LPC_ERR_INVALID; }
-        return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
-    }
+    // the extended fields of a z reservoir are checked by the call that takes them
+    if (mode == kWhole && rf.any_z()) return create_with_z_halos(p, o, F, omega, solid, rho0, a, stream, out);
     // Small lattices are checked on the host before any device work.  A large
     // lattice's values are checked on the device, in its uploaded copies (a
     // host scan of gigabytes cost as much as the upload and the pack
