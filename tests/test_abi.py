@@ -196,3 +196,39 @@ def test_wait_selftest_rejects_bad_arguments_on_host(lib):
     assert lib.lpc_wait_selftest(0, 0, None) == B.LPC_ERR_INVALID
     assert lib.lpc_wait_selftest(1, 4_000_000_001, None) == B.LPC_ERR_INVALID
     assert b"budget" in lib.lpc_last_error()
+
+
+def _create_slab(lib, p, halo=1, opts=None, rho0=None):
+    N = p.nx * p.ny * (p.nz + 2)
+    z = np.zeros(N)
+    h = ctypes.c_void_p()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.lattice_create_slab(ctypes.byref(p), halo, ctypes.byref(opts) if opts is not None else None, dp(z),
+                                 dp(z), np.zeros(N, np.uint8).ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                 dp(rho0) if rho0 is not None else None, None, None, ctypes.byref(h))
+    return st, h
+
+
+def test_slab_arguments_rejected_on_host(lib):
+    """Slab misuse is rejected before any device work: a halo other than one
+    plane, region labels, a Boltzmann start without rho0, a z reservoir, and
+    plane queries on a NULL handle."""
+    st, h = _create_slab(lib, _params(), halo=2)
+    assert st == B.LPC_ERR_INVALID and not h.value and b"halo" in lib.lpc_last_error()
+    opts = B.lpc_options()
+    lab = np.zeros(4 * 4 * 6, np.uint8)
+    opts.region = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    opts.n_regions = 1
+    st, h = _create_slab(lib, _params(), opts=opts)
+    assert st == B.LPC_ERR_INVALID and b"region" in lib.lpc_last_error()
+    st, h = _create_slab(lib, _params(init=1))
+    assert st == B.LPC_ERR_INVALID and b"rho0" in lib.lpc_last_error()
+    opts = B.lpc_options()
+    opts.reservoir[4] = B.lpc_reservoir(1, 0, 0.0, 1.0, 1.0, 0.0)
+    st, h = _create_slab(lib, _params(periodic=(1, 1, 0)), opts=opts)
+    assert st == B.LPC_ERR_INVALID and b"halo planes" in lib.lpc_last_error()
+    ps = B.lpc_plane_set()
+    assert lib.lattice_slab_planes(None, 0, ctypes.byref(ps)) == B.LPC_ERR_INVALID
+    assert lib.lattice_set_tiling(None, 16, 40) == B.LPC_ERR_INVALID
+    out = np.zeros(4)
+    assert lib.lattice_dmsd(None, 0, 0, 1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == B.LPC_ERR_INVALID
