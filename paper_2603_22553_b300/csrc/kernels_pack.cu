@@ -380,10 +380,15 @@ namespace {
 // z-1, z+1 for k = 0..5; ghosts hold the periodic images, zero behind
 // walls; z wraps, the hop across a z wall being zero), the stay weight with
 // the same FP32 sum as the step kernels, R, and the out-weight pair of every
-// MSD axis.  Positions x >= nx of the unpadded pitch get zeros.
+// MSD axis.  With gdx the x pairs are not stored: the x out-weights of a site
+// are the in-weights of its x neighbours, which the kernel holds, except at
+// the two ends of a 64-column tile, whose values gdx keeps
+// ([nz][tiles_x][nyp][2], nyp = ny rounded up to 8 so that rows are 16-byte
+// multiples: w_-x of the tile's first column, w_+x of its last site).
+// Positions x >= nx of the unpadded pitch get zeros.
 template <typename WT>
 __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __restrict__ gs,
-                              float2* __restrict__ gR, WT* __restrict__ gdm) {
+                              float2* __restrict__ gR, WT* __restrict__ gdm, WT* __restrict__ gdx) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= v.Ns) return;
     const int x = (int)(g % v.Xs);
@@ -415,11 +420,19 @@ __global__ void k_gather_pack(LatticeView v, WT* __restrict__ win, float* __rest
     gs[g] = stay_weight(wo);
     gR[g] = v.R[p];
     for (int a = 0; a < 3; ++a)
-        if (gdm && (v.msd_axes >> a & 1)) {
+        if (gdm && (v.msd_axes >> a & 1) && !(a == 0 && gdx)) {
             // the stored out-weights themselves (exact in their own type)
             gdm[2 * (a * v.Ns + g)] = W[(2 * a) * v.Np + p];
             gdm[2 * (a * v.Ns + g) + 1] = W[(2 * a + 1) * v.Np + p];
         }
+    if (gdx && x % 64 == 0) {
+        const int tiles_x = (v.nx + 63) / 64;
+        const int nyp = (v.ny + 7) / 8 * 8;
+        const int xl = min(x + 63, v.nx - 1);      // the tile's last site
+        const long long e = 2 * (((long long)z * tiles_x + x / 64) * nyp + y);
+        gdx[e] = W[1 * v.Np + p];
+        gdx[e + 1] = W[0 * v.Np + p + (xl - x)];
+    }
 }
 
 }  // namespace
@@ -555,15 +568,17 @@ cudaError_t launch_link_pack(const LatticeView& v, int wdtype, void* L, void* X0
 // Pitch of the gather-form arrays: rows start on 256-byte boundaries.
 int gather_pitch(int nx) { return (nx + 63) / 64 * 64; }
 
-cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm, void* dx,
                                cudaStream_t st) {
     const int B = 256;
     const long long g = (v.Ns + B - 1) / B;
     if (wdtype == LPC_WEIGHTS_BF16)
         k_gather_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, static_cast<__nv_bfloat16*>(win), s, R,
-                                                                static_cast<__nv_bfloat16*>(dm));
+                                                                static_cast<__nv_bfloat16*>(dm),
+                                                                static_cast<__nv_bfloat16*>(dx));
     else
-        k_gather_pack<float><<<(unsigned)g, B, 0, st>>>(v, static_cast<float*>(win), s, R, static_cast<float*>(dm));
+        k_gather_pack<float><<<(unsigned)g, B, 0, st>>>(v, static_cast<float*>(win), s, R, static_cast<float*>(dm),
+                                                        static_cast<float*>(dx));
     return cudaGetLastError();
 }
 

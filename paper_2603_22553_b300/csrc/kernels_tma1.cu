@@ -94,19 +94,30 @@ namespace {
 
 // state slot:  rho [TY+2][W] f32 | m [TY+2][W] f32x2 | mu_n [TY+2][W] f32
 // static slot, gather form: win [6][TY][64] WT | s [TY][64] f32 | R [TY][64] f32x2
-//              | dm_n [TY][64] WTx2 | lab [TY][64] u8 (region labels, with regions only)
+//              | dm_n [TY][64] WTx2 (pairs of MSD axes y, z) | dx [TY] WTx2 (x out-weights
+//              at the tile's ends) | lab [TY][64] u8 (region labels, with regions only)
 // static slot, link form:   lx [TY][64] WT | ly [TY+1][64] WT (the row above too) | lz [TY][64] WT
 //              | R [TY][64] f32x2
 // (each part on a 128-byte boundary, as TMA requires)
 struct T1Slots {
     int m, mu[3], bytes1;
-    int s, R, dm[3], lab, bytes2;
+    int s, R, dm[3], dx, lab, bytes2;
     int lx, ly, lz;
 };
 __host__ __device__ inline int up128(int n) { return (n + 127) / 128 * 128; }
-// ndm: MSD axes whose out-weight pairs are staged (source-attributed MSD sums)
-__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm,
-                                            bool lnk = false) {
+// MSD sums over source sites (regions, reservoir faces: src) take every
+// site's out-weights of each MSD axis.  Those of x come from the x
+// neighbours' in-weights, which the gather holds, and from the tile-edge
+// array; those of y and z are staged as pairs.  Returned: the bitmask, over
+// the index n of the MSD axes in order, of the staged pairs.
+__host__ __device__ inline int t1_dm_staged(int msd, bool src) {
+    if (!src) return 0;
+    const int nmsd = (msd & 1) + ((msd >> 1) & 1) + ((msd >> 2) & 1);
+    return ((1 << nmsd) - 1) & ~(msd & 1);
+}
+// dmn: t1_dm_staged; dmx: the tile-edge x out-weights are staged
+__host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, bool rho_only, bool reg, int dmn,
+                                            bool dmx, bool lnk = false) {
     T1Slots L;
     const int H = TY + 2;
     int off = up128(H * W * 4);
@@ -129,6 +140,7 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
         if (!rho_only) off += up128(C * 8);
         L.s = off;
         for (int n = 0; n < 3; ++n) L.dm[n] = off;
+        L.dx = off;
         L.lab = off;
         if (reg) off += up128(C);
         L.bytes2 = off;
@@ -142,8 +154,10 @@ __host__ __device__ inline T1Slots t1_slots(int W, int TY, int nmsd, int wb, boo
     if (!rho_only) off += up128(C * 8);
     for (int n = 0; n < 3; ++n) {
         L.dm[n] = off;
-        if (n < ndm) off += up128(C * 2 * wb);
+        if (dmn >> n & 1) off += up128(C * 2 * wb);
     }
+    L.dx = off;
+    if (dmx) off += up128(TY * 2 * wb);
     L.lab = off;
     if (reg) off += up128(C);
     L.bytes2 = off;
@@ -185,11 +199,14 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
     static_assert(KS <= 32, "one lane per item sum");
     const int W = g.W, S1 = g.S1, S2 = g.S2;
     // MSD increments: summed over the source sites with their out-weights
-    // (staged pairs) where regions or reservoir faces need that attribution,
-    // else over the destination sites with the in-weights and source states
-    // the gather already holds (the same total, without the pair traffic)
-    const int ndm = LNK ? 0 : ((REG || g.dm_src) ? NMSD : 0);
-    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG, ndm, LNK);
+    // where regions or reservoir faces need that attribution (x from the
+    // neighbours' in-weights and the tile-edge values, y and z from staged
+    // pairs), else over the destination sites with the in-weights and source
+    // states the gather already holds (the same total, without the pairs)
+    const bool src_msd = !LNK && (REG || g.dm_src);
+    const int dmn = t1_dm_staged(MSD, src_msd);
+    const bool dmx = src_msd && (MSD & 1);
+    const T1Slots SL = t1_slots(W, TY, NMSD, (int)sizeof(WT), RHO, REG, dmn, dmx, LNK);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * g.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * g.slot2);
@@ -295,7 +312,8 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                         if (!RHO) tma3(st + SL.R, &maps.gR, fb, 2 * sx, sy, z);
 #pragma unroll
                         for (int m = 0; m < NMSD; ++m)
-                            if (ndm) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
+                            if (dmn >> m & 1) tma4(st + SL.dm[m], &maps.gdm, fb, 2 * sx, sy, z, axis_of[m]);
+                        if (dmx) tma3(st + SL.dx, &maps.gdx, fb, 2 * sy, tx, z);
                         if (REG) tma3(st + SL.lab, &maps.glab, fb, sx, sy, z);
                         *issued2 = ++n2;
                         c2.next(S2);
@@ -550,7 +568,24 @@ k_step_tma1(const __grid_constant__ TBMaps maps, LatticeView v, T1Geom g) {
                     if (LNK) {
                         dd0[n] = site_dmsd(lwo0, muc[n].x, q0.rc, a);
                         dd1[n] = site_dmsd(lwo1, muc[n].y, q1.rc, a);
-                    } else if (ndm) {
+                    } else if (dmx && n == 0) {
+                        // x out-weights: w_+x(x) = win_+x(x + 1), w_-x(x) = win_-x(x - 1),
+                        // from the lane's own pair and its neighbours' by shuffles; the
+                        // tile's first column and last site from the tile-edge values
+                        const float2 ex = lds_w2<WT>(reinterpret_cast<const WT*>(ss + SL.dx) + 2 * warp);
+                        const float up = __shfl_up_sync(0xffffffffu, win2[1].y, 1);
+                        const float dn = __shfl_down_sync(0xffffffffu, win2[0].x, 1);
+                        const int last = min(kTX - 1, v.nx - 1 - tx * kTX);   // the tile's last site
+                        const bool end0 = lane == (last >> 1) && !(last & 1);
+                        const bool end1 = lane == (last >> 1) && (last & 1);
+                        float wo0[6], wo1[6];
+                        wo0[0] = end0 ? ex.y : win2[0].y;
+                        wo0[1] = lane == 0 ? ex.x : up;
+                        wo1[0] = end1 ? ex.y : dn;
+                        wo1[1] = win2[1].x;
+                        dd0[n] = site_dmsd(wo0, muc[n].x, q0.rc, 0);
+                        dd1[n] = site_dmsd(wo1, muc[n].y, q1.rc, 0);
+                    } else if (dmn >> n & 1) {
                         const float4 dm = lds_w4<WT>(reinterpret_cast<const WT*>(ss + SL.dm[n]) + 2 * os);
                         float wo0[6], wo1[6];
                         wo0[2 * a] = dm.x; wo0[2 * a + 1] = dm.y;
@@ -764,7 +799,7 @@ k_step_tma1_multi(const __grid_constant__ T1MultiParams P) {
     constexpr int TY = NC;
     constexpr int KSP = 8;
     const int W = P.W, S1 = P.S1, S2 = P.S2;
-    const T1Slots SL = t1_slots(W, TY, 0, (int)sizeof(WT), false, false, 0, false);
+    const T1Slots SL = t1_slots(W, TY, 0, (int)sizeof(WT), false, false, 0, false, false);
     unsigned char* ring1 = smem;
     unsigned char* ring2 = smem + (size_t)S1 * P.slot1;
     uint64_t* full1 = reinterpret_cast<uint64_t*>(ring2 + (size_t)S2 * P.slot2);
@@ -1108,8 +1143,8 @@ int t1_box_width(int G) { return (kTX + 2 * G + 3) / 4 * 4; }
 // Ring depth d and shared memory of a tile height: S1 = d + 2 state slots
 // (centre and above held), S2 = d + 1 static slots (centre held); per slot one
 // full and one empty barrier, and a header per state slot.
-void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, int ndm, bool lnk) {
-    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg, ndm, lnk);
+void t1_rings(T1Choice& c, int TY, int nmsd, int wb, bool rho_only, bool reg, int dmn, bool dmx, bool lnk) {
+    const T1Slots L = t1_slots(c.W, TY, nmsd, wb, rho_only, reg, dmn, dmx, lnk);
     const int ksp = reg ? ItemSums<true>::KSP : ItemSums<false>::KSP;
     const int fixed = 128 + 3 * 8 + 2 * TY * ksp * 8 + 64;   // slack, item barriers/counts/sums, flags
     const int budget = device_props().max_smem_optin - 1024 - fixed;
@@ -1131,20 +1166,22 @@ T1Choice t1_choose(const LatticeView& v, int wdtype, bool rho_only = false, bool
     const int nmsd = popc(v.msd_axes);
     const int wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
     const bool lnk = v.lnk != nullptr;         // the lattice's static data is in link form
-    const int ndm = (!lnk && v.gdm) ? nmsd : 0;  // pairs staged where the lattice keeps them
+    // pairs staged where the lattice keeps them (source-attributed MSD sums)
+    const int dmn = t1_dm_staged(v.msd_axes, !lnk && v.gdm);
+    const bool dmx = !lnk && v.gdm && (v.msd_axes & 1);
     T1Choice c{};
     c.W = t1_box_width(v.G);
     bool chosen = false;
     if (v.t1_ty == 8 || v.t1_ty == 12 || v.t1_ty == 16) {       // set by the caller or the autotuner
-        t1_rings(c, v.t1_ty, nmsd, wb, false, false, ndm, lnk);
+        t1_rings(c, v.t1_ty, nmsd, wb, false, false, dmn, dmx, lnk);
         chosen = c.depth >= 1;
     }
     for (int i = 0; i < 3 && !chosen; ++i) {
-        t1_rings(c, kShapes[i], nmsd, wb, false, false, ndm, lnk);
+        t1_rings(c, kShapes[i], nmsd, wb, false, false, dmn, dmx, lnk);
         if ((c.depth >= LPC_T1_MIN_DEPTH && v.ny > kShapes[i] / 2) || i == 2) break;
     }
-    if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0, lnk);
-    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, lnk ? 0 : nmsd, lnk);
+    if (rho_only) t1_rings(c, c.TY, 0, wb, true, false, 0, false, lnk);
+    else if (reg) t1_rings(c, c.TY, nmsd, wb, false, true, t1_dm_staged(v.msd_axes, !lnk), !lnk && (v.msd_axes & 1), lnk);
     return c;
 }
 
@@ -1298,6 +1335,14 @@ bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps) {
             const cuuint32_t bd[4] = {(cuuint32_t)(2 * kTX), TY, 1, 1};
             ok = ok && tma_encode(&maps->gdm, dt, 4, v.gdm, dd, sd, bd);
         }
+        if (v.gdx) {
+            // tile-edge x out-weights [nz][tiles_x][nyp][2]: a box of the TY rows of one tile
+            const cuuint64_t nyp = (cuuint64_t)((v.ny + 7) / 8 * 8), ntx = (cuuint64_t)((v.nx + kTX - 1) / kTX);
+            const cuuint64_t dx[3] = {2 * nyp, ntx, nz};
+            const cuuint64_t sx[2] = {2 * nyp * e, 2 * nyp * ntx * e};
+            const cuuint32_t bx[3] = {2 * TY, 1, 1};
+            ok = ok && tma_encode(&maps->gdx, dt, 3, v.gdx, dx, sx, bx);
+        }
         if (v.region && v.Xr == v.Xs) {
             const cuuint64_t dl[3] = {Xs, ny, nz};
             const cuuint64_t sl[2] = {Xs, Xs * ny};
@@ -1389,12 +1434,14 @@ cudaError_t launch_tma1(const LatticeView& v, int wdtype, const TBMaps& maps, un
     g.slot2 = c.L.bytes2;
     g.tx1 = (c.TY + 2) * c.W * (rho_only ? 4 : 12 + 4 * nmsd);
     g.dm_src = (!rho_only && !lnk && v.gdm) ? 1 : 0;
-    const int ndm = (reg || g.dm_src) ? nmsd : 0;
+    const int dmn = t1_dm_staged(v.msd_axes & (rho_only ? 0 : 7), !rho_only && !lnk && (reg || g.dm_src));
+    const bool dmx = !rho_only && !lnk && (reg || g.dm_src) && (v.msd_axes & 1);
     g.abig = v.link_a;
     if (lnk)   // three link boxes (one with the row above), R and the labels
         g.tx2 = c.TY * kTX * (3 * wb + (rho_only ? 0 : 8) + (reg ? 1 : 0)) + kTX * wb;
     else
-        g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * ndm) + (reg ? 1 : 0));
+        g.tx2 = c.TY * kTX * (6 * wb + 4 + (rho_only ? 0 : 8 + 2 * wb * popc(dmn)) + (reg ? 1 : 0)) +
+                (dmx ? c.TY * 2 * wb : 0);
     t1_items(v, c.TY, &g.tiles_x, &g.tiles, &g.cz, &g.n_items);
     const int sms = device_props().sm_count;
     if (g.n_items > t1_max_items()) return cudaErrorInvalidConfiguration;

@@ -53,7 +53,11 @@ struct LatticeView {
     const void* gwin;                // [6][Ns] in-weights win_k(x) = w_k(x - e_k), float or bf16
     const float* gs;                 // [Ns] stay weight 1 - sum_k w_k(x)
     const float2* gR;                // [Ns] rotation
-    const void* gdm;                 // [3][Ns][2] (w_+a(x), w_-a(x)) for the MSD axes, float or bf16
+    const void* gdm;                 // [3][Ns][2] (w_+a(x), w_-a(x)) for the MSD axes y, z, float or bf16
+    // with the x pairs: [nz][tiles_x][nyp][2] (nyp = ny rounded up to 8) the x out-weights at the edges
+    // of each 64-column tile, (w_-x of its first column, w_+x of its last
+    // site); the other x out-weights are the in-weights of the neighbours
+    const void* gdx;
     int Xs;
     long long Ns;
     // link form of the static data (plain lattices; one-step TMA kernel), null
@@ -584,7 +588,7 @@ cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* map
                               unsigned int* words, cudaStream_t st);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);
 int gather_pitch(int nx);
-cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm,
+cudaError_t launch_gather_pack(const LatticeView& v, int wdtype, void* win, float* s, float2* R, void* dm, void* dx,
                                cudaStream_t st);
 // Link form of a plain lattice's static data (v.Xs, v.ny1 set); bad / a_out:
 // device words (a link that does not fit the form; alpha/6 as stored).

@@ -101,6 +101,7 @@ struct lpc_lattice {
     float* gs = nullptr;
     float2* gR = nullptr;
     void* gdm = nullptr;
+    void* gdx = nullptr;                // inside the gwin block
     int Xs = 0;
     long long Ns = 0;
     // link form of the static data (plain lattices), instead of the gather form
@@ -204,7 +205,7 @@ LatticeView make_view(lpc_lattice* h, int in) {
     v.rho_out = h->rho[in ^ 1]; v.m_out = h->m[in ^ 1];
     for (int a = 0; a < 3; ++a) { v.mu_in[a] = h->mu[in][a]; v.mu_out[a] = h->mu[in ^ 1][a]; }
     v.w = h->w; v.R = h->R;
-    v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.Xs = h->Xs; v.Ns = h->Ns;
+    v.gwin = h->gwin; v.gs = h->gs; v.gR = h->gR; v.gdm = h->gdm; v.gdx = h->gdx; v.Xs = h->Xs; v.Ns = h->Ns;
     v.lnk = h->lnk; v.lnk_x0 = h->lnk_x0; v.ny1 = h->ny1; v.link_a = h->link_a;
     v.partials = h->partials; v.counter = h->counter; v.step = h->dstep;
     v.histM = h->histM; v.histP = h->histP; v.histD = h->histD; v.cap = h->cap;
@@ -276,10 +277,17 @@ lpc_status ensure_history(lpc_lattice* h, long long needed) {
     return LPC_OK;
 }
 
+// Bytes of the x out-weights at the tile edges ([nz][tiles_x][nyp][2]).
+size_t gather_dx_bytes(const lpc_params& p) {
+    const size_t wb = p.weight_dtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    return ((size_t)p.nz * ((p.nx + 63) / 64) * ((p.ny + 7) / 8 * 8) * 2 * wb + 255) / 256 * 256;
+}
+
 // win (6 planes), s, R and, with any MSD axis, one (w+a, w-a) plane per axis
-size_t gather_bytes(long long Ns, int wdtype, int msd) {
-    const size_t wb = wdtype == LPC_WEIGHTS_BF16 ? 2 : 4;
-    return (size_t)Ns * (6 * wb + 4 + 8 + (msd ? 3 * 2 * wb : 0));
+// (the x pairs replaced by the tile-edge array)
+size_t gather_bytes(long long Ns, const lpc_params& p, int msd) {
+    const size_t wb = p.weight_dtype == LPC_WEIGHTS_BF16 ? 2 : 4;
+    return (size_t)Ns * (6 * wb + 4 + 8 + (msd ? 3 * 2 * wb : 0)) + ((msd & 1) ? gather_dx_bytes(p) : 0);
 }
 
 // The gather form keeps the MSD out-weight pairs only where the MSD sums are
@@ -359,7 +367,7 @@ lpc_status ensure_gather(lpc_lattice* h) {
             }
         }
     }
-    char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
+    char* blk = (char*)dalloc(h, gather_bytes(Ns, h->p, gather_dm(h) ? h->p.msd_axes : 0));
     if (!blk) { set_error("gather-form allocation failed"); return LPC_ERR_OOM; }
     h->Xs = Xs;
     h->Ns = Ns;
@@ -370,8 +378,10 @@ lpc_status ensure_gather(lpc_lattice* h) {
     h->gR = (float2*)blk;
     blk += (size_t)Ns * 8;
     h->gdm = gather_dm(h) ? (void*)blk : nullptr;       // [3][Ns][2] weights, indexed by axis
+    blk += gather_dm(h) ? (size_t)Ns * 3 * 2 * wbytes(h) : 0;
+    h->gdx = (gather_dm(h) && (h->p.msd_axes & 1)) ? (void*)blk : nullptr;
     LatticeView v = make_view(h, h->cur);
-    cudaError_t e = launch_gather_pack(v, h->p.weight_dtype, h->gwin, h->gs, h->gR, h->gdm, h->wstream);
+    cudaError_t e = launch_gather_pack(v, h->p.weight_dtype, h->gwin, h->gs, h->gR, h->gdm, h->gdx, h->wstream);
     if (e != cudaSuccess) return cuda_fail(e, "gather pack");
     return LPC_OK;
 }
@@ -512,9 +522,9 @@ void drop_static(lpc_lattice* h) {
     if (!h->gwin && !h->lnk) return;
     cudaStreamSynchronize(h->wstream);
     drop_graphs(h);
-    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
+    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p, gather_dm(h) ? h->p.msd_axes : 0));
     if (h->lnk) dfree(h, h->lnk, h->lnk_bytes);
-    h->gwin = nullptr; h->gs = nullptr; h->gR = nullptr; h->gdm = nullptr;
+    h->gwin = nullptr; h->gs = nullptr; h->gR = nullptr; h->gdm = nullptr; h->gdx = nullptr;
     h->lnk = nullptr; h->lnk_x0 = nullptr; h->lnk_bytes = 0; h->ny1 = 0; h->link_a = 0.0f;
     h->Xs = 0; h->Ns = 0;
     h->maps_K = 0;          // re-encode the tensor maps on the next launch
@@ -531,7 +541,7 @@ void release_all(lpc_lattice* h) {
     }
     dfree(h, h->w, Np * 6 * wbytes(h));
     dfree(h, h->R, Np * 8);
-    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p.weight_dtype, gather_dm(h) ? h->p.msd_axes : 0));
+    if (h->gwin) dfree(h, h->gwin, gather_bytes(h->Ns, h->p, gather_dm(h) ? h->p.msd_axes : 0));
     if (h->lnk) dfree(h, h->lnk, h->lnk_bytes);
     dfree(h, h->solid, (size_t)h->N);
     if (h->region) dfree(h, h->region, (size_t)h->Xr * h->p.ny * h->p.nz);
@@ -925,7 +935,7 @@ lpc_status lattice_footprint(const lpc_params* p, int64_t steps, int64_t* bytes)
     b += (long long)history_bytes(cap, 1);
     b += 16 * N;    // transient copies of F and omega during create
     if (p->nx >= 64 && p->ny >= 16 && N >= (1LL << 20))     // the automatic schedule's gather form
-        b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, p->weight_dtype, 0);
+        b += (long long)gather_bytes((long long)gather_pitch(p->nx) * p->ny * p->nz, *p, 0);
     *bytes = b;
     return LPC_OK;
 }

@@ -12,11 +12,11 @@ namespace lpc {
 
 // Tensor maps of one input buffer parity (kernel parameter, __grid_constant__).
 // w, R: padded hop-weight planes and rotation (multi-step kernel); gwin, gs,
-// gR, gdm: the gather-form static arrays (one-step kernel); glab: the region
+// gR, gdm, gdx: the gather-form static arrays (one-step kernel); glab: the region
 // labels (uint8, same rows as the gather form); glnk1, glnk2: the link form
 // (boxes of TY and TY + 1 rows).
 struct TBMaps {
-    CUtensorMap rho, m, mu[3], w, R, gwin, gs, gR, gdm, glab, glnk1, glnk2;
+    CUtensorMap rho, m, mu[3], w, R, gwin, gs, gR, gdm, gdx, glab, glnk1, glnk2;
 };
 
 bool tma_encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,

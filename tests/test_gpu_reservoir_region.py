@@ -270,6 +270,74 @@ def test_fused_region_sums_match_the_separate_pass(msd_axes, wdt):
         lat.close()
 
 
+RES_FACE = ((-0.75, 1.25, 0.5 - 0.25j), (0.5, 0.625, 1.0 + 0.0j), (0.25, 0.75, 0.0j), (-1.5, 2.0, 0.0j),
+            (-0.25, 1.5, 0.75 + 0.5j), (0.75, 0.5, 0.25 - 0.5j))
+
+# (nz, ny, nx), periodic (x, y, z), reservoir faces, regions, MSD axes, weight type
+SOURCE_SUM_CASES = [
+    ((12, 20, 97), (1, 1, 1), (), 3, 1, 0),           # periodic x; the last tile's last site is a lane's first
+    ((10, 18, 131), (0, 1, 1), (0, 1), 2, 5, 1),       # x reservoirs, BF16, a last tile of 3 sites, MSD x and z
+    ((10, 16, 64), (0, 0, 1), (0, 2), 0, 7, 0),        # reservoirs without regions, one full tile, every axis
+    ((9, 20, 33), (0, 1, 1), (0, 1), 0, 1, 0),         # a single tile of 33 sites between two reservoirs
+    ((8, 24, 100), (1, 0, 0), (2, 3, 4), 2, 3, 0),     # the last site is a lane's second; y and z reservoirs
+]
+
+
+@pytest.mark.parametrize("shape,periodic,faces,nreg,msd,wdt", SOURCE_SUM_CASES)
+def test_source_attributed_msd_sums_of_the_one_step_tma_kernel(shape, periodic, faces, nreg, msd, wdt):
+    """With regions or reservoir faces the MSD increments are summed over
+    source sites from their out-weights; the one-step TMA kernel takes the x
+    out-weights from the x neighbours' in-weights (the tile's two ends from a
+    small edge array) and stages those of y and z.  Ragged last tiles that end
+    on either site of a lane, periodic and reservoir x faces: states
+    bit-identical to the register-pipelined schedule (separate region pass,
+    out-weights read directly), totals and region sums equal to FP32
+    summation order, and against the FP64 oracle."""
+    from paper_2603_22553_b300 import binding as B
+    inp = lpc_inputs.random_case(shape, 360 + shape[2], periodic=periodic, solid_frac=0.2, alpha=0.8,
+                                 msd_axes=msd, weight_dtype=wdt)
+    inp.reservoirs = tuple(RES_FACE[f] if f in faces else None for f in range(6))
+    kw, lab = {}, None
+    if nreg:
+        lab = lpc_inputs.random_regions(shape, 361 + shape[2], nreg)
+        kw = dict(region=lab, n_regions=nreg)
+    steps = 50
+    tma = _lattice(inp, "tb1", **kw)
+    tma.set_static_form(B.LPC_STATIC_GATHER)
+    ref = _lattice(inp, "step1", **kw)
+    for lat in (tma, ref):
+        lat.step(steps)
+    info = tma.info()
+    assert info["kernel"] == B.LPC_KERNEL_TB and info["block_steps"] == 1 and info["static_form"] == 1
+    assert np.array_equal(tma.density(), ref.density()) and np.array_equal(tma.magnetization(), ref.magnetization())
+    P0 = ref.population()[0]
+    assert np.max(np.abs(tma.fid() - ref.fid())) <= 1e-6 * P0
+    for a in range(3):
+        if msd >> a & 1:
+            assert np.array_equal(tma.moment(a), ref.moment(a))
+            r = ref.msd(a)
+            assert np.max(np.abs(tma.msd(a)[1:] - r[1:])) <= 1e-5 * np.max(np.abs(r[1:])), a
+            for g in range(nreg):
+                rr = ref.msd_region(g, a)
+                assert np.max(np.abs(tma.msd_region(g, a) - rr)) <= 1e-5 * np.max(np.abs(rr)) + 1e-12, (g, a)
+    pk = oracle.pack_input(inp, H.MODE_OF_DTYPE[wdt])
+    o = oracle.run(pk, inp.uniform_rho0(), steps, msd_axes=msd, region=lab, n_regions=nreg)
+    g = _read(tma, msd)
+    _compare_fid_pop(g, o, 1e-5)
+    for a in range(3):
+        if msd >> a & 1:
+            assert np.max(np.abs(g["msd%d" % a][10:] / o.msd(a)[10:] - 1.0)) <= 1e-5, a
+    for r in range(nreg):
+        assert H.rel_l2(tma.fid_region(r), o.Mr[r]) <= 1e-5
+        for a in range(3):
+            if msd >> a & 1:
+                ms = tma.msd_region(r, a)
+                rr = np.concatenate([[0.0], np.cumsum(o.Dr[r, a])]) / o.P[0]
+                assert np.max(np.abs(ms[10:] - rr[10:])) <= 1e-5 * np.max(np.abs(rr[10:])), (r, a)
+    for lat in (tma, ref):
+        lat.close()
+
+
 def test_kohn_vacf_and_region_diffusion_parity():
     """Eq. 4 (Kohn route) from a Boltzmann start and the diffusion of the
     particles of each region, from the GPU's histories (downstream) against
