@@ -582,8 +582,9 @@ int t1_default_items_per_cta();
 constexpr int kMaxMulti = 24;
 bool t1_multi_member(const LatticeView& v, int wdtype);
 int t1_multi_group(const LatticeView& v, int wdtype);
-// maps[i]: the tensor maps of lattice i's current input buffer; words: two
-// device words (work queue, CTAs done), zeroed here before the launch.
+// maps[i]: the tensor maps of lattice i's current input buffer; words: the
+// launch's work-queue counter (one device word, zeroed here before the
+// launch); each lattice counts its stored items in its own counter word.
 cudaError_t launch_tma1_multi(const LatticeView* views, const TBMaps* const* maps, int count, int wdtype,
                               unsigned int* words, cudaStream_t st);
 bool t1_encode_maps(const LatticeView& v, int wdtype, TBMaps* maps);

@@ -4,7 +4,9 @@ every step compared, not sampled sites).
 * Particle in electrolyte bath, 256^3 (FP32): the first 1000 of its 10 000
   steps, the FID of every step and its spectrum (a plain DFT, Eq. 9; by
   Parseval its relative error equals the FID's) and the final densities,
-  against the FP64 oracle on the same FP32 weights.
+  against the FP64 oracle on the same FP32 weights.  The oracle takes about
+  three minutes of host time per 1000 steps; ``LPC_FULL_PARITY=1`` runs the
+  whole configured run of 10 000 steps (a 10 001-point spectrum).
 * Supercapacitor slab, 2048 x 256 x 256 (BF16 weights, first moment along
   x, walls in x): the first 100 of its 5000 steps in the oracle's matched
   BF16 mode: the density profile along x (sum over y and z), MSD_x, the FID
@@ -19,7 +21,8 @@ rounding (the 87 % of the bath that is uniform bulk electrolyte, F = 0: all
 weights alpha/6 and s_f32 - s = +4.9e-9) the bias does not average out, and
 populations drift by up to n 2^-25 relative after n steps (3.0e-5 at
 n = 1000); the other rounding errors are random and far smaller.  The bound
-is max(1e-5, n 2^-25).
+is max(1e-5, n 2^-25), and never above the 1e-4 that the method's results
+are held to.
 """
 import os
 
@@ -34,13 +37,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _tol(steps):
-    return max(1e-5, steps * 2.0 ** -25)
+    return min(1e-4, max(1e-5, steps * 2.0 ** -25))
 
 
-def test_particle_in_bath_256_first_1000_steps_whole_lattice():
+def test_particle_in_bath_256_whole_lattice():
     from paper_2603_22553_b300.lattice import Lattice
     inp = lpc_inputs.particle_in_bath()
-    steps = 1000
+    steps = 10000 if os.environ.get("LPC_FULL_PARITY") == "1" else 1000
     lat = Lattice.from_input(inp)
     lat.step(steps)
     M, P = lat.fid(), lat.population()
@@ -52,7 +55,7 @@ def test_particle_in_bath_256_first_1000_steps_whole_lattice():
     _, S_o = oracle.spectrum(o.M, inp.dt)
     e = {"fid": H.rel_l2(M, o.M), "spectrum": H.rel_l2(S_g, S_o), "rho": H.rel_l2(rho, o.rho),
          "pop": float(np.max(np.abs(P / o.P - 1.0)))}
-    print("256^3 bath, 1000 steps, kernel %d form %d:" % (info["kernel"], info["static_form"]), e)
+    print("256^3 bath, %d steps, kernel %d form %d:" % (steps, info["kernel"], info["static_form"]), e)
     tol = _tol(steps)
     assert e["fid"] <= tol and e["spectrum"] <= tol and e["rho"] <= tol and e["pop"] <= tol, e
 
