@@ -70,9 +70,9 @@ __device__ __forceinline__ int reservoir_ghost(const LatticeView& v, const ResFa
 template <typename WT>
 __global__ void k_pack(LatticeView v, const double* __restrict__ F, const double* __restrict__ omega,
                        const uint8_t* __restrict__ solid, double alpha, const double* __restrict__ links,
-                       double dt, double kT, ResFaces rf) {
-    const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pidx >= v.Np) return;
+                       double dt, double kT, ResFaces rf, long long p0, long long p1) {
+    const long long pidx = p0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pidx >= p1) return;
     WT* W = static_cast<WT*>(const_cast<void*>(v.w));
     float2* R = const_cast<float2*>(v.R);
     const int px = (int)(pidx % v.Xp);
@@ -320,13 +320,17 @@ int grid_for(long long n, int block) {
 
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
                         const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
-                        const ResFaces& rf, cudaStream_t st) {
+                        const ResFaces& rf, cudaStream_t st, int z0, int z1) {
+    if (z1 < 0) z1 = v.nz;
+    const long long plane = (long long)v.Xp * v.Yp;
+    const long long p0 = z0 * plane, p1 = z1 * plane;
+    if (p1 <= p0) return cudaSuccess;
     const int B = 256;
-    const long long g = (v.Np + B - 1) / B;
+    const long long g = (p1 - p0 + B - 1) / B;
     if (wdtype == LPC_WEIGHTS_BF16)
-        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf);
+        k_pack<__nv_bfloat16><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf, p0, p1);
     else
-        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf);
+        k_pack<float><<<(unsigned)g, B, 0, st>>>(v, F, omega, solid, alpha, alpha_links, dt, kT, rf, p0, p1);
     return cudaGetLastError();
 }
 

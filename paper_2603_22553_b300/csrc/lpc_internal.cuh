@@ -505,9 +505,11 @@ const DeviceProps& device_props();
 // Launchers (return cudaSuccess or the launch error).
 // alpha_links: null (alpha on every link) or device [3][N] per-link factors.
 // rf: reservoir faces (their out- and in-weights are packed beside the others).
+// [z0, z1): the planes packed (z1 < 0: to the last); a plane's weights read
+// the fields of the plane and of its z neighbours only.
 cudaError_t launch_pack(const LatticeView& v, int wdtype, const double* F, const double* omega,
                         const uint8_t* solid, double alpha, const double* alpha_links, double dt, double kT,
-                        const ResFaces& rf, cudaStream_t st);
+                        const ResFaces& rf, cudaStream_t st, int z0 = 0, int z1 = -1);
 // Write the reservoir values into the ghost sites of the reservoir faces, in
 // both state buffers.
 cudaError_t launch_reservoir_ghosts(const LatticeView& v, const ResFaces& rf, cudaStream_t st);

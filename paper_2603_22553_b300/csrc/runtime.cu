@@ -760,9 +760,48 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
         const long long minus_one = -1;
         e = cudaMemsetAsync(h->counter, 0, 256, h->wstream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->dstep, &minus_one, 8, cudaMemcpyHostToDevice, h->wstream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dO, omega, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid, solid, (size_t)N, cudaMemcpyHostToDevice, h->wstream);
+        // Large lattices without per-link factors upload F, omega and the
+        // mask in chunks of planes and pack each chunk on a second stream as
+        // soon as the chunk above it has arrived (a plane's weights read its
+        // own and its z neighbours' fields), so the pack overlaps the upload;
+        // the last chunk's arrival also releases the chunks that wrap in z.
+        const LatticeView pv = make_view(h, 1);    // the pack writes the static planes
+        const long long uplane = (long long)p->nx * p->ny;
+        const int nchunk = (!alpha_links && N >= (1LL << 22)) ? std::min(8, p->nz) : 1;
+        cudaStream_t ps = nullptr;
+        cudaEvent_t pev[9] = {};
+        bool packed = false;
+        if (e == cudaSuccess && nchunk > 1) {
+            e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+            for (int c = 0; c <= nchunk && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&pev[c], cudaEventDisableTiming);
+            auto zc = [&](int c) { return (int)((long long)p->nz * c / nchunk); };
+            for (int c = 0; c < nchunk && e == cudaSuccess; ++c) {
+                const long long o = zc(c) * uplane, n = (zc(c + 1) - zc(c)) * uplane;
+                e = cudaMemcpyAsync(dF + o, F + o, (size_t)n * 8, cudaMemcpyHostToDevice, h->wstream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(dO + o, omega + o, (size_t)n * 8, cudaMemcpyHostToDevice, h->wstream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid + o, solid + o, (size_t)n, cudaMemcpyHostToDevice, h->wstream);
+                if (e == cudaSuccess) e = cudaEventRecord(pev[c], h->wstream);
+            }
+            // chunk c waits for chunk c + 1 (its upper neighbour plane); with a
+            // periodic z the first and last chunks wait for the last one, and
+            // the first goes last on the pack stream
+            const bool wrap = p->periodic[2] != 0;
+            for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
+                const int c = wrap ? (i + 1) % nchunk : i;
+                const int need = (wrap && (c == 0 || c == nchunk - 1)) ? nchunk - 1 : std::min(c + 1, nchunk - 1);
+                e = cudaStreamWaitEvent(ps, pev[need], 0);
+                if (e == cudaSuccess)
+                    e = launch_pack(pv, p->weight_dtype, dF, dO, h->solid, p->alpha, nullptr, p->dt, p->kT, rf, ps,
+                                    zc(c), zc(c + 1));
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(pev[nchunk], ps);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->wstream, pev[nchunk], 0);
+            packed = e == cudaSuccess;
+        } else {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dO, omega, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->solid, solid, (size_t)N, cudaMemcpyHostToDevice, h->wstream);
+        }
         if (e == cudaSuccess && rho0) e = cudaMemcpyAsync(dR0, rho0, (size_t)N * 8, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess && alpha_links) e = cudaMemcpyAsync(dA, alpha_links, (size_t)N * 24, cudaMemcpyHostToDevice, h->wstream);
         if (e == cudaSuccess && o.region) {
@@ -778,7 +817,8 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
         if (e == cudaSuccess) st = ensure_history(h, 1024);
         if (e == cudaSuccess && st == LPC_OK) {
             LatticeView v = make_view(h, 1);   // writes go to buffer 0
-            e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, dA, p->dt, p->kT, rf, h->wstream);
+            if (!packed)
+                e = launch_pack(v, p->weight_dtype, dF, dO, h->solid, p->alpha, dA, p->dt, p->kT, rf, h->wstream);
             if (e == cudaSuccess)
                 e = launch_init_state(v, dR0, p->init, dF, h->solid, p->kT, h->scratch, h->wstream);
             if (e == cudaSuccess) e = launch_reservoir_ghosts(v, rf, h->wstream);
@@ -788,6 +828,13 @@ lpc_status create_impl(const lpc_params* p, const lpc_options* opt, const double
                 e = launch_region_sums(updated_view(h, 0), p->weight_dtype, h->rpart, h->counter + 12, false, h->wstream);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->wstream);
+        if (ps) {
+            // after an error the pack stream may still run: wait for it before the temporaries go
+            cudaStreamSynchronize(ps);
+            cudaStreamDestroy(ps);
+        }
+        for (int c = 0; c < 9; ++c)
+            if (pev[c]) cudaEventDestroy(pev[c]);
     }
     dfree(h, dF, (size_t)N * 8); dfree(h, dO, (size_t)N * 8); dfree(h, dR0, (size_t)N * 8);
     dfree(h, dA, (size_t)N * 24);
