@@ -46,6 +46,30 @@ def test_geometry_and_weights(case, wdt):
     lat.close()
 
 
+@pytest.mark.parametrize("shift_sd", [5.0, 150.0])
+def test_rotation_factors_small_and_large_phases(shift_sd):
+    """R = exp(i omega dt) (Eq. 7-8) as the pack stores it, for the method's
+    small phases (shifts of a few ppm) and for phases of several radians: the
+    FP32 value of the FP64 oracle's phase factor in all but a handful of
+    sites, never more than one unit in the last place from it."""
+    from paper_2603_22553_b300.lattice import Lattice
+    inp = lpc_inputs.random_case((24, 40, 70), 390, solid_frac=0.1, shift_sd=shift_sd, msd_axes=0)
+    theta = np.abs(inp.omega * inp.dt)
+    if shift_sd > 100:
+        assert np.mean(theta > 0.25) > 0.5 and theta.max() > 3.0     # both paths, and the wrap of large phases
+    else:
+        assert theta.max() < 0.25
+    lat = Lattice.from_input(inp)
+    R = lat.rotation().astype(np.float64)
+    lat.close()
+    pk = oracle.pack_input(inp, oracle.MODE_F32)
+    Ro = pk.R.reshape(inp.F.shape)
+    for part, ref in ((R[..., 0], Ro.real), (R[..., 1], Ro.imag)):
+        d = _ulp_diff(part, ref, 24)
+        assert d.max() <= 1.0
+        assert np.mean(part != ref) < 1e-4
+
+
 @pytest.mark.parametrize("case", range(4))
 def test_parity_small_fp32(case):
     inp = H.small_cases()[case]
